@@ -1,0 +1,360 @@
+"""Benchmark: BinSketch hot path on one GB300 (or N, one process per GPU).
+
+One step = sketch a CSR batch of n binary vectors (Definition "BinSketch") and
+run the all-pairs top-k ranking by estimated Jaccard (Alg. 1-3, Experiment 2
+as top-k), i.e. every row of the hot path.  The workload is the text-BoW
+configuration: n = 100,000 vectors over d = 1,000,000, nnz per row log-normal
+(median 200, sigma 1) clipped to [1, 5000], Zipf(1.0) columns, N = 4096,
+top-50 by Jaccard.  Inputs are synthetic and seeded (per rank: seed = rank).
+
+Prints one JSON line (rank 0).  ``value`` is pair estimates per second
+(ordered pairs q != j, each scored and filtered into the fused top-k), summed
+over ranks; ``e2e`` is the same through the C ABI with the CSR copied in from
+pinned host memory and the top-k copied back inside the timed region.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("CSR→sketch GB/s; sketch-pair estimates/s (top-k fused); "
+          "query p99 at fixed MSE")
+WORKLOAD = dict(workload="text-BoW all-pairs top-k", n=100_000, d=1_000_000, N=4096, k=50,
+                by="js", nnz="lognormal(median 200, sigma 1) clip [1,5000]", columns="Zipf(1.0)")
+
+
+def sketch_bytes(n, nnz, N):
+    """Algorithmic HBM bytes of one sketch launch: indices + offsets in, sketches + counts out."""
+    return 4 * nnz + 8 * (n + 1) + n * N // 8 + 4 * n
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def profile_traffic(kernel_file, name):
+    """dram bytes per launch recorded under profiles/ for the current kernel source, else None."""
+    src = os.path.join(ROOT, "paper_1910_04658_gb300", "csrc", kernel_file)
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", f"{name}.txt")
+    try:
+        rec = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                rec[k.strip()] = v.strip()
+        if rec.get("source_sha256_16") == sha:
+            return float(rec["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on a bounded sample of the same workload
+# ----------------------------------------------------------------------------
+
+def oracle_sample(csr, N, k, budget_s):
+    """Time the oracle: full sketch, then top-k for as many query rows as fit
+    in budget_s; returns (pair estimates/s, sketch GB/s, rows, seconds, threads)."""
+    import oracle
+    t0 = time.perf_counter()
+    sk, pc = oracle.sketch(csr.row_ptr, csr.col, csr.d, N, 0)
+    t_sketch = time.perf_counter() - t0
+    rows, t_topk, batch = 0, 0.0, 16
+    rng = np.random.default_rng(1)
+    while t_topk < budget_s:
+        q = rng.choice(csr.n, batch, replace=False)
+        t0 = time.perf_counter()
+        oracle.topk(sk[q], sk, N, oracle.JS, k, exclude_self=False)
+        t_topk += time.perf_counter() - t0
+        rows += batch
+        batch = min(batch * 2, 1024)
+    pairs_per_s = rows * (csr.n - 1) / t_topk
+    n = csr.n
+    step_s = t_sketch + n * (t_topk / rows)
+    total_pairs = n * (n - 1)
+    gbs = sketch_bytes(n, csr.nnz, N) / t_sketch / 1e9
+    return total_pairs / step_s, pairs_per_s, gbs, rows, t_topk + t_sketch, oracle.num_threads()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_1910_04658_gb300 import inputs
+    csr = inputs.bow_corpus(0)
+    N, k = WORKLOAD["N"], WORKLOAD["k"]
+    vals = []
+    info = None
+    for step in range(args.warmup + args.steps):
+        budget = 2.0 if step < args.warmup else 8.0
+        res = oracle_sample(csr, N, k, budget)
+        if step >= args.warmup:
+            vals.append(res[0])
+            info = res
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pair-estimates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": (WORKLOAD["n"] * (WORKLOAD["n"] - 1)) / value * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": dict(WORKLOAD, step="oracle: full sketch + sampled top-k rows"),
+        "cpu_baseline": {"kind": "oracle", "value": value, "unit": "pair-estimates/s",
+                         "cores": info[5],
+                         "sample": f"full sketch of 100,000 rows + top-{k} of {info[3]} sampled "
+                                   f"query rows per step, extrapolated to all rows"},
+        "e2e": {"value": value, "unit": "pair-estimates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    from paper_1910_04658_gb300 import api, binding as B, build, inputs
+
+    build.build()
+    B.lib()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    N, k = WORKLOAD["N"], WORKLOAD["k"]
+    csr = inputs.bow_corpus(seed=rank)
+    n, nnz = csr.n, csr.nnz
+    rp = torch.from_numpy(csr.row_ptr.view(np.int64)).to(dev)
+    col = torch.from_numpy(csr.col.view(np.int32)).to(dev)
+    sk = torch.empty((n, N // 32), dtype=torch.int32, device=dev)
+    pc = torch.empty((n,), dtype=torch.int32, device=dev)
+    score = torch.empty((n, k), dtype=torch.float32, device=dev)
+    idx = torch.empty((n, k), dtype=torch.int32, device=dev)
+    wsb = B.bs_topk_workspace_bytes(n, n, N, k)
+    ws = torch.empty((max(wsb, 16),), dtype=torch.uint8, device=dev)
+    launches_per_step = 2 + (1 if wsb else 0)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty((256 << 20,), dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def step(ev=None):
+        if ev: ev[0].record(stream)
+        B.bs_sketch(rp, col, n, nnz, csr.d, N, 0, sk, pc, stream)
+        if ev: ev[1].record(stream)
+        B.bs_topk(sk, pc, n, sk, pc, n, N, B.BS_JS, k, 1, score, idx, ws if wsb else None, wsb,
+                  stream)
+        if ev: ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    assert B.bs_get_async_error(stream) == 0
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # device-timed region: inputs resident; L2 flushed before every step (outside the events)
+    t_sk, t_tk = [], []
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        wall0 = time.perf_counter()
+        for s in range(args.steps):
+            flush.zero_()
+            step(evs[s])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    barrier()
+    for e in evs:
+        t_sk.append(e[0].elapsed_time(e[1]) / 1e3)
+        t_tk.append(e[1].elapsed_time(e[2]) / 1e3)
+    step_s = [a + b for a, b in zip(t_sk, t_tk)]
+    total_s = sum(step_s)
+    pairs = n * (n - 1)
+
+    # end to end through the C ABI: pinned host CSR in, top-k out, every step
+    h_rp = torch.from_numpy(csr.row_ptr.view(np.int64)).pin_memory()
+    h_col = torch.from_numpy(csr.col.view(np.int32)).pin_memory()
+    h_score = torch.empty((n, k), dtype=torch.float32).pin_memory()
+    h_idx = torch.empty((n, k), dtype=torch.int32).pin_memory()
+    e2e_s = []
+    for s in range(args.warmup + args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rp.copy_(h_rp, non_blocking=True)
+        col.copy_(h_col, non_blocking=True)
+        step()
+        h_score.copy_(score, non_blocking=True)
+        h_idx.copy_(idx, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if s >= args.warmup:
+            e2e_s.append(e0.elapsed_time(e1) / 1e3)
+    h2d = csr.row_ptr.nbytes + csr.col.nbytes
+    d2h = n * k * 8
+
+    # max over ranks, sums of units
+    t_max = total_s
+    e2e_max = sum(e2e_s)
+    if dist is not None:
+        t = torch.tensor([total_s, sum(e2e_s)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max, e2e_max = float(t[0]), float(t[1])
+    value = world * pairs * args.steps / t_max
+    e2e_value = world * pairs * args.steps / e2e_max
+
+    # roofline of the dominant kernel (the fused count + top-k launch)
+    W = N // 32
+    popc_per_launch = pairs * W            # one AND + POPC per 32-bit word pair
+    tk_mean = sum(t_tk) / len(t_tk)
+    pk = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max_mhz = pk.get("sm_max_mhz", 2070.0)
+    popc_peak = 16 * sm_count * sm_max_mhz * 1e6 / 1e12   # 16 POPC/clk/SM
+    achieved = popc_per_launch / tk_mean / 1e12
+    traffic = profile_traffic("bs_pairs.cu", "pair_topk_traffic")
+    sk_mean = sum(t_sk) / len(t_sk)
+    sk_gbs = sketch_bytes(n, nnz, N) / sk_mean / 1e9
+    hbm_peak = pk.get("hbm_gbs", 6800.0)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "pair-estimates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32+f32",
+        "data": "synthetic",
+        "config": dict(WORKLOAD, l2="flushed (256 MB write) before every timed step",
+                       parallelism=f"independent corpus per rank x{world}"),
+        "roofline": {"bound": "alu", "kernel": "pair_kernel<TOPK,JS> (AND+POPC)",
+                     "achieved": achieved, "peak": popc_peak, "unit": "Tword-popc/s",
+                     "frac": achieved / popc_peak, "traffic": traffic,
+                     "peak_source": "16 POPC/clk/SM x SMs x max SM clock (recipe units/clocks)"},
+        "components": {
+            "sketch_ms": sk_mean * 1e3, "sketch_GBps": sk_gbs,
+            "sketch_frac_of_measured_hbm": sk_gbs / hbm_peak,
+            "topk_ms": tk_mean * 1e3, "topk_pair_estimates_per_s": pairs / tk_mean,
+            "wall_s_timed_region": wall},
+        "e2e": {"value": e2e_value, "unit": "pair-estimates/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, pps, gbs, rows, secs, thr = oracle_sample(csr, N, k, args.cpu_budget)
+        line["cpu_baseline"] = {
+            "value": v, "unit": "pair-estimates/s", "cores": thr, "kind": "oracle",
+            "sample": f"oracle: full sketch ({gbs:.3f} GB/s) + top-{k} of {rows} sampled query "
+                      f"rows vs all 100,000, extrapolated to the full step ({secs:.1f} s of CPU work)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist_mod
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    try:
+        run_ours(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,170 @@
+/*
+ * binsketch.h -- C ABI of the GB300 BinSketch library (libbinsketch.so).
+ *
+ * BinSketch (Pratap, Bera, Revanuru, arXiv 1910.04658) compresses a sparse
+ * binary vector a in {0,1}^d into an N-bit vector a_s whose bit j is the OR
+ * of the bits of a mapped to j by a random mapping pi : [d] -> [N]
+ * (Definition "BinSketch", Sec. 3), and estimates inner product, Hamming
+ * distance, Jaccard and cosine similarity of two vectors from the counts
+ * |a_s|, |b_s| and <a_s, b_s> of their sketches (Alg. 1-4, Sec. 3.1-3.4).
+ * Ranking (Experiment 2, Sec. 4) is offered as a per-query top-k.
+ *
+ * Conventions shared by every call
+ *  - All array arguments are DEVICE pointers owned by the caller; the library
+ *    allocates nothing on these paths and never frees caller memory.
+ *  - Every call is asynchronous on `stream` (NULL = legacy default stream)
+ *    and never synchronises.  Argument errors are reported immediately by the
+ *    return value and nothing is launched.  Data errors found by the kernels
+ *    (column index >= d, malformed row offsets) do not fault: the offending
+ *    row is skipped (its sketch and count are written as zero) and a sticky
+ *    per-device flag is raised; bs_get_async_error() reads and clears it.
+ *  - Sketch layout: row r of a sketch matrix is N/32 consecutive uint32
+ *    words; bucket j is bit (j & 31) of word (j >> 5) (LSB first).  Rows are
+ *    contiguous (row stride N/32 words).
+ *  - Column indices are 0-based (the paper counts from 1).
+ *  - The mapping pi is a seeded multiply-add-shift hash (the paper only
+ *    requires a random mapping): (mult, add) are the first two SplitMix64
+ *    outputs of `seed` with mult forced odd;
+ *    pi(i) = floor(N * hi32(mult * i + add mod 2^64) / 2^32).
+ *    Sketches are comparable only when made with the same (seed, N).
+ */
+#ifndef BINSKETCH_H
+#define BINSKETCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t / CUstream. */
+typedef struct CUstream_st *bs_stream_t;
+
+typedef enum {
+    BS_OK = 0,
+    BS_ERR_INVALID_ARG = 1,   /* NULL pointer, bad size or N, k out of range  */
+    BS_ERR_INDEX_RANGE = 2,   /* (async) a column index was >= d              */
+    BS_ERR_ROWPTR = 3,        /* (async) row offsets decrease or exceed nnz   */
+    BS_ERR_CUDA = 4,          /* a CUDA runtime/driver call failed            */
+    BS_ERR_NO_MEMORY = 5,     /* workspace too small                          */
+    BS_ERR_TIMEOUT = 6,       /* a bounded device wait gave up                */
+    BS_ERR_UNSUPPORTED = 7    /* valid request outside what is implemented    */
+} bs_status;
+
+/* Similarity measures (bit mask for bs_estimate_pairs, one value for bs_topk). */
+enum { BS_IP = 1, BS_HAM = 2, BS_JS = 4, BS_COS = 8 };
+
+/* Limits. */
+enum { BS_N_MAX = 65536, BS_TOPK_K_MAX = 128 };
+
+/*
+ * bs_sketch -- sketch a CSR batch of binary vectors (Definition "BinSketch",
+ * Sec. 3: a_s[j] = OR_{i : pi(i) = j} a[i]) and count |a_s| (Alg. 1 step 1).
+ *
+ *  row_ptr  uint64[n_rows + 1]  row r lists col[row_ptr[r] .. row_ptr[r+1])
+ *  col      uint32[nnz]         column indices, < d; any order, repeats allowed
+ *  n_rows   number of vectors (0 is a valid empty batch)
+ *  nnz      number of entries of `col` (row_ptr[n_rows] must equal it)
+ *  d        original dimension
+ *  N        sketch length in bits: a multiple of 32, 32 <= N <= BS_N_MAX
+ *  seed     selects the mapping pi (see above)
+ *  sketch   uint32[n_rows][N/32] output
+ *  popcnt   uint32[n_rows] output |a_s| (may be NULL)
+ * Errors: BS_ERR_INVALID_ARG for NULL pointers (with n_rows > 0) or bad N;
+ *         asynchronous BS_ERR_INDEX_RANGE / BS_ERR_ROWPTR for bad data.
+ */
+bs_status bs_sketch(const uint64_t *row_ptr, const uint32_t *col, uint32_t n_rows, uint64_t nnz,
+                    uint32_t d, uint32_t N, uint64_t seed, uint32_t *sketch, uint32_t *popcnt,
+                    bs_stream_t stream);
+
+/*
+ * bs_sketch_parity -- the BCS sketch of the same batch (Definition "BCS",
+ * Sec. 2): u_s[j] = sum_{i : pi(i) = j} u[i] mod 2, with the same mapping.
+ * Arguments and errors as bs_sketch.  Rows must not repeat a column (a
+ * repeat would cancel itself).
+ */
+bs_status bs_sketch_parity(const uint64_t *row_ptr, const uint32_t *col, uint32_t n_rows,
+                           uint64_t nnz, uint32_t d, uint32_t N, uint64_t seed,
+                           uint32_t *sketch, uint32_t *popcnt, bs_stream_t stream);
+
+/*
+ * bs_popcount_rows -- |a_s| of n_rows packed sketches (Alg. 1 step 1), for
+ * callers that hold sketches without their counts.
+ *  sketch uint32[n_rows][N/32] in, popcnt uint32[n_rows] out.
+ */
+bs_status bs_popcount_rows(const uint32_t *sketch, uint32_t n_rows, uint32_t N, uint32_t *popcnt,
+                           bs_stream_t stream);
+
+/*
+ * bs_estimate_pairs -- every (A row i, B row j) pair: the common-bit count
+ * n_{a_s,b_s} = <a_s, b_s> (Alg. 1 step 2) and the requested estimates in
+ * FP32: IP (Alg. 1), Ham (Alg. 2, read as n_a + n_b - 2 n_{a,b}), JS (Alg. 3)
+ * and Cos (Alg. 4).
+ *
+ *  A, B       uint32[nA][N/32], uint32[nB][N/32] sketches (same seed and N)
+ *  pcA, pcB   uint32[nA], uint32[nB] their |a_s| (from bs_sketch or
+ *             bs_popcount_rows)
+ *  N          a multiple of 32, 32 <= N <= BS_N_MAX
+ *  measures   OR of BS_IP | BS_HAM | BS_JS | BS_COS (0 allowed with counts)
+ *  out        float[m][nA][nB], m = number of bits set in `measures`, planes
+ *             in the order IP, HAM, JS, COS (may be NULL when measures = 0)
+ *  counts     uint32[nA][nB] common-bit counts (may be NULL)
+ * Saturated counts are clamped so that N - |a_s|, N - |b_s| and
+ * N - |a_s OR b_s| are at least 1; Cos = 0 when an estimated size is 0 and
+ * JS = 0 when the estimated union is 0.  Estimates are not clamped.
+ */
+bs_status bs_estimate_pairs(const uint32_t *A, const uint32_t *pcA, uint32_t nA,
+                            const uint32_t *B, const uint32_t *pcB, uint32_t nB, uint32_t N,
+                            uint32_t measures, float *out, uint32_t *counts, bs_stream_t stream);
+
+/*
+ * bs_topk_workspace_bytes -- device workspace bs_topk needs for this shape
+ * (0 when the problem runs without a cross-block merge).
+ */
+size_t bs_topk_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k);
+
+/*
+ * bs_topk -- ranking (Experiment 2, Sec. 4) as a top-k: for every query row
+ * q, the k DB rows with the best estimate `by` (one of BS_IP, BS_JS, BS_COS:
+ * largest first; BS_HAM: smallest first), ties broken by smaller DB index.
+ * The count/estimate matrix is never materialised.
+ *
+ *  Q, pcQ       uint32[nQ][N/32] query sketches and their |a_s|
+ *  DB, pcDB     uint32[nDB][N/32] database sketches and their |b_s|
+ *  k            1 <= k <= BS_TOPK_K_MAX
+ *  exclude_self non-zero: skip the pair (q, q) -- for all-pairs use with
+ *               Q == DB (query row q is DB row q)
+ *  score        float[nQ][k] estimates of the returned pairs, best first;
+ *               unused slots (nDB < k) hold -inf (+inf for BS_HAM)
+ *  idx          uint32[nQ][k] DB row of each slot; 0xFFFFFFFF when unused
+ *  workspace    device memory of at least bs_topk_workspace_bytes(...)
+ *               bytes (may be NULL when that is 0); contents are scratch
+ * Errors: BS_ERR_NO_MEMORY when workspace_bytes is too small.
+ */
+bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
+                  const uint32_t *DB, const uint32_t *pcDB, uint32_t nDB, uint32_t N,
+                  uint32_t by, uint32_t k, int exclude_self, float *score, uint32_t *idx,
+                  void *workspace, size_t workspace_bytes, bs_stream_t stream);
+
+/*
+ * bs_get_async_error -- synchronise `stream`, return the first data error
+ * raised by a kernel on the current device since the last call (BS_OK if
+ * none) and clear it.  BS_ERR_CUDA if the synchronisation itself failed.
+ */
+bs_status bs_get_async_error(bs_stream_t stream);
+
+/* Hash parameters (mult, add) that `seed` selects (host computation). */
+void bs_hash_params(uint64_t seed, uint64_t *mult, uint64_t *add);
+
+/* Human-readable name of a status. */
+const char *bs_status_string(bs_status s);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int bs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BINSKETCH_H */

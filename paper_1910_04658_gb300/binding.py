@@ -1,0 +1,131 @@
+"""Thin ctypes binding of libbinsketch.so (the C ABI in include/binsketch.h).
+
+Each function has the name of the C entry point it calls and only marshals
+arguments: tensors become device pointers, ``stream=None`` becomes the current
+torch stream.  All work runs in the library's CUDA kernels; if the library is
+missing, ``lib()`` raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_build", "libbinsketch.so")
+
+BS_IP, BS_HAM, BS_JS, BS_COS = 1, 2, 4, 8
+MEASURE_BITS = {"ip": BS_IP, "ham": BS_HAM, "js": BS_JS, "cos": BS_COS}
+BS_TOPK_K_MAX = 128
+BS_N_MAX = 65536
+STATUS = {0: "BS_OK", 1: "BS_ERR_INVALID_ARG", 2: "BS_ERR_INDEX_RANGE", 3: "BS_ERR_ROWPTR",
+          4: "BS_ERR_CUDA", 5: "BS_ERR_NO_MEMORY", 6: "BS_ERR_TIMEOUT", 7: "BS_ERR_UNSUPPORTED"}
+
+_lock = threading.Lock()
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point
+_u32, _u64, _i32, _sz, _vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p
+SIGNATURES = [
+    ("bs_sketch", _i32, [_vp, _vp, _u32, _u64, _u32, _u32, _u64, _vp, _vp, _vp]),
+    ("bs_sketch_parity", _i32, [_vp, _vp, _u32, _u64, _u32, _u32, _u64, _vp, _vp, _vp]),
+    ("bs_popcount_rows", _i32, [_vp, _u32, _u32, _vp, _vp]),
+    ("bs_estimate_pairs", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp]),
+    ("bs_topk_workspace_bytes", _sz, [_u32, _u32, _u32, _u32]),
+    ("bs_topk", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, _i32, _vp, _vp, _vp,
+                       _sz, _vp]),
+    ("bs_get_async_error", _i32, [_vp]),
+    ("bs_hash_params", None, [_u64, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
+    ("bs_status_string", ctypes.c_char_p, [_i32]),
+    ("bs_version", _i32, []),
+]
+
+
+class BinSketchError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is not built; run paper_1910_04658_gb300.build.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, res, args in SIGNATURES:
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _p(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _s(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise BinSketchError(rc, where)
+
+
+def bs_sketch(row_ptr, col, n_rows, nnz, d, N, seed, sketch, popcnt=None, stream=None):
+    _check(lib().bs_sketch(_p(row_ptr), _p(col), n_rows, nnz, d, N, seed, _p(sketch), _p(popcnt),
+                           _s(stream)), "bs_sketch")
+
+
+def bs_sketch_parity(row_ptr, col, n_rows, nnz, d, N, seed, sketch, popcnt=None, stream=None):
+    _check(lib().bs_sketch_parity(_p(row_ptr), _p(col), n_rows, nnz, d, N, seed, _p(sketch),
+                                  _p(popcnt), _s(stream)), "bs_sketch_parity")
+
+
+def bs_popcount_rows(sketch, n_rows, N, popcnt, stream=None):
+    _check(lib().bs_popcount_rows(_p(sketch), n_rows, N, _p(popcnt), _s(stream)), "bs_popcount_rows")
+
+
+def bs_estimate_pairs(A, pcA, nA, B, pcB, nB, N, measures, out=None, counts=None, stream=None):
+    _check(lib().bs_estimate_pairs(_p(A), _p(pcA), nA, _p(B), _p(pcB), nB, N, measures, _p(out),
+                                   _p(counts), _s(stream)), "bs_estimate_pairs")
+
+
+def bs_topk_workspace_bytes(nQ, nDB, N, k) -> int:
+    return int(lib().bs_topk_workspace_bytes(nQ, nDB, N, k))
+
+
+def bs_topk(Q, pcQ, nQ, DB, pcDB, nDB, N, by, k, exclude_self, score, idx, workspace=None,
+            workspace_bytes=0, stream=None):
+    _check(lib().bs_topk(_p(Q), _p(pcQ), nQ, _p(DB), _p(pcDB), nDB, N, by, k, int(exclude_self),
+                         _p(score), _p(idx), _p(workspace), workspace_bytes, _s(stream)), "bs_topk")
+
+
+def bs_get_async_error(stream=None) -> int:
+    return int(lib().bs_get_async_error(_s(stream)))
+
+
+def bs_hash_params(seed: int):
+    m, a = _u64(), _u64()
+    lib().bs_hash_params(seed, ctypes.byref(m), ctypes.byref(a))
+    return m.value, a.value
+
+
+def bs_status_string(code: int) -> str:
+    return lib().bs_status_string(code).decode()
+
+
+def bs_version() -> int:
+    return int(lib().bs_version())

@@ -1,0 +1,181 @@
+// Internal helpers shared by the CUDA translation units of libbinsketch.
+// Nothing here is part of the C ABI (see include/binsketch.h).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "binsketch.h"
+
+namespace bs {
+
+// ---------------------------------------------------------------------------
+// Host-side shared state
+// ---------------------------------------------------------------------------
+
+// Device address of the sticky data-error word of the current device
+// (defined in bs_sketch.cu); nullptr if it could not be resolved.
+unsigned int *error_word();
+
+// Number of SMs of the current device (cached).
+int sm_count();
+
+// cuTensorMapEncodeTiled resolved through the runtime (no -lcuda needed).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled();
+
+// SplitMix64-derived hash parameters (host).
+void hash_params(uint64_t seed, uint64_t *mult, uint64_t *add);
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+
+// pi(i) = floor(N * hi32(mult * i + add mod 2^64) / 2^32)
+__device__ __forceinline__ uint32_t bucket_of(uint32_t i, uint64_t mult, uint64_t add, uint32_t N) {
+    const uint64_t h = mult * (uint64_t)i + add;
+    return __umulhi((uint32_t)(h >> 32), N);
+}
+
+__device__ __forceinline__ void raise_error(unsigned int *err, unsigned int code) {
+    if (err) atomicCAS(err, 0u, code);
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// ---- mbarrier ---------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after `limit_ns` of wall time and returns false.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) return false;
+    }
+}
+
+// ---- TMA --------------------------------------------------------------------
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
+                                            int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// consumer-warps-only named barrier
+__device__ __forceinline__ void named_sync(uint32_t id, uint32_t nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Estimation (Alg. 1-4) from integer counts, FP32.
+//
+// With n = 1 - 1/N, L = ln n, A = N - a, B = N - b and U = N - (a + b - c)
+// (a = |a_s|, b = |b_s|, c = <a_s, b_s>), Alg. 1 gives n^{n_a} = A/N, so its
+// log argument n^{n_a} + n^{n_b} + c/N - 1 equals U/N and
+//    IP * L = ln(A B / (N U)),  n_a * L = ln(A / N),  n_u * L = ln(U / N)
+//   Ham * L = ln(U^2 / (A B))            (Ham = n_a + n_b - 2 IP)
+//        JS = ln(A B / (N U)) / ln(U / N) (IP / (IP + Ham) = IP / n_u)
+//       Cos = -ln(A B / (N U)) / sqrt(ln(A/N) ln(B/N))
+// Every logarithm is of a ratio p/q of exact integers, taken as
+// log1p((p - q)/q) when p is near q, so the FP32 result keeps ~1e-7 relative
+// accuracy even where the estimate itself is close to 0.
+// Saturation: a, b and the union a + b - c are capped at N - 1, so A, B, U >= 1.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float ln_ratio(long long p, long long q) {
+    const long long diff = p - q;
+    const long long ad = diff < 0 ? -diff : diff;
+    if (2 * ad <= q) return log1pf((float)diff / (float)q);
+    return logf((float)p / (float)q);
+}
+
+struct Clamped {
+    long long A, B, U;
+};
+
+__device__ __forceinline__ Clamped clamp_counts(uint32_t a, uint32_t b, uint32_t c, uint32_t N) {
+    const uint32_t cap = N - 1;
+    uint32_t u = a + b - c;
+    a = a < cap ? a : cap;
+    b = b < cap ? b : cap;
+    u = u < cap ? u : cap;
+    Clamped r;
+    r.A = (long long)(N - a);
+    r.B = (long long)(N - b);
+    r.U = (long long)(N - u);
+    return r;
+}
+
+// ln(A/N) for a row count a (per row, reused across pairs).
+__device__ __forceinline__ float row_log(uint32_t a, uint32_t N) {
+    const uint32_t cap = N - 1;
+    a = a < cap ? a : cap;
+    return ln_ratio((long long)(N - a), (long long)N);
+}
+
+// measure codes used inside the kernels
+enum { M_IP = 0, M_HAM = 1, M_JS = 2, M_COS = 3 };
+
+// One estimate; lnA = row_log(a), lnB = row_log(b); invL = 1/ln(1 - 1/N).
+template <int M>
+__device__ __forceinline__ float estimate_one(uint32_t a, uint32_t b, uint32_t c, uint32_t N,
+                                              float lnA, float lnB, float invL) {
+    const Clamped k = clamp_counts(a, b, c, N);
+    if (M == M_IP) {
+        return ln_ratio(k.A * k.B, (long long)N * k.U) * invL;
+    } else if (M == M_HAM) {
+        return ln_ratio(k.U * k.U, k.A * k.B) * invL;
+    } else if (M == M_JS) {
+        const float lu = ln_ratio(k.U, (long long)N);
+        if (lu == 0.0f) return 0.0f;
+        return ln_ratio(k.A * k.B, (long long)N * k.U) / lu;
+    } else {
+        const float p = lnA * lnB;
+        if (!(p > 0.0f)) return 0.0f;
+        return -ln_ratio(k.A * k.B, (long long)N * k.U) * rsqrtf(p);
+    }
+}
+
+}  // namespace bs

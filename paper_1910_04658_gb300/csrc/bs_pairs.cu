@@ -1,0 +1,596 @@
+// Pair counting and estimation: Alg. 1 step 2 (n_{a_s,b_s} = <a_s, b_s>),
+// the estimators of Alg. 1-4, and the ranking of Experiment 2 (Sec. 4) as a
+// fused per-query top-k.  Variant "LOP3+POPC": the common-bit count of two
+// packed rows is the sum over words of popc(a_w & b_w).
+//
+// Block layout: one producer warp streams 128-byte-wide k-chunks of a BM-row
+// query tile and a BN-row database tile into a STAGES-deep shared-memory ring
+// with TMA (cp.async.bulk.tensor, 128-byte swizzle, mbarrier completion); 8
+// consumer warps (16x16 threads, each owning 2 query rows x 8 database rows)
+// read 16-byte swizzled words, AND them and accumulate popcounts in
+// registers.  Either the estimates are written out (bs_estimate_pairs) or
+// each pair's score is filtered against the running k-th best of its query
+// row and kept in a per-row candidate buffer that is bitonic-sorted and cut
+// back to k whenever it could overflow (bs_topk); the count matrix never
+// reaches HBM.  When few query tiles exist the database is split across
+// blocks and a second kernel merges the per-split top-k lists.
+#include <math.h>
+
+#include "bs_internal.cuh"
+
+namespace bs {
+
+constexpr int KC = 32;            // words per k-chunk (128 bytes of a row)
+constexpr int BM = 32;            // query rows per block
+constexpr int BN = 128;           // database rows per tile
+constexpr int STAGES = 4;
+constexpr int CONSUMERS = 256;    // 8 warps
+constexpr int THREADS = CONSUMERS + 32;
+constexpr int CAP = 256;          // candidate slots per query row
+constexpr int A_TILE_BYTES = BM * KC * 4;
+constexpr int B_TILE_BYTES = BN * KC * 4;
+constexpr int STAGE_BYTES = A_TILE_BYTES + B_TILE_BYTES;
+constexpr uint32_t NO_IDX = 0xFFFFFFFFu;
+
+static_assert(STAGE_BYTES % 1024 == 0, "stages must keep 1024-byte alignment for the swizzle");
+static_assert(BN <= CAP - BS_TOPK_K_MAX, "a full tile of candidates must fit after a merge");
+
+enum { MODE_ESTIMATE = 0, MODE_TOPK = 1 };
+
+struct PairArgs {
+    const uint32_t *Q;      // [nQ][W]   (LDG producer path)
+    const uint32_t *DB;     // [nDB][W]
+    const uint32_t *pcQ;
+    const uint32_t *pcDB;
+    uint32_t nQ, nDB, N, W, nK;
+    float invL;             // 1 / ln(1 - 1/N)
+    // estimate mode
+    uint32_t measures;      // bit mask
+    float *out;
+    uint32_t *counts;
+    // top-k mode
+    uint32_t k;
+    int exclude_self;
+    uint32_t splits;        // database splits (grid.y)
+    uint32_t tiles_per_split;
+    float *score;           // final output (splits == 1)
+    uint32_t *idx;
+    float *ws_key;          // [splits][nQ][k] (splits > 1)
+    uint32_t *ws_idx;
+    unsigned int *err;
+};
+
+struct __align__(8) PairSmemHdr {
+    uint64_t full[STAGES];
+    uint64_t empty[STAGES];
+    int abort_flag;
+};
+
+// better(a, b): a ranks strictly before b -- larger key, then smaller index
+__device__ __forceinline__ bool better(float ka, uint32_t ia, float kb, uint32_t ib) {
+    return ka > kb || (ka == kb && ia < ib);
+}
+
+// Bitonic sort (best first) of n = power of two entries by one warp.
+__device__ void warp_sort_best_first(float *key, uint32_t *ix, int n, int lane) {
+    for (int size = 2; size <= n; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = lane; t < (n >> 1); t += 32) {
+                const int i = 2 * t - (t & (stride - 1));
+                const int j = i + stride;
+                const bool up = (i & size) == 0;
+                const float ki = key[i], kj = key[j];
+                const uint32_t ii = ix[i], ij = ix[j];
+                if (better(kj, ij, ki, ii) == up) {
+                    key[i] = kj; key[j] = ki;
+                    ix[i] = ij; ix[j] = ii;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Sort a candidate row and keep its best min(cnt, k); returns the new count.
+__device__ int shrink_row(float *key, uint32_t *ix, int cnt, int k, int lane) {
+    int n = 32;
+    while (n < cnt) n <<= 1;
+    for (int t = cnt + lane; t < n; t += 32) {
+        key[t] = -INFINITY;
+        ix[t] = NO_IDX;
+    }
+    __syncwarp();
+    warp_sort_best_first(key, ix, n, lane);
+    return cnt < k ? cnt : k;
+}
+
+// word (4-word group q of row r) inside a 128-byte-swizzled tile of 32-word rows
+__device__ __forceinline__ const uint4 *swz(const uint32_t *tile, int r, int q) {
+    return reinterpret_cast<const uint4 *>(tile + r * KC + (((q ^ (r & 7)) << 2)));
+}
+
+template <int M>
+__device__ __forceinline__ float rank_key(uint32_t a, uint32_t b, uint32_t c, uint32_t N, float lnA,
+                                          float lnB, float invL) {
+    const float v = estimate_one<M>(a, b, c, N, lnA, lnB, invL);
+    return M == M_HAM ? -v : v;
+}
+
+// Producer (LDG path, any N multiple of 32): one warp copies a tile with plain
+// loads into the same swizzled layout TMA would produce.
+__device__ __forceinline__ void ldg_fill(uint32_t *tile, const uint32_t *src, uint32_t n_src,
+                                         int row0, int rows, int kc, uint32_t W, int lane) {
+    const uint32_t w = (uint32_t)kc * KC + lane;
+    for (int r0 = 0; r0 < rows; r0 += 8) {
+        uint32_t v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int r = r0 + u;
+            const uint32_t gr = (uint32_t)(row0 + r);
+            v[u] = (r < rows && gr < n_src && w < W) ? __ldg(src + (size_t)gr * W + w) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int r = r0 + u;
+            if (r < rows) tile[r * KC + ((((lane >> 2) ^ (r & 7)) << 2) | (lane & 3))] = v[u];
+        }
+    }
+}
+
+template <int MODE, int M, bool TMA>
+__global__ void __launch_bounds__(THREADS, 1)
+    pair_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUtensorMap mapDB,
+                const PairArgs p) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // 1024-byte aligned base for the swizzled tiles
+    uint8_t *base = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint32_t *tiles = reinterpret_cast<uint32_t *>(base);
+    PairSmemHdr *hdr = reinterpret_cast<PairSmemHdr *>(base + STAGES * STAGE_BYTES);
+    uint8_t *after_hdr = base + STAGES * STAGE_BYTES + sizeof(PairSmemHdr);
+    // per-row data
+    float *row_ln = reinterpret_cast<float *>(after_hdr);            // [BM]
+    uint32_t *row_pc = reinterpret_cast<uint32_t *>(row_ln + BM);    // [BM]
+    int *cand_cnt = reinterpret_cast<int *>(row_pc + BM);            // [BM]
+    float *thr_key = reinterpret_cast<float *>(cand_cnt + BM);       // [BM]
+    uint32_t *thr_idx = reinterpret_cast<uint32_t *>(thr_key + BM);  // [BM]
+    float *cand_key = reinterpret_cast<float *>(thr_idx + BM);       // [BM][CAP]
+    uint32_t *cand_idx = reinterpret_cast<uint32_t *>(cand_key + BM * CAP);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+
+    const uint32_t row0 = blockIdx.x * BM;
+    uint32_t tile_begin, tile_end;
+    const uint32_t n_tiles_total = (p.nDB + BN - 1) / BN;
+    if (MODE == MODE_TOPK) {
+        tile_begin = blockIdx.y * p.tiles_per_split;
+        tile_end = min(n_tiles_total, tile_begin + p.tiles_per_split);
+        if (tile_begin > tile_end) tile_begin = tile_end;
+    } else {
+        tile_begin = blockIdx.y;
+        tile_end = blockIdx.y + 1;
+    }
+
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&hdr->full[s], TMA ? 1u : 32u);
+            mbar_init(&hdr->empty[s], CONSUMERS / 32);
+        }
+        hdr->abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (tid < BM) {
+        const uint32_t q = row0 + tid;
+        const uint32_t a = q < p.nQ ? p.pcQ[q] : 0u;
+        row_pc[tid] = a;
+        row_ln[tid] = row_log(a, p.N);
+        cand_cnt[tid] = 0;
+        thr_key[tid] = -INFINITY;
+        thr_idx[tid] = NO_IDX;
+    }
+    __syncthreads();
+
+    volatile int *abort_flag = &hdr->abort_flag;
+
+    if (warp == CONSUMERS / 32) {
+        // ------------------------------ producer ------------------------------
+        uint32_t it = 0;
+        for (uint32_t t = tile_begin; t < tile_end; ++t) {
+            for (uint32_t kc = 0; kc < p.nK; ++kc, ++it) {
+                const uint32_t s = it % STAGES;
+                const uint32_t use = it / STAGES;
+                if (use > 0 && !*abort_flag) {
+                    bool ok = true;
+                    if (lane == 0) ok = mbar_wait(&hdr->empty[s], (use - 1) & 1u);
+                    ok = __shfl_sync(0xffffffffu, ok, 0);
+                    if (!ok) {
+                        if (lane == 0) {
+                            raise_error(p.err, BS_ERR_TIMEOUT);
+                            *abort_flag = 1;
+                        }
+                    }
+                }
+                __syncwarp();
+                if (*abort_flag) continue;
+                uint32_t *tA = tiles + (size_t)s * (STAGE_BYTES / 4);
+                uint32_t *tB = tA + A_TILE_BYTES / 4;
+                if (TMA) {
+                    if (lane == 0) {
+                        mbar_arrive_expect_tx(&hdr->full[s], STAGE_BYTES);
+                        tma_load_2d(tA, &mapQ, &hdr->full[s], (int)(kc * KC), (int)row0);
+                        tma_load_2d(tB, &mapDB, &hdr->full[s], (int)(kc * KC), (int)(t * BN));
+                    }
+                } else {
+                    ldg_fill(tA, p.Q, p.nQ, (int)row0, BM, (int)kc, p.W, lane);
+                    ldg_fill(tB, p.DB, p.nDB, (int)(t * BN), BN, (int)kc, p.W, lane);
+                    mbar_arrive(&hdr->full[s]);
+                }
+            }
+        }
+        // drain: make sure no copy into this block's shared memory is still in flight
+        if (TMA && lane == 0 && it > 0) {
+            const uint32_t first = it > (uint32_t)STAGES ? it - STAGES : 0u;
+            for (uint32_t j = first; j < it; ++j) mbar_wait(&hdr->full[j % STAGES], (j / STAGES) & 1u);
+        }
+        return;
+    }
+
+    // ------------------------------- consumers --------------------------------
+    const int ty = tid >> 4;   // 0..15
+    const int tx = tid & 15;   // 0..15
+    uint32_t it = 0;
+    for (uint32_t t = tile_begin; t < tile_end; ++t) {
+        uint32_t acc[2][8];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0u;
+
+        for (uint32_t kc = 0; kc < p.nK; ++kc, ++it) {
+            const uint32_t s = it % STAGES;
+            if (!*abort_flag && !mbar_wait(&hdr->full[s], (it / STAGES) & 1u)) {
+                raise_error(p.err, BS_ERR_TIMEOUT);
+                *abort_flag = 1;
+            }
+            const uint32_t *tA = tiles + (size_t)s * (STAGE_BYTES / 4);
+            const uint32_t *tB = tA + A_TILE_BYTES / 4;
+#pragma unroll 2
+            for (int q = 0; q < KC / 4; ++q) {
+                uint4 a[2], b[8];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) a[i] = *swz(tA, ty + 16 * i, q);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) b[j] = *swz(tB, tx + 16 * j, q);
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        acc[i][j] += __popc(a[i].x & b[j].x) + __popc(a[i].y & b[j].y) +
+                                     __popc(a[i].z & b[j].z) + __popc(a[i].w & b[j].w);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&hdr->empty[s]);
+        }
+
+        // ------------------------------ epilogue ------------------------------
+        const uint32_t col0 = t * BN;
+        if (MODE == MODE_ESTIMATE) {
+            const size_t plane = (size_t)p.nQ * p.nDB;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = ty + 16 * i;
+                const uint32_t q = row0 + r;
+                if (q >= p.nQ) continue;
+                const uint32_t a = row_pc[r];
+                const float lnA = row_ln[r];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const uint32_t c = col0 + tx + 16 * j;
+                    if (c >= p.nDB) continue;
+                    const size_t o = (size_t)q * p.nDB + c;
+                    const uint32_t cnt = acc[i][j];
+                    if (p.counts) p.counts[o] = cnt;
+                    if (p.measures) {
+                        const uint32_t b = __ldg(p.pcDB + c);
+                        const float lnB = row_log(b, p.N);
+                        float *dst = p.out + o;
+                        if (p.measures & BS_IP) { *dst = estimate_one<M_IP>(a, b, cnt, p.N, lnA, lnB, p.invL); dst += plane; }
+                        if (p.measures & BS_HAM) { *dst = estimate_one<M_HAM>(a, b, cnt, p.N, lnA, lnB, p.invL); dst += plane; }
+                        if (p.measures & BS_JS) { *dst = estimate_one<M_JS>(a, b, cnt, p.N, lnA, lnB, p.invL); dst += plane; }
+                        if (p.measures & BS_COS) { *dst = estimate_one<M_COS>(a, b, cnt, p.N, lnA, lnB, p.invL); }
+                    }
+                }
+            }
+        } else {
+            uint32_t bcnt[8];
+            float lnB[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t c = col0 + tx + 16 * j;
+                bcnt[j] = c < p.nDB ? __ldg(p.pcDB + c) : 0u;
+                lnB[j] = M == M_COS ? row_log(bcnt[j], p.N) : 0.0f;
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = ty + 16 * i;
+                const uint32_t q = row0 + r;
+                if (q >= p.nQ) continue;
+                const float tk = thr_key[r];
+                const uint32_t ti = thr_idx[r];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const uint32_t c = col0 + tx + 16 * j;
+                    if (c >= p.nDB || (p.exclude_self && c == q)) continue;
+                    const float key = rank_key<M>(row_pc[r], bcnt[j], acc[i][j], p.N, row_ln[r],
+                                                  lnB[j], p.invL);
+                    if (better(key, c, tk, ti)) {
+                        const int slot = atomicAdd(&cand_cnt[r], 1);
+                        if (slot < CAP) {   // always true: a shrink leaves room for a tile
+                            cand_key[r * CAP + slot] = key;
+                            cand_idx[r * CAP + slot] = c;
+                        }
+                    }
+                }
+            }
+            named_sync(1, CONSUMERS);
+            // shrink rows that could not take another full tile
+            for (int r = warp; r < BM; r += CONSUMERS / 32) {
+                const int cnt = cand_cnt[r];
+                if (cnt > CAP - BN) {
+                    const int kept = shrink_row(cand_key + r * CAP, cand_idx + r * CAP, cnt,
+                                                (int)p.k, lane);
+                    if (lane == 0) {
+                        cand_cnt[r] = kept;
+                        if (kept == (int)p.k) {
+                            thr_key[r] = cand_key[r * CAP + kept - 1];
+                            thr_idx[r] = cand_idx[r * CAP + kept - 1];
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            named_sync(1, CONSUMERS);
+        }
+    }
+
+    if (MODE == MODE_TOPK) {
+        for (int r = warp; r < BM; r += CONSUMERS / 32) {
+            const uint32_t q = row0 + r;
+            if (q >= p.nQ) continue;
+            const int kept = shrink_row(cand_key + r * CAP, cand_idx + r * CAP, cand_cnt[r],
+                                        (int)p.k, lane);
+            for (int s = lane; s < (int)p.k; s += 32) {
+                float kk = s < kept ? cand_key[r * CAP + s] : -INFINITY;
+                uint32_t ii = s < kept ? cand_idx[r * CAP + s] : NO_IDX;
+                if (p.splits == 1) {
+                    const size_t o = (size_t)q * p.k + s;
+                    p.score[o] = (M == M_HAM) ? -kk : kk;
+                    p.idx[o] = ii;
+                } else {
+                    const size_t o = ((size_t)blockIdx.y * p.nQ + q) * p.k + s;
+                    p.ws_key[o] = kk;
+                    p.ws_idx[o] = ii;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Merge the per-split top-k lists of each query row (one warp per row).
+template <int M>
+__global__ void __launch_bounds__(256)
+    merge_topk_kernel(const float *__restrict__ ws_key, const uint32_t *__restrict__ ws_idx,
+                      uint32_t nQ, uint32_t k, uint32_t splits, float *__restrict__ score,
+                      uint32_t *__restrict__ idx) {
+    __shared__ float skey[8][CAP];
+    __shared__ uint32_t sidx[8][CAP];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *key = skey[warp];
+    uint32_t *ix = sidx[warp];
+    for (uint32_t q = blockIdx.x * 8 + warp; q < nQ; q += gridDim.x * 8) {
+        int cnt = 0;
+        float tk = -INFINITY;
+        uint32_t ti = NO_IDX;
+        for (uint32_t s = 0; s < splits; ++s) {
+            const size_t o = ((size_t)s * nQ + q) * k;
+            for (uint32_t t0 = 0; t0 < k; t0 += 32) {
+                const uint32_t t = t0 + lane;
+                float kk = -INFINITY;
+                uint32_t ii = NO_IDX;
+                if (t < k) {
+                    kk = ws_key[o + t];
+                    ii = ws_idx[o + t];
+                }
+                const bool take = t < k && ii != NO_IDX && better(kk, ii, tk, ti);
+                const uint32_t m = __ballot_sync(0xffffffffu, take);
+                const int slot = cnt + __popc(m & ((1u << lane) - 1u));
+                if (take && slot < CAP) {
+                    key[slot] = kk;
+                    ix[slot] = ii;
+                }
+                cnt += __popc(m);
+            }
+            __syncwarp();
+            if (cnt > CAP - (int)k) {
+                cnt = shrink_row(key, ix, cnt, (int)k, lane);
+                if (cnt == (int)k) {
+                    tk = key[k - 1];
+                    ti = ix[k - 1];
+                }
+            }
+        }
+        const int kept = shrink_row(key, ix, cnt, (int)k, lane);
+        for (uint32_t t = lane; t < k; t += 32) {
+            const float kk = (int)t < kept ? key[t] : -INFINITY;
+            score[(size_t)q * k + t] = (M == M_HAM) ? -kk : kk;
+            idx[(size_t)q * k + t] = (int)t < kept ? ix[t] : NO_IDX;
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+static size_t pair_smem_bytes(int mode) {
+    size_t b = 1024 /* alignment slack */ + (size_t)STAGES * STAGE_BYTES + sizeof(PairSmemHdr) +
+               5 * BM * 4;
+    if (mode == MODE_TOPK) b += (size_t)BM * CAP * 8;
+    return b;
+}
+
+static bool make_map(CUtensorMap *m, const uint32_t *ptr, uint32_t rows, uint32_t W, int box_rows) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {W, rows};
+    cuuint64_t strides[1] = {(cuuint64_t)W * 4};
+    cuuint32_t box[2] = {KC, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, (void *)ptr, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static bool tma_ok(const uint32_t *A, const uint32_t *B, uint32_t N) {
+    return (N % 128) == 0 && N >= 1024 && (reinterpret_cast<uintptr_t>(A) & 15u) == 0 &&
+           (reinterpret_cast<uintptr_t>(B) & 15u) == 0;
+}
+
+template <int MODE, int M>
+static bs_status launch_pairs(const PairArgs &p, dim3 grid, cudaStream_t stream) {
+    CUtensorMap mq, md;
+    memset(&mq, 0, sizeof(mq));
+    memset(&md, 0, sizeof(md));
+    bool use_tma = tma_ok(p.Q, p.DB, p.N);
+    if (use_tma) {
+        use_tma = make_map(&mq, p.Q, p.nQ, p.W, BM) && make_map(&md, p.DB, p.nDB, p.W, BN);
+    }
+    const size_t smem = pair_smem_bytes(MODE);
+    if (use_tma) {
+        auto kern = pair_kernel<MODE, M, true>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return BS_ERR_CUDA;
+        kern<<<grid, THREADS, smem, stream>>>(mq, md, p);
+    } else {
+        auto kern = pair_kernel<MODE, M, false>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return BS_ERR_CUDA;
+        kern<<<grid, THREADS, smem, stream>>>(mq, md, p);
+    }
+    return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+}
+
+static bool valid_N(uint32_t N) { return N >= 32 && N <= BS_N_MAX && (N % 32) == 0; }
+
+static float inv_ln_n(uint32_t N) { return (float)(1.0 / log1p(-1.0 / (double)N)); }
+
+// database splits for a top-k problem on this device
+static uint32_t topk_splits(uint32_t nQ, uint32_t nDB) {
+    const uint32_t row_blocks = (nQ + BM - 1) / BM;
+    const uint32_t tiles = (nDB + BN - 1) / BN;
+    if (row_blocks == 0 || tiles == 0) return 1;
+    const uint32_t target = 2u * (uint32_t)sm_count();
+    uint32_t s = (target + row_blocks - 1) / row_blocks;
+    // keep at least 4 tiles per split
+    const uint32_t max_s = (tiles + 3) / 4;
+    if (s > max_s) s = max_s;
+    if (s < 1) s = 1;
+    // make the split count match the per-split tile count exactly
+    const uint32_t per = (tiles + s - 1) / s;
+    return (tiles + per - 1) / per;
+}
+
+}  // namespace bs
+
+using namespace bs;
+
+extern "C" {
+
+bs_status bs_estimate_pairs(const uint32_t *A, const uint32_t *pcA, uint32_t nA, const uint32_t *B,
+                            const uint32_t *pcB, uint32_t nB, uint32_t N, uint32_t measures,
+                            float *out, uint32_t *counts, bs_stream_t stream) {
+    if (!valid_N(N) || (measures & ~15u)) return BS_ERR_INVALID_ARG;
+    if (nA == 0 || nB == 0) return BS_OK;
+    if (!A || !B || !pcA || !pcB) return BS_ERR_INVALID_ARG;
+    if (measures && !out) return BS_ERR_INVALID_ARG;
+    if (!measures && !counts) return BS_OK;
+    unsigned int *err = error_word();
+    if (!err) return BS_ERR_CUDA;
+    PairArgs p = {};
+    p.Q = A; p.DB = B; p.pcQ = pcA; p.pcDB = pcB;
+    p.nQ = nA; p.nDB = nB; p.N = N; p.W = N / 32; p.nK = (p.W + KC - 1) / KC;
+    p.invL = inv_ln_n(N);
+    p.measures = measures; p.out = out; p.counts = counts;
+    p.splits = 1; p.err = err;
+    dim3 grid((nA + BM - 1) / BM, (nB + BN - 1) / BN);
+    if (grid.y > 65535) return BS_ERR_UNSUPPORTED;
+    return launch_pairs<MODE_ESTIMATE, 0>(p, grid, (cudaStream_t)stream);
+}
+
+size_t bs_topk_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k) {
+    (void)N;
+    if (nQ == 0 || nDB == 0 || k == 0) return 0;
+    const uint32_t s = topk_splits(nQ, nDB);
+    if (s <= 1) return 0;
+    return (size_t)s * nQ * k * (sizeof(float) + sizeof(uint32_t));
+}
+
+bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
+                  const uint32_t *pcDB, uint32_t nDB, uint32_t N, uint32_t by, uint32_t k,
+                  int exclude_self, float *score, uint32_t *idx, void *workspace,
+                  size_t workspace_bytes, bs_stream_t stream) {
+    if (!valid_N(N)) return BS_ERR_INVALID_ARG;
+    if (k == 0 || k > BS_TOPK_K_MAX) return BS_ERR_INVALID_ARG;
+    if (by != BS_IP && by != BS_HAM && by != BS_JS && by != BS_COS) return BS_ERR_INVALID_ARG;
+    if (nQ == 0) return BS_OK;
+    if (!Q || !pcQ || !score || !idx) return BS_ERR_INVALID_ARG;
+    if (nDB > 0 && (!DB || !pcDB)) return BS_ERR_INVALID_ARG;
+    if (exclude_self && nQ > nDB) return BS_ERR_INVALID_ARG;
+    unsigned int *err = error_word();
+    if (!err) return BS_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    PairArgs p = {};
+    p.Q = Q; p.DB = DB; p.pcQ = pcQ; p.pcDB = pcDB;
+    p.nQ = nQ; p.nDB = nDB; p.N = N; p.W = N / 32; p.nK = (p.W + KC - 1) / KC;
+    p.invL = inv_ln_n(N);
+    p.k = k; p.exclude_self = exclude_self; p.err = err;
+    p.score = score; p.idx = idx;
+    const uint32_t tiles = (nDB + BN - 1) / BN;
+    const uint32_t splits = topk_splits(nQ, nDB);
+    p.splits = splits;
+    p.tiles_per_split = splits ? (tiles + splits - 1) / splits : 0;
+    if (splits > 1) {
+        const size_t need = (size_t)splits * nQ * k * (sizeof(float) + sizeof(uint32_t));
+        if (!workspace || workspace_bytes < need) return BS_ERR_NO_MEMORY;
+        if ((reinterpret_cast<uintptr_t>(workspace) & 15u) != 0) return BS_ERR_INVALID_ARG;
+        p.ws_key = reinterpret_cast<float *>(workspace);
+        p.ws_idx = reinterpret_cast<uint32_t *>(p.ws_key + (size_t)splits * nQ * k);
+    }
+    dim3 grid((nQ + BM - 1) / BM, splits);
+    if (grid.y > 65535) return BS_ERR_UNSUPPORTED;
+    bs_status st1;
+    switch (by) {
+        case BS_IP: st1 = launch_pairs<MODE_TOPK, M_IP>(p, grid, st); break;
+        case BS_HAM: st1 = launch_pairs<MODE_TOPK, M_HAM>(p, grid, st); break;
+        case BS_JS: st1 = launch_pairs<MODE_TOPK, M_JS>(p, grid, st); break;
+        default: st1 = launch_pairs<MODE_TOPK, M_COS>(p, grid, st); break;
+    }
+    if (st1 != BS_OK || splits <= 1) return st1;
+    const uint32_t blocks = (nQ + 7) / 8;
+    switch (by) {
+        case BS_IP: merge_topk_kernel<M_IP><<<blocks, 256, 0, st>>>(p.ws_key, p.ws_idx, nQ, k, splits, score, idx); break;
+        case BS_HAM: merge_topk_kernel<M_HAM><<<blocks, 256, 0, st>>>(p.ws_key, p.ws_idx, nQ, k, splits, score, idx); break;
+        case BS_JS: merge_topk_kernel<M_JS><<<blocks, 256, 0, st>>>(p.ws_key, p.ws_idx, nQ, k, splits, score, idx); break;
+        default: merge_topk_kernel<M_COS><<<blocks, 256, 0, st>>>(p.ws_key, p.ws_idx, nQ, k, splits, score, idx); break;
+    }
+    return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,286 @@
+// Sketching: Definition "BinSketch" (Sec. 3) and BCS (Definition "BCS", Sec. 2).
+//
+// One warp per CSR row.  The row's N/32-word sketch lives in shared memory,
+// the warp streams the row's column indices with coalesced 16-byte loads
+// (after peeling to 16-byte alignment), hashes each index to its bucket and
+// sets the bucket bit with a shared-memory atomicOr (atomicXor for BCS).  The
+// finished row is written to HBM with 16-byte stores and its popcount |a_s|
+// is reduced across the warp on the way out.  HBM traffic per row is the
+// algorithmic minimum: the row's indices and offsets in, N/8 + 4 bytes out.
+#include <mutex>
+
+#include "bs_internal.cuh"
+
+namespace bs {
+
+// Sticky first data error per device; read and cleared by bs_get_async_error.
+__device__ unsigned int g_async_error;
+
+unsigned int *error_word() {
+    static std::mutex mu;
+    static unsigned int *ptr[256] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return nullptr;
+    std::lock_guard<std::mutex> g(mu);
+    if (!ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_async_error) != cudaSuccess) return nullptr;
+        ptr[dev] = (unsigned int *)p;
+    }
+    return ptr[dev];
+}
+
+int sm_count() {
+    static std::mutex mu;
+    static int cnt[256] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return 148;
+    std::lock_guard<std::mutex> g(mu);
+    if (!cnt[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cnt[dev] = v > 0 ? v : 148;
+    }
+    return cnt[dev];
+}
+
+EncodeTiledFn encode_tiled() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014).
+static uint64_t splitmix64(uint64_t *s) {
+    uint64_t z = (*s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+void hash_params(uint64_t seed, uint64_t *mult, uint64_t *add) {
+    uint64_t s = seed;
+    *mult = splitmix64(&s) | 1ull;
+    *add = splitmix64(&s);
+}
+
+// ---------------------------------------------------------------------------
+// K1: sketch kernel
+// ---------------------------------------------------------------------------
+
+constexpr int kSketchWarps = 8;
+
+template <bool PARITY>
+__device__ __forceinline__ void set_bucket(uint32_t *s, uint32_t i, uint32_t d, uint64_t mult,
+                                           uint64_t add, uint32_t N, bool &bad) {
+    if (i >= d) {
+        bad = true;
+        return;
+    }
+    const uint32_t j = bucket_of(i, mult, add, N);
+    if (PARITY)
+        atomicXor(&s[j >> 5], 1u << (j & 31));
+    else
+        atomicOr(&s[j >> 5], 1u << (j & 31));
+}
+
+template <bool PARITY>
+__global__ void __launch_bounds__(kSketchWarps * 32)
+    sketch_kernel(const uint64_t *__restrict__ row_ptr, const uint32_t *__restrict__ col,
+                  uint32_t n_rows, uint64_t nnz, uint32_t d, uint32_t N, uint64_t mult,
+                  uint64_t add, uint32_t *__restrict__ sketch, uint32_t *__restrict__ popcnt,
+                  unsigned int *err) {
+    extern __shared__ __align__(16) uint32_t smem_words[];
+    const uint32_t W = N >> 5;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    uint32_t *s = smem_words + (size_t)warp * W;
+    const uint32_t nwarps = gridDim.x * kSketchWarps;
+    const bool vec_out = (W & 3u) == 0 && ((reinterpret_cast<uintptr_t>(sketch) & 15u) == 0);
+
+    for (uint32_t r = blockIdx.x * kSketchWarps + warp; r < n_rows; r += nwarps) {
+        const uint64_t b = row_ptr[r];
+        const uint64_t e = row_ptr[r + 1];
+        for (uint32_t w = lane; w < W; w += 32) s[w] = 0u;
+        __syncwarp();
+
+        bool bad = false;
+        const bool ok = (b <= e) && (e <= nnz);
+        if (ok) {
+            // peel until col + k is 16-byte aligned
+            const uint32_t mis = (uint32_t)((reinterpret_cast<uintptr_t>(col + b) >> 2) & 3u);
+            uint64_t k = b;
+            const uint64_t peel_end = min(e, b + ((4u - mis) & 3u));
+            if (k + lane < peel_end) set_bucket<PARITY>(s, col[k + lane], d, mult, add, N, bad);
+            k = peel_end;
+            const uint64_t nvec = (e - k) >> 2;
+            const uint4 *v = reinterpret_cast<const uint4 *>(col + k);
+            // four independent 16-byte loads in flight per lane before any atomics
+            for (uint64_t t = lane; t < nvec; t += 128) {
+                uint4 x[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (t + 32 * u < nvec) x[u] = __ldg(v + t + 32 * u);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (t + 32 * u < nvec) {
+                        set_bucket<PARITY>(s, x[u].x, d, mult, add, N, bad);
+                        set_bucket<PARITY>(s, x[u].y, d, mult, add, N, bad);
+                        set_bucket<PARITY>(s, x[u].z, d, mult, add, N, bad);
+                        set_bucket<PARITY>(s, x[u].w, d, mult, add, N, bad);
+                    }
+                }
+            }
+            k += nvec << 2;
+            if (k + lane < e) set_bucket<PARITY>(s, col[k + lane], d, mult, add, N, bad);
+        }
+        bad = __any_sync(0xffffffffu, bad);
+        if (lane == 0) {
+            if (!ok) raise_error(err, BS_ERR_ROWPTR);
+            else if (bad) raise_error(err, BS_ERR_INDEX_RANGE);
+        }
+        const bool zero = !ok || bad;
+        __syncwarp();
+
+        uint32_t cnt = 0;
+        uint32_t *out = sketch + (size_t)r * W;
+        if (vec_out) {
+            const uint4 *sv = reinterpret_cast<const uint4 *>(s);
+            uint4 *ov = reinterpret_cast<uint4 *>(out);
+            for (uint32_t t = lane; t < (W >> 2); t += 32) {
+                uint4 x = zero ? make_uint4(0, 0, 0, 0) : sv[t];
+                cnt += __popc(x.x) + __popc(x.y) + __popc(x.z) + __popc(x.w);
+                ov[t] = x;
+            }
+        } else {
+            for (uint32_t t = lane; t < W; t += 32) {
+                const uint32_t x = zero ? 0u : s[t];
+                cnt += __popc(x);
+                out[t] = x;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (popcnt && lane == 0) popcnt[r] = cnt;
+        __syncwarp();
+    }
+}
+
+__global__ void popcount_rows_kernel(const uint32_t *__restrict__ sk, uint32_t n_rows, uint32_t W,
+                                     uint32_t *__restrict__ pc) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n_rows; r += nwarps) {
+        uint32_t cnt = 0;
+        const uint32_t *row = sk + (size_t)r * W;
+        for (uint32_t t = lane; t < W; t += 32) cnt += __popc(row[t]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0) pc[r] = cnt;
+    }
+}
+
+static bool valid_N(uint32_t N) { return N >= 32 && N <= BS_N_MAX && (N % 32) == 0; }
+
+template <bool PARITY>
+static bs_status launch_sketch(const uint64_t *row_ptr, const uint32_t *col, uint32_t n_rows,
+                               uint64_t nnz, uint32_t d, uint32_t N, uint64_t seed,
+                               uint32_t *sketch, uint32_t *popcnt, bs_stream_t stream) {
+    if (!valid_N(N)) return BS_ERR_INVALID_ARG;
+    if (n_rows == 0) return BS_OK;
+    if (!row_ptr || !sketch || (nnz > 0 && !col)) return BS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(col) & 3u) != 0) return BS_ERR_INVALID_ARG;
+    unsigned int *err = error_word();
+    if (!err) return BS_ERR_CUDA;
+    uint64_t mult, add;
+    hash_params(seed, &mult, &add);
+    const size_t smem = (size_t)kSketchWarps * (N / 32) * sizeof(uint32_t);
+    auto kern = sketch_kernel<PARITY>;
+    if (smem > 48 * 1024) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return BS_ERR_CUDA;
+    }
+    const uint32_t want = (n_rows + kSketchWarps - 1) / kSketchWarps;
+    const uint32_t cap = (uint32_t)sm_count() * 32u;
+    const uint32_t grid = want < cap ? want : cap;
+    kern<<<grid, kSketchWarps * 32, smem, (cudaStream_t)stream>>>(row_ptr, col, n_rows, nnz, d, N,
+                                                                  mult, add, sketch, popcnt, err);
+    return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+}
+
+}  // namespace bs
+
+using namespace bs;
+
+extern "C" {
+
+bs_status bs_sketch(const uint64_t *row_ptr, const uint32_t *col, uint32_t n_rows, uint64_t nnz,
+                    uint32_t d, uint32_t N, uint64_t seed, uint32_t *sketch, uint32_t *popcnt,
+                    bs_stream_t stream) {
+    return launch_sketch<false>(row_ptr, col, n_rows, nnz, d, N, seed, sketch, popcnt, stream);
+}
+
+bs_status bs_sketch_parity(const uint64_t *row_ptr, const uint32_t *col, uint32_t n_rows,
+                           uint64_t nnz, uint32_t d, uint32_t N, uint64_t seed, uint32_t *sketch,
+                           uint32_t *popcnt, bs_stream_t stream) {
+    return launch_sketch<true>(row_ptr, col, n_rows, nnz, d, N, seed, sketch, popcnt, stream);
+}
+
+bs_status bs_popcount_rows(const uint32_t *sketch, uint32_t n_rows, uint32_t N, uint32_t *popcnt,
+                           bs_stream_t stream) {
+    if (!valid_N(N)) return BS_ERR_INVALID_ARG;
+    if (n_rows == 0) return BS_OK;
+    if (!sketch || !popcnt) return BS_ERR_INVALID_ARG;
+    const uint32_t want = (n_rows + 7) / 8;
+    const uint32_t cap = (uint32_t)sm_count() * 32u;
+    popcount_rows_kernel<<<want < cap ? want : cap, 256, 0, (cudaStream_t)stream>>>(
+        sketch, n_rows, N / 32, popcnt);
+    return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+}
+
+bs_status bs_get_async_error(bs_stream_t stream) {
+    unsigned int *err = error_word();
+    if (!err) return BS_ERR_CUDA;
+    unsigned int host = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return BS_ERR_CUDA;
+    if (cudaMemcpyAsync(&host, err, sizeof(host), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return BS_ERR_CUDA;
+    if (cudaMemsetAsync(err, 0, sizeof(unsigned int), s) != cudaSuccess) return BS_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return BS_ERR_CUDA;
+    return (bs_status)host;
+}
+
+void bs_hash_params(uint64_t seed, uint64_t *mult, uint64_t *add) {
+    uint64_t m, a;
+    hash_params(seed, &m, &a);
+    if (mult) *mult = m;
+    if (add) *add = a;
+}
+
+const char *bs_status_string(bs_status s) {
+    switch (s) {
+        case BS_OK: return "ok";
+        case BS_ERR_INVALID_ARG: return "invalid argument";
+        case BS_ERR_INDEX_RANGE: return "column index out of range";
+        case BS_ERR_ROWPTR: return "malformed row offsets";
+        case BS_ERR_CUDA: return "CUDA error";
+        case BS_ERR_NO_MEMORY: return "workspace too small";
+        case BS_ERR_TIMEOUT: return "device wait timed out";
+        case BS_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+int bs_version(void) { return 100; }
+
+}  // extern "C"
