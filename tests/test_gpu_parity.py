@@ -147,9 +147,13 @@ def test_estimates_ragged_tiles(N):
 @pytest.mark.parametrize("N", [256, 1024])
 def test_estimates_saturated_regime(N):
     # nnz uniform in [N/4, 4N]: sketches near saturation (clamp reading)
+    # plus a few rows of 20N columns, whose sketches fill up (|a_s| = N)
     c = inputs.uniform_csr(3, 90, 100_000, N // 4, 4 * N)
+    f = inputs.uniform_csr(4, 6, 100_000, 20 * N, 20 * N)
+    rp = np.concatenate([c.row_ptr, f.row_ptr[1:] + c.row_ptr[-1]]).astype(np.uint64)
+    c = inputs.CSR(rp, np.concatenate([c.col, f.col]), c.d)
     sk, pc = _gpu_sketch(c, N, 8)
-    assert (u32(pc) >= N - 1).any()
+    assert (u32(pc) == N).any()
     _check_pairs(sk, pc, sk, pc, N)
 
 
