@@ -198,7 +198,7 @@ def run_ours(args, rank, world, dist):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     N, k = WORKLOAD["N"], WORKLOAD["k"]
-    csr = inputs.bow_corpus(seed=rank)
+    csr = inputs.bow_corpus(seed=rank, n=args.n)
     n, nnz = csr.n, csr.nnz
     rp = torch.from_numpy(csr.row_ptr.view(np.int64)).to(dev)
     col = torch.from_numpy(csr.col.view(np.int32)).to(dev)
@@ -302,7 +302,7 @@ def run_ours(args, rank, world, dist):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32+f32",
         "data": "synthetic",
-        "config": dict(WORKLOAD, l2="flushed (256 MB write) before every timed step",
+        "config": dict(WORKLOAD, n=n, l2="flushed (256 MB write) before every timed step",
                        parallelism=f"independent corpus per rank x{world}"),
         "roofline": {"bound": "alu", "kernel": "pair_kernel<TOPK,JS> (AND+POPC)",
                      "achieved": achieved, "peak": popc_peak, "unit": "Tword-popc/s",
@@ -318,7 +318,7 @@ def run_ours(args, rank, world, dist):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and n == WORKLOAD["n"]:
         v, pps, gbs, rows, secs, thr = oracle_sample(csr, N, k, args.cpu_budget)
         line["cpu_baseline"] = {
             "value": v, "unit": "pair-estimates/s", "cores": thr, "kind": "oracle",
@@ -336,6 +336,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=WORKLOAD["n"],
+                    help="rows of the corpus (smaller only for profiling captures)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
