@@ -148,6 +148,27 @@ bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
                   void *workspace, size_t workspace_bytes, bs_stream_t stream);
 
 /*
+ * bs_topk_noalloc -- bs_topk for callers that may not allocate GPU memory
+ * (a serving process whose arena owns the whole device, a plugin living in
+ * another framework's allocator, a request path that must not pay for an
+ * allocation).  The paper has no counterpart: this is a library service.
+ * Same arguments, results and errors as bs_topk, minus the workspace: the
+ * scratch bs_topk would need lives in a fixed device array of
+ * BS_TOPK_NOALLOC_SCRATCH_BYTES inside the library, present on every GPU that
+ * loads it until the process exits.  Shapes whose bs_topk_workspace_bytes()
+ * exceeds that size are refused with BS_ERR_NO_MEMORY (nothing launched).
+ * The array's address is looked up on the first call on each device (make
+ * that call before any stream capture).  Calls share the array: calls whose
+ * kernels overlap on the GPU race on it and must be serialised by the caller.
+ * Allocates nothing.
+ */
+enum { BS_TOPK_NOALLOC_SCRATCH_BYTES = 16 << 20 };
+bs_status bs_topk_noalloc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
+                          const uint32_t *DB, const uint32_t *pcDB, uint32_t nDB, uint32_t N,
+                          uint32_t by, uint32_t k, int exclude_self, float *score, uint32_t *idx,
+                          bs_stream_t stream);
+
+/*
  * bs_get_async_error -- synchronise `stream`, return the first data error
  * raised by a kernel on the current device since the last call (BS_OK if
  * none) and clear it.  BS_ERR_CUDA if the synchronisation itself failed.

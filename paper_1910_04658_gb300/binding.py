@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(PKG, "_build", "libbinsketch.so")
 BS_IP, BS_HAM, BS_JS, BS_COS = 1, 2, 4, 8
 MEASURE_BITS = {"ip": BS_IP, "ham": BS_HAM, "js": BS_JS, "cos": BS_COS}
 BS_TOPK_K_MAX = 128
+BS_TOPK_NOALLOC_SCRATCH_BYTES = 16 << 20
 BS_N_MAX = 65536
 STATUS = {0: "BS_OK", 1: "BS_ERR_INVALID_ARG", 2: "BS_ERR_INDEX_RANGE", 3: "BS_ERR_ROWPTR",
           4: "BS_ERR_CUDA", 5: "BS_ERR_NO_MEMORY", 6: "BS_ERR_TIMEOUT", 7: "BS_ERR_UNSUPPORTED"}
@@ -34,6 +35,8 @@ SIGNATURES = [
     ("bs_topk_workspace_bytes", _sz, [_u32, _u32, _u32, _u32]),
     ("bs_topk", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, _i32, _vp, _vp, _vp,
                        _sz, _vp]),
+    ("bs_topk_noalloc", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, _i32, _vp, _vp,
+                               _vp]),
     ("bs_get_async_error", _i32, [_vp]),
     ("bs_hash_params", None, [_u64, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     ("bs_status_string", ctypes.c_char_p, [_i32]),
@@ -111,6 +114,12 @@ def bs_topk(Q, pcQ, nQ, DB, pcDB, nDB, N, by, k, exclude_self, score, idx, works
             workspace_bytes=0, stream=None):
     _check(lib().bs_topk(_p(Q), _p(pcQ), nQ, _p(DB), _p(pcDB), nDB, N, by, k, int(exclude_self),
                          _p(score), _p(idx), _p(workspace), workspace_bytes, _s(stream)), "bs_topk")
+
+
+def bs_topk_noalloc(Q, pcQ, nQ, DB, pcDB, nDB, N, by, k, exclude_self, score, idx, stream=None):
+    _check(lib().bs_topk_noalloc(_p(Q), _p(pcQ), nQ, _p(DB), _p(pcDB), nDB, N, by, k,
+                                 int(exclude_self), _p(score), _p(idx), _s(stream)),
+           "bs_topk_noalloc")
 
 
 def bs_get_async_error(stream=None) -> int:
