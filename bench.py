@@ -208,7 +208,7 @@ def run_ours(args, rank, world, dist):
     idx = torch.empty((n, k), dtype=torch.int32, device=dev)
     wsb = B.bs_topk_workspace_bytes(n, n, N, k)
     ws = torch.empty((max(wsb, 16),), dtype=torch.uint8, device=dev)
-    launches_per_step = 2 + (1 if wsb else 0)
+    launches_per_step = 2 + (1 if wsb else 0)   # sketch, count+top-k, merge (when split)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty((256 << 20,), dtype=torch.uint8, device=dev)   # > 129 MB L2
 
@@ -283,18 +283,47 @@ def run_ours(args, rank, world, dist):
     value = world * pairs * args.steps / t_max
     e2e_value = world * pairs * args.steps / e2e_max
 
+    # the CUDA-core (POPC) variant on the same workload, once, for comparison
+    t_popc = None
+    if not args.no_popc_compare:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        B.bs_topk_ex(sk, pc, n, sk, pc, n, N, B.BS_JS, k, 1, score, idx, ws if wsb else None, wsb,
+                     B.BS_VARIANT_POPC, stream)
+        e1.record(stream)
+        e1.synchronize()
+        t_popc = e0.elapsed_time(e1) / 1e3
+
     # roofline of the dominant kernel (the fused count + top-k launch)
     W = N // 32
-    popc_per_launch = pairs * W            # one AND + POPC per 32-bit word pair
+    t_tk_sorted = sorted(t_tk)
     tk_mean = sum(t_tk) / len(t_tk)
     pk = measured_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max_mhz = pk.get("sm_max_mhz", 2070.0)
-    popc_peak = 16 * sm_count * sm_max_mhz * 1e6 / 1e12   # 16 POPC/clk/SM
-    achieved = popc_per_launch / tk_mean / 1e12
-    traffic = profile_traffic("bs_pairs.cu", "pair_topk_traffic")
-    sk_mean = sum(t_sk) / len(t_sk)
-    sk_gbs = sketch_bytes(n, nnz, N) / sk_mean / 1e9
+    use_tc = N % 128 == 0 and 256 <= N <= 8192 and k <= 100
+    if use_tc:
+        # dense 0/1 contraction on the FP8 tensor pipe: 2 flops per (pair, bit)
+        flops = 2.0 * pairs * N
+        bf16 = pk.get("bf16_tflops")
+        peak = (bf16 if bf16 else 1900.0) * (4.5 / 2.25)
+        roof = {"bound": "tensor", "kernel": "pair_tc_kernel<JS> (tcgen05.mma kind::f8f6f4)",
+                "achieved": flops / tk_mean / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / tk_mean / 1e12 / peak,
+                "traffic": profile_traffic("bs_pairs_tc.cu", "pair_tc_topk_traffic"),
+                "peak_source": ("measured cuBLAS bf16 burst x 2 (nominal fp8/bf16 dense ratio)"
+                                if bf16 else "fallback 1.9 PF bf16 x 2")}
+    else:
+        popc_peak = 16 * sm_count * sm_max_mhz * 1e6 / 1e12   # 16 POPC/clk/SM
+        achieved = pairs * W / tk_mean / 1e12
+        roof = {"bound": "alu", "kernel": "pair_kernel<TOPK,JS> (AND+POPC)",
+                "achieved": achieved, "peak": popc_peak, "unit": "Tword-popc/s",
+                "frac": achieved / popc_peak,
+                "traffic": profile_traffic("bs_pairs.cu", "pair_topk_traffic"),
+                "peak_source": "16 POPC/clk/SM x SMs x max SM clock (recipe units/clocks)"}
+    sk_med = sorted(t_sk)[len(t_sk) // 2]
+    sk_gbs = sketch_bytes(n, nnz, N) / sk_med / 1e9
     hbm_peak = pk.get("hbm_gbs", 6800.0)
 
     line = {
@@ -304,14 +333,14 @@ def run_ours(args, rank, world, dist):
         "data": "synthetic",
         "config": dict(WORKLOAD, n=n, l2="flushed (256 MB write) before every timed step",
                        parallelism=f"independent corpus per rank x{world}"),
-        "roofline": {"bound": "alu", "kernel": "pair_kernel<TOPK,JS> (AND+POPC)",
-                     "achieved": achieved, "peak": popc_peak, "unit": "Tword-popc/s",
-                     "frac": achieved / popc_peak, "traffic": traffic,
-                     "peak_source": "16 POPC/clk/SM x SMs x max SM clock (recipe units/clocks)"},
+        "roofline": roof,
         "components": {
-            "sketch_ms": sk_mean * 1e3, "sketch_GBps": sk_gbs,
+            "sketch_ms_median": sk_med * 1e3, "sketch_GBps": sk_gbs,
             "sketch_frac_of_measured_hbm": sk_gbs / hbm_peak,
-            "topk_ms": tk_mean * 1e3, "topk_pair_estimates_per_s": pairs / tk_mean,
+            "topk_ms": tk_mean * 1e3, "topk_ms_min": t_tk_sorted[0] * 1e3,
+            "topk_pair_estimates_per_s": pairs / tk_mean,
+            "topk_variant": "tensor cores (tcgen05)" if use_tc else "CUDA cores (POPC)",
+            "popc_variant_topk_ms": t_popc * 1e3 if t_popc else None,
             "wall_s_timed_region": wall},
         "e2e": {"value": e2e_value, "unit": "pair-estimates/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -336,6 +365,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-popc-compare", action="store_true",
+                    help="skip the one-off CUDA-core variant launch reported for comparison")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"],
                     help="rows of the corpus (smaller only for profiling captures)")
     args = ap.parse_args()

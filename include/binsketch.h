@@ -119,8 +119,10 @@ bs_status bs_estimate_pairs(const uint32_t *A, const uint32_t *pcA, uint32_t nA,
                             uint32_t measures, float *out, uint32_t *counts, bs_stream_t stream);
 
 /*
- * bs_topk_workspace_bytes -- device workspace bs_topk needs for this shape
- * (0 when the problem runs without a cross-block merge).
+ * bs_topk_workspace_bytes -- device workspace bs_topk / bs_topk_ex need for
+ * this shape, whichever kernel runs: per-split candidate lists when the
+ * database is split across blocks, and for the tensor-core kernel a
+ * k-chunk-tiled copy of Q and DB (N/8 bytes per row, rows rounded up to 128).
  */
 size_t bs_topk_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k);
 
@@ -128,7 +130,9 @@ size_t bs_topk_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k
  * bs_topk -- ranking (Experiment 2, Sec. 4) as a top-k: for every query row
  * q, the k DB rows with the best estimate `by` (one of BS_IP, BS_JS, BS_COS:
  * largest first; BS_HAM: smallest first), ties broken by smaller DB index.
- * The count/estimate matrix is never materialised.
+ * The count/estimate matrix is never materialised.  The pair counts run on
+ * the tensor cores where bs_topk_ex's BS_VARIANT_TC applies, else on the
+ * CUDA cores (BS_VARIANT_POPC).
  *
  *  Q, pcQ       uint32[nQ][N/32] query sketches and their |a_s|
  *  DB, pcDB     uint32[nDB][N/32] database sketches and their |b_s|
@@ -139,13 +143,35 @@ size_t bs_topk_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k
  *               unused slots (nDB < k) hold -inf (+inf for BS_HAM)
  *  idx          uint32[nQ][k] DB row of each slot; 0xFFFFFFFF when unused
  *  workspace    device memory of at least bs_topk_workspace_bytes(...)
- *               bytes (may be NULL when that is 0); contents are scratch
+ *               bytes, 256-byte aligned (may be NULL when that is 0);
+ *               contents are scratch
  * Errors: BS_ERR_NO_MEMORY when workspace_bytes is too small.
  */
 bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
                   const uint32_t *DB, const uint32_t *pcDB, uint32_t nDB, uint32_t N,
                   uint32_t by, uint32_t k, int exclude_self, float *score, uint32_t *idx,
                   void *workspace, size_t workspace_bytes, bs_stream_t stream);
+
+/*
+ * bs_topk_ex -- bs_topk with an explicit choice of the pair-counting kernel.
+ * The ranking and the results are the same; only the way <a_s, b_s> is
+ * computed differs:
+ *   BS_VARIANT_POPC  AND + population count on 32-bit words (CUDA cores),
+ *                    any N and k;
+ *   BS_VARIANT_TC    0/1 bits widened to FP8 and multiplied on the tensor
+ *                    cores (tcgen05.mma, exact FP32 accumulation), for
+ *                    N % 128 == 0, 256 <= N <= 8192, k <= 100 and 16-byte
+ *                    aligned Q and DB; BS_ERR_UNSUPPORTED otherwise;
+ *   BS_VARIANT_AUTO  the tensor-core kernel where it applies, else POPC
+ *                    (this is what bs_topk does).
+ * bs_topk_workspace_bytes() covers every variant.
+ */
+enum { BS_VARIANT_AUTO = 0, BS_VARIANT_POPC = 1, BS_VARIANT_TC = 2 };
+bs_status bs_topk_ex(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
+                     const uint32_t *DB, const uint32_t *pcDB, uint32_t nDB, uint32_t N,
+                     uint32_t by, uint32_t k, int exclude_self, float *score, uint32_t *idx,
+                     void *workspace, size_t workspace_bytes, uint32_t variant,
+                     bs_stream_t stream);
 
 /*
  * bs_topk_noalloc -- bs_topk for callers that may not allocate GPU memory

@@ -40,13 +40,13 @@ def estimate_pairs(A, pcA, Bm, pcB, N: int, measures=("ip", "ham", "js", "cos"),
 
 
 def topk(Q, pcQ, DB, pcDB, N: int, k: int, by: str = "js", exclude_self: bool = False,
-         stream=None, workspace=None):
+         stream=None, workspace=None, variant: str = "auto"):
     nQ, nDB = Q.shape[0], DB.shape[0]
     score = torch.empty((nQ, k), dtype=torch.float32, device=Q.device)
     idx = torch.empty((nQ, k), dtype=torch.int32, device=Q.device)
     wsb = B.bs_topk_workspace_bytes(nQ, nDB, N, k)
     if wsb and (workspace is None or workspace.numel() < wsb):
         workspace = torch.empty((wsb,), dtype=torch.uint8, device=Q.device)
-    B.bs_topk(Q, pcQ, nQ, DB, pcDB, nDB, N, B.MEASURE_BITS[by], k, exclude_self, score, idx,
-              workspace if wsb else None, wsb, stream)
+    B.bs_topk_ex(Q, pcQ, nQ, DB, pcDB, nDB, N, B.MEASURE_BITS[by], k, exclude_self, score, idx,
+                 workspace if wsb else None, wsb, B.VARIANTS[variant], stream)
     return score, idx

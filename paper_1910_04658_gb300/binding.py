@@ -15,6 +15,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "_build", "libbinsketch.so")
 
 BS_IP, BS_HAM, BS_JS, BS_COS = 1, 2, 4, 8
+BS_VARIANT_AUTO, BS_VARIANT_POPC, BS_VARIANT_TC = 0, 1, 2
+VARIANTS = {"auto": 0, "popc": 1, "tc": 2}
 MEASURE_BITS = {"ip": BS_IP, "ham": BS_HAM, "js": BS_JS, "cos": BS_COS}
 BS_TOPK_K_MAX = 128
 BS_TOPK_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -35,6 +37,8 @@ SIGNATURES = [
     ("bs_topk_workspace_bytes", _sz, [_u32, _u32, _u32, _u32]),
     ("bs_topk", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, _i32, _vp, _vp, _vp,
                        _sz, _vp]),
+    ("bs_topk_ex", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, _i32, _vp, _vp, _vp,
+                          _sz, _u32, _vp]),
     ("bs_topk_noalloc", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, _i32, _vp, _vp,
                                _vp]),
     ("bs_get_async_error", _i32, [_vp]),
@@ -114,6 +118,13 @@ def bs_topk(Q, pcQ, nQ, DB, pcDB, nDB, N, by, k, exclude_self, score, idx, works
             workspace_bytes=0, stream=None):
     _check(lib().bs_topk(_p(Q), _p(pcQ), nQ, _p(DB), _p(pcDB), nDB, N, by, k, int(exclude_self),
                          _p(score), _p(idx), _p(workspace), workspace_bytes, _s(stream)), "bs_topk")
+
+
+def bs_topk_ex(Q, pcQ, nQ, DB, pcDB, nDB, N, by, k, exclude_self, score, idx, workspace=None,
+               workspace_bytes=0, variant=0, stream=None):
+    _check(lib().bs_topk_ex(_p(Q), _p(pcQ), nQ, _p(DB), _p(pcDB), nDB, N, by, k, int(exclude_self),
+                            _p(score), _p(idx), _p(workspace), workspace_bytes, variant,
+                            _s(stream)), "bs_topk_ex")
 
 
 def bs_topk_noalloc(Q, pcQ, nQ, DB, pcDB, nDB, N, by, k, exclude_self, score, idx, stream=None):

@@ -82,14 +82,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: gives up after `limit_ns` of wall time and returns false.
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
+// Bounded wait: returns false after ~4e9 SM cycles (about 2 s at full clock;
+// longer at lower clocks) without the phase completing.  The cycle counter is
+// read only after a burst of polls, so the common short wait costs nothing
+// beyond the polls themselves.
+constexpr long long kWaitLimitCycles = 4000000000ll;
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = globaltimer_ns();
-    for (uint32_t it = 1;; ++it) {
+#pragma unroll 1
+    for (int i = 0; i < 32; ++i)
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) return false;
+    const long long t0 = clock64();
+    for (;;) {
+#pragma unroll 1
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > kWaitLimitCycles) return false;
     }
 }
 
@@ -118,17 +125,20 @@ __device__ __forceinline__ void named_sync(uint32_t id, uint32_t nthreads) {
 //   Ham * L = ln(U^2 / (A B))            (Ham = n_a + n_b - 2 IP)
 //        JS = ln(A B / (N U)) / ln(U / N) (IP / (IP + Ham) = IP / n_u)
 //       Cos = -ln(A B / (N U)) / sqrt(ln(A/N) ln(B/N))
-// Every logarithm is of a ratio p/q of exact integers, taken as
-// log1p((p - q)/q) when p is near q, so the FP32 result keeps ~1e-7 relative
-// accuracy even where the estimate itself is close to 0.
+// Every logarithm is of a ratio p/q of exact positive integers, taken as
+// +log1p((p - q)/q) for p >= q and -log1p((q - p)/p) for p < q: the argument
+// of log1p is never negative, so its condition number stays below 1 and the
+// FP32 result keeps ~1e-7 relative accuracy even where the estimate itself is
+// close to 0 -- with one log1p and no branch.
 // Saturation: a, b and the union a + b - c are capped at N - 1, so A, B, U >= 1.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ float ln_ratio(long long p, long long q) {
     const long long diff = p - q;
     const long long ad = diff < 0 ? -diff : diff;
-    if (2 * ad <= q) return log1pf((float)diff / (float)q);
-    return logf((float)p / (float)q);
+    const long long den = diff < 0 ? p : q;
+    const float r = log1pf((float)ad / (float)den);
+    return diff < 0 ? -r : r;
 }
 
 struct Clamped {
@@ -177,5 +187,45 @@ __device__ __forceinline__ float estimate_one(uint32_t a, uint32_t b, uint32_t c
         return -ln_ratio(k.A * k.B, (long long)N * k.U) * rsqrtf(p);
     }
 }
+
+// better(a, b): (key a, index a) ranks strictly before (key b, index b) --
+// larger key first, then smaller index
+__device__ __forceinline__ bool better(float ka, uint32_t ia, float kb, uint32_t ib) {
+    return ka > kb || (ka == kb && ia < ib);
+}
+
+// ranking key of a measure: the estimate, negated for Ham (smaller is better)
+template <int M>
+__device__ __forceinline__ float rank_key(uint32_t a, uint32_t b, uint32_t c, uint32_t N, float lnA,
+                                          float lnB, float invL) {
+    const float v = estimate_one<M>(a, b, c, N, lnA, lnB, invL);
+    return M == M_HAM ? -v : v;
+}
+
+// ---- host: top-k variants (bs_pairs.cu, bs_pairs_tc.cu) ----------------------
+enum { VARIANT_AUTO = 0, VARIANT_POPC = 1, VARIANT_TC = 2 };
+
+// POPC variant (bs_pairs.cu)
+uint32_t popc_splits(uint32_t nQ, uint32_t nDB);
+bs_status topk_popc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
+                    const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
+                    int exclude_self, float *score, uint32_t *idx, float *ws_key, uint32_t *ws_idx,
+                    uint32_t splits, unsigned int *err, cudaStream_t stream);
+// merge per-split lists ws_key/ws_idx [splits][nQ][k] into score/idx
+bs_status launch_merge(int measure, const float *ws_key, const uint32_t *ws_idx, uint32_t nQ,
+                       uint32_t k, uint32_t splits, float *score, uint32_t *idx, cudaStream_t stream);
+
+// tensor-core variant (bs_pairs_tc.cu)
+bool tc_supported(const uint32_t *Q, const uint32_t *DB, uint32_t N, uint32_t k);
+uint32_t tc_splits(uint32_t nQ, uint32_t nDB);
+// bytes of the k-chunk-tiled copy of an n-row sketch matrix
+size_t tc_tiled_bytes(uint32_t n, uint32_t N);
+// tiled: scratch for the tiled copies, tc_tiled_bytes(nQ) + tc_tiled_bytes(nDB)
+// bytes (only the first part is used when Q and DB are the same matrix)
+bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
+                  const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
+                  int exclude_self, float *score, uint32_t *idx, float *ws_key, uint32_t *ws_idx,
+                  uint32_t splits, void *tiled, unsigned int *err, cudaStream_t stream);
+bool tc_shape_ok(uint32_t N, uint32_t k);
 
 }  // namespace bs

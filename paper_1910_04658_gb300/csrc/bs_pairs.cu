@@ -66,11 +66,6 @@ struct __align__(8) PairSmemHdr {
     int abort_flag;
 };
 
-// better(a, b): a ranks strictly before b -- larger key, then smaller index
-__device__ __forceinline__ bool better(float ka, uint32_t ia, float kb, uint32_t ib) {
-    return ka > kb || (ka == kb && ia < ib);
-}
-
 // Bitonic sort (best first) of n = power of two entries by one warp.
 __device__ void warp_sort_best_first(float *key, uint32_t *ix, int n, int lane) {
     for (int size = 2; size <= n; size <<= 1) {
@@ -107,13 +102,6 @@ __device__ int shrink_row(float *key, uint32_t *ix, int cnt, int k, int lane) {
 // word (4-word group q of row r) inside a 128-byte-swizzled tile of 32-word rows
 __device__ __forceinline__ const uint4 *swz(const uint32_t *tile, int r, int q) {
     return reinterpret_cast<const uint4 *>(tile + r * KC + (((q ^ (r & 7)) << 2)));
-}
-
-template <int M>
-__device__ __forceinline__ float rank_key(uint32_t a, uint32_t b, uint32_t c, uint32_t N, float lnA,
-                                          float lnB, float invL) {
-    const float v = estimate_one<M>(a, b, c, N, lnA, lnB, invL);
-    return M == M_HAM ? -v : v;
 }
 
 // Producer (LDG path, any N multiple of 32): one warp copies a tile with plain
@@ -490,8 +478,8 @@ static bool valid_N(uint32_t N) { return N >= 32 && N <= BS_N_MAX && (N % 32) ==
 
 static float inv_ln_n(uint32_t N) { return (float)(1.0 / log1p(-1.0 / (double)N)); }
 
-// database splits for a top-k problem on this device
-static uint32_t topk_splits(uint32_t nQ, uint32_t nDB) {
+// database splits of the POPC top-k on this device
+uint32_t popc_splits(uint32_t nQ, uint32_t nDB) {
     const uint32_t row_blocks = (nQ + BM - 1) / BM;
     const uint32_t tiles = (nDB + BN - 1) / BN;
     if (row_blocks == 0 || tiles == 0) return 1;
@@ -504,6 +492,57 @@ static uint32_t topk_splits(uint32_t nQ, uint32_t nDB) {
     // make the split count match the per-split tile count exactly
     const uint32_t per = (tiles + s - 1) / s;
     return (tiles + per - 1) / per;
+}
+
+bs_status launch_merge(int measure, const float *ws_key, const uint32_t *ws_idx, uint32_t nQ,
+                       uint32_t k, uint32_t splits, float *score, uint32_t *idx, cudaStream_t st) {
+    const uint32_t blocks = (nQ + 7) / 8;
+    switch (measure) {
+        case M_IP: merge_topk_kernel<M_IP><<<blocks, 256, 0, st>>>(ws_key, ws_idx, nQ, k, splits, score, idx); break;
+        case M_HAM: merge_topk_kernel<M_HAM><<<blocks, 256, 0, st>>>(ws_key, ws_idx, nQ, k, splits, score, idx); break;
+        case M_JS: merge_topk_kernel<M_JS><<<blocks, 256, 0, st>>>(ws_key, ws_idx, nQ, k, splits, score, idx); break;
+        default: merge_topk_kernel<M_COS><<<blocks, 256, 0, st>>>(ws_key, ws_idx, nQ, k, splits, score, idx); break;
+    }
+    return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+}
+
+bs_status topk_popc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
+                    const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
+                    int exclude_self, float *score, uint32_t *idx, float *ws_key, uint32_t *ws_idx,
+                    uint32_t splits, unsigned int *err, cudaStream_t st) {
+    PairArgs p = {};
+    p.Q = Q; p.DB = DB; p.pcQ = pcQ; p.pcDB = pcDB;
+    p.nQ = nQ; p.nDB = nDB; p.N = N; p.W = N / 32; p.nK = (p.W + KC - 1) / KC;
+    p.invL = inv_ln_n(N);
+    p.k = k; p.exclude_self = exclude_self; p.err = err;
+    p.score = score; p.idx = idx;
+    const uint32_t tiles = (nDB + BN - 1) / BN;
+    p.splits = splits;
+    p.tiles_per_split = splits ? (tiles + splits - 1) / splits : 0;
+    p.ws_key = ws_key;
+    p.ws_idx = ws_idx;
+    dim3 grid((nQ + BM - 1) / BM, splits);
+    if (grid.y > 65535) return BS_ERR_UNSUPPORTED;
+    switch (measure) {
+        case M_IP: return launch_pairs<MODE_TOPK, M_IP>(p, grid, st);
+        case M_HAM: return launch_pairs<MODE_TOPK, M_HAM>(p, grid, st);
+        case M_JS: return launch_pairs<MODE_TOPK, M_JS>(p, grid, st);
+        default: return launch_pairs<MODE_TOPK, M_COS>(p, grid, st);
+    }
+}
+
+static int measure_code(uint32_t by) {
+    switch (by) {
+        case BS_IP: return M_IP;
+        case BS_HAM: return M_HAM;
+        case BS_JS: return M_JS;
+        case BS_COS: return M_COS;
+    }
+    return -1;
+}
+
+static size_t ws_bytes(uint32_t splits, uint32_t nQ, uint32_t k) {
+    return splits <= 1 ? 0 : (size_t)splits * nQ * k * (sizeof(float) + sizeof(uint32_t));
 }
 
 }  // namespace bs
@@ -533,21 +572,34 @@ bs_status bs_estimate_pairs(const uint32_t *A, const uint32_t *pcA, uint32_t nA,
     return launch_pairs<MODE_ESTIMATE, 0>(p, grid, (cudaStream_t)stream);
 }
 
-size_t bs_topk_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k) {
-    (void)N;
-    if (nQ == 0 || nDB == 0 || k == 0) return 0;
-    const uint32_t s = topk_splits(nQ, nDB);
-    if (s <= 1) return 0;
-    return (size_t)s * nQ * k * (sizeof(float) + sizeof(uint32_t));
+// Workspace of one top-k call: the per-split lists (when the database is split
+// across blocks) and, for the tensor-core kernel, the k-chunk-tiled copies of
+// both operands; each part starts on a 256-byte boundary.
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static size_t tc_workspace(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, uint32_t splits) {
+    return align256(ws_bytes(splits, nQ, k)) + align256(tc_tiled_bytes(nQ, N)) +
+           align256(tc_tiled_bytes(nDB, N));
 }
 
-bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
-                  const uint32_t *pcDB, uint32_t nDB, uint32_t N, uint32_t by, uint32_t k,
-                  int exclude_self, float *score, uint32_t *idx, void *workspace,
-                  size_t workspace_bytes, bs_stream_t stream) {
+size_t bs_topk_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k) {
+    if (nQ == 0 || nDB == 0 || k == 0) return 0;
+    size_t need = ws_bytes(popc_splits(nQ, nDB), nQ, k);
+    if (valid_N(N) && tc_shape_ok(N, k)) {
+        const size_t t = tc_workspace(nQ, nDB, N, k, tc_splits(nQ, nDB));
+        if (t > need) need = t;
+    }
+    return need;
+}
+
+bs_status bs_topk_ex(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
+                     const uint32_t *pcDB, uint32_t nDB, uint32_t N, uint32_t by, uint32_t k,
+                     int exclude_self, float *score, uint32_t *idx, void *workspace,
+                     size_t workspace_bytes, uint32_t variant, bs_stream_t stream) {
     if (!valid_N(N)) return BS_ERR_INVALID_ARG;
     if (k == 0 || k > BS_TOPK_K_MAX) return BS_ERR_INVALID_ARG;
-    if (by != BS_IP && by != BS_HAM && by != BS_JS && by != BS_COS) return BS_ERR_INVALID_ARG;
+    const int m = measure_code(by);
+    if (m < 0 || variant > BS_VARIANT_TC) return BS_ERR_INVALID_ARG;
     if (nQ == 0) return BS_OK;
     if (!Q || !pcQ || !score || !idx) return BS_ERR_INVALID_ARG;
     if (nDB > 0 && (!DB || !pcDB)) return BS_ERR_INVALID_ARG;
@@ -556,41 +608,42 @@ bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uin
     if (!err) return BS_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
 
-    PairArgs p = {};
-    p.Q = Q; p.DB = DB; p.pcQ = pcQ; p.pcDB = pcDB;
-    p.nQ = nQ; p.nDB = nDB; p.N = N; p.W = N / 32; p.nK = (p.W + KC - 1) / KC;
-    p.invL = inv_ln_n(N);
-    p.k = k; p.exclude_self = exclude_self; p.err = err;
-    p.score = score; p.idx = idx;
-    const uint32_t tiles = (nDB + BN - 1) / BN;
-    const uint32_t splits = topk_splits(nQ, nDB);
-    p.splits = splits;
-    p.tiles_per_split = splits ? (tiles + splits - 1) / splits : 0;
-    if (splits > 1) {
-        const size_t need = (size_t)splits * nQ * k * (sizeof(float) + sizeof(uint32_t));
+    bool use_tc = false;
+    if (variant == BS_VARIANT_TC) {
+        if (nDB == 0 || !tc_supported(Q, DB, N, k)) return BS_ERR_UNSUPPORTED;
+        use_tc = true;
+    } else if (variant == BS_VARIANT_AUTO) {
+        use_tc = nDB > 0 && tc_supported(Q, DB, N, k);
+    }
+    const uint32_t splits = use_tc ? tc_splits(nQ, nDB) : popc_splits(nQ, nDB);
+    const size_t need = use_tc ? tc_workspace(nQ, nDB, N, k, splits) : ws_bytes(splits, nQ, k);
+    float *ws_key = nullptr;
+    uint32_t *ws_idx = nullptr;
+    void *tiled = nullptr;
+    if (need > 0) {
         if (!workspace || workspace_bytes < need) return BS_ERR_NO_MEMORY;
-        if ((reinterpret_cast<uintptr_t>(workspace) & 15u) != 0) return BS_ERR_INVALID_ARG;
-        p.ws_key = reinterpret_cast<float *>(workspace);
-        p.ws_idx = reinterpret_cast<uint32_t *>(p.ws_key + (size_t)splits * nQ * k);
+        if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return BS_ERR_INVALID_ARG;
+        uint8_t *w = reinterpret_cast<uint8_t *>(workspace);
+        if (splits > 1) {
+            ws_key = reinterpret_cast<float *>(w);
+            ws_idx = reinterpret_cast<uint32_t *>(ws_key + (size_t)splits * nQ * k);
+        }
+        tiled = w + align256(ws_bytes(splits, nQ, k));
     }
-    dim3 grid((nQ + BM - 1) / BM, splits);
-    if (grid.y > 65535) return BS_ERR_UNSUPPORTED;
-    bs_status st1;
-    switch (by) {
-        case BS_IP: st1 = launch_pairs<MODE_TOPK, M_IP>(p, grid, st); break;
-        case BS_HAM: st1 = launch_pairs<MODE_TOPK, M_HAM>(p, grid, st); break;
-        case BS_JS: st1 = launch_pairs<MODE_TOPK, M_JS>(p, grid, st); break;
-        default: st1 = launch_pairs<MODE_TOPK, M_COS>(p, grid, st); break;
-    }
-    if (st1 != BS_OK || splits <= 1) return st1;
-    const uint32_t blocks = (nQ + 7) / 8;
-    switch (by) {
-        case BS_IP: merge_topk_kernel<M_IP><<<blocks, 256, 0, st>>>(p.ws_key, p.ws_idx, nQ, k, splits, score, idx); break;
-        case BS_HAM: merge_topk_kernel<M_HAM><<<blocks, 256, 0, st>>>(p.ws_key, p.ws_idx, nQ, k, splits, score, idx); break;
-        case BS_JS: merge_topk_kernel<M_JS><<<blocks, 256, 0, st>>>(p.ws_key, p.ws_idx, nQ, k, splits, score, idx); break;
-        default: merge_topk_kernel<M_COS><<<blocks, 256, 0, st>>>(p.ws_key, p.ws_idx, nQ, k, splits, score, idx); break;
-    }
-    return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+    bs_status s1 = use_tc ? topk_tc(Q, pcQ, nQ, DB, pcDB, nDB, N, m, k, exclude_self, score, idx,
+                                    ws_key, ws_idx, splits, tiled, err, st)
+                          : topk_popc(Q, pcQ, nQ, DB, pcDB, nDB, N, m, k, exclude_self, score, idx,
+                                      ws_key, ws_idx, splits, err, st);
+    if (s1 != BS_OK || splits <= 1) return s1;
+    return launch_merge(m, ws_key, ws_idx, nQ, k, splits, score, idx, st);
+}
+
+bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
+                  const uint32_t *pcDB, uint32_t nDB, uint32_t N, uint32_t by, uint32_t k,
+                  int exclude_self, float *score, uint32_t *idx, void *workspace,
+                  size_t workspace_bytes, bs_stream_t stream) {
+    return bs_topk_ex(Q, pcQ, nQ, DB, pcDB, nDB, N, by, k, exclude_self, score, idx, workspace,
+                      workspace_bytes, BS_VARIANT_AUTO, stream);
 }
 
 }  // extern "C"

@@ -1,0 +1,708 @@
+// Pair counting on the 5th-generation tensor cores, fused with the estimates
+// and the per-query top-k (Alg. 1 step 2, Alg. 1-4, Experiment 2 as top-k).
+//
+// The common-bit count <a_s, b_s> is a dot product of two 0/1 vectors, i.e.
+// one entry of the product Q * DB^T of the 0/1 sketch matrices.  Packed bits
+// cannot feed tcgen05.mma directly (kind::i8 is not available on sm_103a), so
+// every bit is widened to one FP8 (E4M3) element in shared memory: a set bit
+// becomes 0x08 = 2^-6 (a single set bit, so 4 elements cost two integer
+// instructions), a clear bit 0.  Each product is 2^-12 and every partial sum is
+// a multiple of 2^-12 not above N * 2^-12 <= 2, which FP32 holds exactly, so
+// the TMEM accumulator times 4096 is the exact integer count.  The widening
+// permutes the order of the K elements (word j of the output holds bits
+// j, j+8, j+16, j+24), identically for both operands, which a dot product
+// does not see.
+//
+// Block (288 threads, one per SM; work item = 128 query rows x a range of
+// 256-row database tiles):
+//   warp 0     TMEM owner (512 columns) and single-thread MMA issuer:
+//              4 x tcgen05.mma.kind::f8f6f4 (M=128, N=256, K=32) per 128-bit
+//              k-chunk, into one of two TMEM accumulators
+//   warps 1-4  fetch the packed bits of three rows each and widen them into
+//              the 128-byte-swizzled K-major FP8 layout the MMA descriptors
+//              point at (a 3-deep operand ring when the heap leaves room, else
+//              2).  The fetches read a k-chunk-tiled copy of the sketches
+//              (128 rows x 16 bytes contiguous per k-chunk, made by
+//              tile_kchunks_kernel), so a warp's load is 512 contiguous bytes;
+//              four k-chunks are in flight per thread.
+//   warps 5-8  epilogue: one query row per thread, 32 TMEM columns per
+//              tcgen05.ld; a closed-form bound on the union count admits only
+//              pairs that can beat the row's current k-th best, whose exact
+//              FP32 estimate then enters a per-row heap in shared memory
+// All waits are bounded (mbarrier try_wait with a wall-clock budget); a
+// timeout raises BS_ERR_TIMEOUT and the block drains instead of hanging.
+#include <math.h>
+
+#include "bs_internal.cuh"
+
+namespace bs {
+namespace tc {
+
+constexpr int BM = 128;                    // query rows per block (UMMA M, TMEM lanes)
+constexpr int BN = 256;                    // database rows per tile (UMMA N)
+constexpr int KCW = 4;                     // packed words per k-chunk (128 bits)
+constexpr int THREADS = 288;
+constexpr int OP_A = BM * 128;             // 16 KB of FP8
+constexpr int OP_B = BN * 128;             // 32 KB of FP8
+constexpr int OP_BYTES = OP_A + OP_B;      // 48 KB per operand slot (one k-chunk)
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t NO_IDX = 0xFFFFFFFFu;
+// Admit when U' >= bound * (1 - 2^-13).  U' is an exact integer and the bound
+// carries ~1e-6 relative FP32 error (ex2.approx, the row constants, the key it
+// was derived from), so 1.2e-4 keeps every pair whose FP32 key beats the
+// threshold (checked against emulated FP32 keys one ulp above it) while
+// letting through almost none that fall a full count short.
+constexpr float FILTER_SLACK = 0.99987793f;
+
+// Shared-memory layout for NOP operand slots (offsets from the 1024-aligned base).
+template <int NOP>
+struct Smem {
+    static constexpr int op = 0;
+    static constexpr int col = op + NOP * OP_BYTES;             // 2 x 2 x 256 floats
+    static constexpr int bars = col + 2 * 2 * BN * 4;
+    static constexpr int heap = bars + 256;
+    static_assert((2 * NOP + 4) * 8 + 8 <= 256, "barrier area");
+};
+static_assert(OP_BYTES % 1024 == 0 && OP_A % 1024 == 0, "alignment");
+
+struct Args {
+    const uint4 *Q, *DB;        // k-chunk-tiled sketches [ceil(n/128)][nKc][128] x 16 bytes
+    const uint32_t *pcQ, *pcDB;
+    uint32_t nQ, nDB, N, W, nKc, nSl;
+    uint32_t k, tiles_per_split, splits;
+    int exclude_self;
+    float invL;        // 1 / ln(1 - 1/N)
+    float log2N, lnN;
+    float *score;      // splits == 1
+    uint32_t *idx;
+    float *ws_key;     // splits > 1: [splits][nQ][k]
+    uint32_t *ws_idx;
+    unsigned int *err;
+};
+
+// ---- tcgen05 wrappers -------------------------------------------------------
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 consecutive TMEM columns of this thread's lane; completes at tmem_wait()
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), leading offset unused for this layout (1).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;                 // LBO (ignored for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;       // SBO
+    d |= (uint64_t)1 << 46;                 // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor: D = F32, A = B = E4M3, both K-major, N = 256, M = 128.
+constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+// Widen 4 packed words (128 bits) of one row into 128 FP8 bytes, i.e. 8
+// 16-byte chunks: chunk 2p holds bits {8b + j} of word p for j = 0..3 and
+// chunk 2p+1 those for j = 4..7 (byte b of output word j).
+__device__ __forceinline__ void widen_regs(uint4 w, uint4 (&o)[8]) {
+    const uint32_t x[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const uint32_t v = x[p];
+        o[2 * p].x = (v << 3) & 0x08080808u;
+        o[2 * p].y = (v << 2) & 0x08080808u;
+        o[2 * p].z = (v << 1) & 0x08080808u;
+        o[2 * p].w = v & 0x08080808u;
+        o[2 * p + 1].x = (v >> 1) & 0x08080808u;
+        o[2 * p + 1].y = (v >> 2) & 0x08080808u;
+        o[2 * p + 1].z = (v >> 3) & 0x08080808u;
+        o[2 * p + 1].w = (v >> 4) & 0x08080808u;
+    }
+}
+
+// Store a widened row into the 128-byte-swizzled K-major tile: row r at
+// (r / 8) * 1024 + (r % 8) * 128, chunk c at position c ^ (r % 8).
+__device__ __forceinline__ void store_row(uint8_t *op_tile, int r, const uint4 (&o)[8]) {
+    uint8_t *row = op_tile + (r >> 3) * 1024 + (r & 7) * 128;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4 *>(row + ((c ^ (r & 7)) << 4)) = o[c];
+}
+
+// Re-layout of a packed sketch matrix [n][W] (W = 4 nKc words) into
+// k-chunk tiles: 16-byte chunk kc of row r goes to
+// dst[((r / 128) * nKc + kc) * 128 + r % 128]; rows past n are zero.  One
+// block moves 128 rows x 8 chunks through shared memory so that both the
+// reads (128-byte row pieces) and the writes (2 KB runs) are coalesced.
+__global__ void __launch_bounds__(256)
+    tile_kchunks_kernel(const uint4 *__restrict__ src, uint32_t n, uint32_t nKc,
+                        uint4 *__restrict__ dst) {
+    __shared__ uint4 buf[8][129];
+    const uint32_t blk = blockIdx.x;
+    const uint32_t kc0 = blockIdx.y * 8;
+    const int t = threadIdx.x;
+    // read: 8 consecutive threads take 8 consecutive chunks of one row
+    for (int i = t; i < 128 * 8; i += 256) {
+        const uint32_t r = i >> 3, c = i & 7;
+        const uint32_t row = blk * 128 + r, kc = kc0 + c;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (row < n && kc < nKc) v = src[(size_t)row * nKc + kc];
+        buf[c][r] = v;
+    }
+    __syncthreads();
+    // write: 128 consecutive threads cover one 2 KB run
+    for (int i = t; i < 128 * 8; i += 256) {
+        const uint32_t c = i >> 7, r = i & 127;
+        const uint32_t kc = kc0 + c;
+        if (kc < nKc) dst[((size_t)blk * nKc + kc) * 128 + r] = buf[c][r];
+    }
+}
+
+// ---- per-row heap of the k best (root = worst), interleaved across rows ------
+struct Heap {
+    float *key;      // key[i * BM + t]
+    uint32_t *ix;
+    int t, size, cap, levels;
+    __device__ float k_at(int i) const { return key[i * BM + t]; }
+    __device__ uint32_t i_at(int i) const { return ix[i * BM + t]; }
+    __device__ void put(int i, float kk, uint32_t ii) { key[i * BM + t] = kk; ix[i * BM + t] = ii; }
+    // append and sift up: parents that rank below the new entry move down
+    __device__ void push(float kk, uint32_t ii) {
+        int i = size++;
+        while (i > 0) {
+            const int p = (i - 1) >> 1;
+            const float pk = k_at(p);
+            const uint32_t pi = i_at(p);
+            if (!better(pk, pi, kk, ii)) break;
+            put(i, pk, pi);
+            i = p;
+        }
+        put(i, kk, ii);
+    }
+    // sift (kk, ii) down from slot i over the first n slots: the worse child
+    // moves up while the new entry ranks above it
+    __device__ void sift_down(int i, float kk, uint32_t ii, int n) {
+        for (;;) {
+            const int l = 2 * i + 1;
+            if (l >= n) break;
+            int m = l;
+            float mk = k_at(l);
+            uint32_t mi = i_at(l);
+            if (l + 1 < n) {
+                const float rk = k_at(l + 1);
+                const uint32_t ri = i_at(l + 1);
+                if (better(mk, mi, rk, ri)) { m = l + 1; mk = rk; mi = ri; }
+            }
+            if (!better(kk, ii, mk, mi)) break;
+            put(i, mk, mi);
+            i = m;
+        }
+        put(i, kk, ii);
+    }
+    __device__ void replace_root(float kk, uint32_t ii) { sift_down(0, kk, ii, size); }
+    // in-place heapsort: best first in slots [0, size)
+    __device__ void sort_best_first() {
+        for (int end = size - 1; end > 0; --end) {
+            const float rk = k_at(0);
+            const uint32_t ri = i_at(0);
+            const float ek = k_at(end);
+            const uint32_t ei = i_at(end);
+            put(end, rk, ri);
+            sift_down(0, ek, ei, end);
+        }
+    }
+};
+
+__host__ __device__ constexpr int heap_levels(int cap) {
+    int lv = 0;
+    while ((1 << lv) <= cap) ++lv;   // a heap of cap entries has lv levels
+    return lv;
+}
+
+// Per-row constants of the admission bound (see filter_bound).
+struct RowFilter {
+    float c0, c1;
+    bool all;       // heap not full (or bound not applicable): admit everything
+};
+
+// Bound on U' = N - min(a+b-c, N-1) that a pair must reach to beat key theta:
+//   JS : log2 U' >= (log2 A' + log2 B' + (theta-1) log2 N) / (1 + theta)   (theta > -1/2)
+//   COS: log2 U' >= (theta s_a s_b - s_a^2 - s_b^2) / ln 2 + log2 N,  s = sqrt(-ln(X'/N))
+//   IP : U' >= A' B' exp(-theta L) / N
+//   HAM: U' >= sqrt(A' B') exp(-theta L / 2)            (theta = -Ham)
+// Column values: JS f0 = log2 B'; COS f0 = s_b; IP f0 = B'; HAM f0 = sqrt(B').
+// Row value (row_const): JS log2 A'; COS s_a; IP A'/N; HAM sqrt(A').
+template <int M>
+__device__ __forceinline__ float row_const(float A, uint32_t N) {
+    if (M == M_JS) return log2f(A);
+    if (M == M_COS) return sqrtf(fmaxf(-logf(A / (float)N), 0.0f));
+    if (M == M_IP) return A / (float)N;
+    return sqrtf(A);
+}
+
+template <int M>
+__device__ __forceinline__ RowFilter make_filter(float theta, float rc, float invL, float log2N) {
+    RowFilter f;
+    f.all = false;
+    const float ln2 = 0.69314718056f;
+    if (M == M_JS) {
+        if (!(theta > -0.5f)) { f.all = true; f.c0 = f.c1 = 0.f; return f; }
+        const float e = 1.0f / (1.0f + theta);
+        f.c0 = e;
+        f.c1 = (rc + (theta - 1.0f) * log2N) * e;
+    } else if (M == M_COS) {
+        f.c0 = theta * rc / ln2;
+        f.c1 = log2N - rc * rc / ln2;
+    } else if (M == M_IP) {
+        // L < 0, invL = 1/L
+        f.c0 = rc * expf(-theta / invL);
+        f.c1 = 0.f;
+    } else {
+        f.c0 = rc * expf(-0.5f * theta / invL);
+        f.c1 = 0.f;
+    }
+    if (!isfinite(f.c0) || !isfinite(f.c1)) f.all = true;
+    return f;
+}
+
+// 2^x on the special-function unit (relative error ~2^-22, far inside the
+// 2^-8 slack of the bound)
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <int M>
+__device__ __forceinline__ bool admit(const RowFilter &f, float U, float f0) {
+    if (f.all) return true;
+    float bound;
+    if (M == M_JS) bound = ex2_approx(fmaf(f.c0, f0, f.c1));
+    else if (M == M_COS) bound = ex2_approx(fmaf(f0, f.c0 - f0 * 1.44269504089f, f.c1));
+    else bound = f.c0 * f0;
+    return U >= bound * FILTER_SLACK;
+}
+
+// Running state of one query row in the epilogue.
+struct RowState {
+    RowFilter filt;
+    float thr_k;       // key and index of the current k-th best (root of the heap)
+    uint32_t thr_i;
+    int size;          // entries in the heap
+};
+
+// A pair that passed the bound: exact FP32 key, then the heap.  Kept out of
+// line -- it runs for a small fraction of the pairs.
+template <int M>
+__device__ __noinline__ RowState consider(RowState st, float *hkey, uint32_t *hix, int t, uint32_t col,
+                                          uint32_t c, uint32_t b, uint32_t a, float lnA, float rc,
+                                          uint32_t N, float invL, float log2N, int cap) {
+    const float lnB = M == M_COS ? row_log(b, N) : 0.0f;
+    const float key = rank_key<M>(a, b, c, N, lnA, lnB, invL);
+    Heap h;
+    h.key = hkey; h.ix = hix; h.t = t; h.size = st.size; h.cap = cap; h.levels = heap_levels(cap);
+    if (h.size < h.cap) {
+        h.push(key, col);
+        st.size = h.size;
+        if (h.size == h.cap) {
+            st.thr_k = h.k_at(0); st.thr_i = h.i_at(0);
+            st.filt = make_filter<M>(st.thr_k, rc, invL, log2N);
+        }
+    } else if (better(key, col, st.thr_k, st.thr_i)) {
+        h.replace_root(key, col);
+        st.thr_k = h.k_at(0); st.thr_i = h.i_at(0);
+        st.filt = make_filter<M>(st.thr_k, rc, invL, log2N);
+    }
+    return st;
+}
+
+// v[j] for a per-lane index j, by a select tree over registers (no local memory)
+__device__ __forceinline__ uint32_t select32(const uint32_t (&v)[32], uint32_t j) {
+    uint32_t t16[16], t8[8], t4[4], t2[2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) t16[i] = (j & 16) ? v[i + 16] : v[i];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t8[i] = (j & 8) ? t16[i + 8] : t16[i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t4[i] = (j & 4) ? t8[i + 4] : t8[i];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) t2[i] = (j & 2) ? t4[i + 2] : t4[i];
+    return (j & 1) ? t2[1] : t2[0];
+}
+
+template <int M, int NOP>
+__global__ void __launch_bounds__(THREADS, 1)
+    pair_tc_kernel(const Args p) {
+    using Smem = tc::Smem<NOP>;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *op = base + Smem::op;
+    float *colv = reinterpret_cast<float *>(base + Smem::col);      // [2][2][BN]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + Smem::bars);
+    uint64_t *op_full = bars, *op_empty = bars + NOP;
+    uint64_t *acc_full = bars + 2 * NOP, *acc_empty = acc_full + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    float *heap_key = reinterpret_cast<float *>(base + Smem::heap);   // [k][BM]
+    uint32_t *heap_ix = reinterpret_cast<uint32_t *>(heap_key + (size_t)p.k * BM);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t row0 = blockIdx.x * BM;
+    const uint32_t n_tiles = (p.nDB + BN - 1) / BN;
+    uint32_t t_begin = blockIdx.y * p.tiles_per_split;
+    uint32_t t_end = min(n_tiles, t_begin + p.tiles_per_split);
+    if (t_begin > t_end) t_begin = t_end;
+    const uint32_t n_my_tiles = t_end - t_begin;
+
+    if (tid == 0) {
+        for (int i = 0; i < NOP; ++i) {
+            mbar_init(&op_full[i], 4);
+            mbar_init(&op_empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], 4);
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(tmem_slot, TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    auto wait = [&](uint64_t *bar, uint32_t parity) {
+        if (*abort_flag) return;
+        if (!mbar_wait(bar, parity)) {
+            raise_error(p.err, BS_ERR_TIMEOUT);
+            *abort_flag = 1;
+        }
+    };
+
+    if (warp == 0) {
+        // ----------------------------- MMA issuer -----------------------------
+        if (lane == 0) {
+            uint32_t kc = 0;
+            for (uint32_t t = 0; t < n_my_tiles; ++t) {
+                const uint32_t ab = t & 1;
+                if (t >= 2) wait(&acc_empty[ab], ((t >> 1) - 1) & 1);
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + ab * BN;
+                for (uint32_t c = 0; c < p.nKc; ++c, ++kc) {
+                    const uint32_t o = kc % NOP;
+                    wait(&op_full[o], (kc / NOP) & 1);
+                    tc_fence_after();
+                    if (!*abort_flag) {
+                        const uint32_t a_addr = smem_u32(op + o * OP_BYTES);
+                        const uint32_t b_addr = a_addr + OP_A;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            mma_f8(d_tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32),
+                                   IDESC, (c | kk) != 0);
+                    }
+                    mma_commit(&op_empty[o]);
+                }
+                mma_commit(&acc_full[ab]);
+            }
+        }
+    } else if (warp < 5) {
+        // ------------------------------ widening ------------------------------
+        // thread e owns query row e and database rows e and e + 128 of a tile
+        const int e = tid - 32;   // 0..127
+        const uint32_t nblk_db = (p.nDB + 127) / 128;
+        const uint4 z = make_uint4(0, 0, 0, 0);
+        const uint32_t total = n_my_tiles * p.nKc;
+        // k-chunk g of this block's sweep: three 16-byte pieces
+        auto fetch = [&](uint32_t g, uint4 &a_, uint4 &b0_, uint4 &b1_) {
+            if (g < total) {
+                const uint32_t t = g / p.nKc, kc = g % p.nKc;
+                const uint32_t bb = 2 * (t_begin + t);
+                a_ = __ldg(p.Q + ((size_t)blockIdx.x * p.nKc + kc) * 128 + e);
+                b0_ = bb < nblk_db ? __ldg(p.DB + ((size_t)bb * p.nKc + kc) * 128 + e) : z;
+                b1_ = bb + 1 < nblk_db ? __ldg(p.DB + ((size_t)(bb + 1) * p.nKc + kc) * 128 + e) : z;
+            }
+        };
+        // four k-chunks in flight; a fixed rotation keeps them in registers
+        uint4 ra[4], rb0[4], rb1[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) fetch(u, ra[u], rb0[u], rb1[u]);
+        for (uint32_t g0 = 0; g0 < total; g0 += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t kc = g0 + u;
+                if (kc >= total) break;
+                const uint32_t o = kc % NOP;
+                if (kc >= NOP) wait(&op_empty[o], ((kc / NOP) - 1) & 1);
+                uint8_t *oA = op + o * OP_BYTES;
+                uint8_t *oB = oA + OP_A;
+                uint4 w8[8];
+                widen_regs(ra[u], w8);
+                store_row(oA, e, w8);
+                widen_regs(rb0[u], w8);
+                store_row(oB, e, w8);
+                widen_regs(rb1[u], w8);
+                store_row(oB, e + 128, w8);
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&op_full[o]);
+                fetch(kc + 4, ra[u], rb0[u], rb1[u]);
+            }
+        }
+    } else {
+        // ------------------------------ epilogue ------------------------------
+        const int e = tid - 160;                   // 0..127
+        const int quarter = warp & 3;              // TMEM lanes this warp may access
+        const int r = quarter * 32 + lane;         // row within the block
+        const uint32_t q = row0 + r;
+        const bool row_ok = q < p.nQ;
+        const uint32_t a = row_ok ? __ldg(p.pcQ + q) : 0u;
+        const uint32_t a_cl = a < p.N - 1 ? a : p.N - 1;
+        const float rc = row_const<M>((float)(p.N - a_cl), p.N);   // from A' >= 1
+        const float lnA = row_log(a, p.N);
+        RowState st;
+        st.filt.all = true; st.filt.c0 = st.filt.c1 = 0.f;
+        st.thr_k = -INFINITY; st.thr_i = NO_IDX; st.size = 0;
+
+        for (uint32_t t = 0; t < n_my_tiles; ++t) {
+            const uint32_t tile = t_begin + t;
+            float *cv = colv + (t & 1) * 2 * BN;
+            // per-column values of this tile (two columns per thread)
+            for (int j = e; j < BN; j += 128) {
+                const uint32_t col = tile * BN + j;
+                const uint32_t b = col < p.nDB ? __ldg(p.pcDB + col) : 0u;
+                const uint32_t b_cl = b < p.N - 1 ? b : p.N - 1;
+                const float Bf = (float)(p.N - b_cl);
+                float f0;
+                if (M == M_JS) f0 = log2f(Bf);
+                else if (M == M_COS) f0 = sqrtf(fmaxf(-logf(Bf / (float)p.N), 0.0f));
+                else if (M == M_IP) f0 = Bf;
+                else f0 = sqrtf(Bf);
+                cv[j] = (float)b;         // raw count: U' is formed from the raw a, b, c
+                cv[BN + j] = f0;
+            }
+            named_sync(2, 128);
+            const uint32_t ab = t & 1;
+            wait(&acc_full[ab], (t >> 1) & 1);
+            tc_fence_after();
+            const float Na = (float)(p.N - a);      // N - a (raw)
+            const uint32_t col0 = tile * BN;
+            // every lane stays in the loops below (they vote); dead rows admit nothing
+            const bool live = row_ok && !*abort_flag;
+            auto score_chunk = [&](const uint32_t (&v)[32], int ch) {
+                // pass 1: which of these 32 pairs can beat the row's k-th best
+                uint32_t mask = 0;
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) {
+                    const int j = ch * 32 + jj;
+                    const float cf = __uint_as_float(v[jj]) * 4096.0f;   // exact count
+                    // U' = N - min(a + b - c, N - 1) = max(N - a - b + c, 1), exact in FP32
+                    const float U = fmaxf(Na - cv[j] + cf, 1.0f);
+                    if (admit<M>(st.filt, U, cv[BN + j])) mask |= 1u << jj;
+                }
+                // columns past the database end and the self pair never rank
+                const uint32_t col_c = col0 + ch * 32;
+                if (col_c + 32 > p.nDB)
+                    mask &= col_c >= p.nDB ? 0u : (0xFFFFFFFFu >> (32 - (p.nDB - col_c)));
+                if (p.exclude_self && q >= col_c && q < col_c + 32) mask &= ~(1u << (q - col_c));
+                if (!live) mask = 0;
+                // pass 2: exact keys for the admitted pairs; the warp loops only as
+                // often as its busiest row needs
+                while (__any_sync(0xffffffffu, mask != 0)) {
+                    if (mask) {
+                        const uint32_t jj = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        const uint32_t c = (uint32_t)(__uint_as_float(select32(v, jj)) * 4096.0f);
+                        const int j = ch * 32 + (int)jj;
+                        st = consider<M>(st, heap_key, heap_ix, r, col_c + jj, c, (uint32_t)cv[j], a,
+                                         lnA, rc, p.N, p.invL, p.log2N, (int)p.k);
+                    }
+                }
+            };
+            // TMEM loads double-buffered: chunk ch + 1 is in flight while ch is scored
+            const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + ab * BN;
+            uint32_t va[32], vb[32];
+            tmem_ld32_async(trow, va);
+            tmem_wait();
+#pragma unroll 1
+            for (int ch = 0; ch < BN / 32; ch += 2) {
+                tmem_ld32_async(trow + (ch + 1) * 32, vb);
+                score_chunk(va, ch);
+                tmem_wait();
+                if (ch + 2 < BN / 32) tmem_ld32_async(trow + (ch + 2) * 32, va);
+                score_chunk(vb, ch + 1);
+                tmem_wait();
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[ab]);
+        }
+        // write this row's list, best first
+        if (row_ok) {
+            Heap h;
+            h.key = heap_key; h.ix = heap_ix; h.t = r; h.size = st.size; h.cap = (int)p.k;
+            h.levels = heap_levels((int)p.k);
+            h.sort_best_first();
+            for (int s = 0; s < (int)p.k; ++s) {
+                const float kk = s < h.size ? h.k_at(s) : -INFINITY;
+                const uint32_t ii = s < h.size ? h.i_at(s) : NO_IDX;
+                if (p.splits == 1) {
+                    const size_t o = (size_t)q * p.k + s;
+                    p.score[o] = M == M_HAM ? -kk : kk;
+                    p.idx[o] = ii;
+                } else {
+                    const size_t o = ((size_t)blockIdx.y * p.nQ + q) * p.k + s;
+                    p.ws_key[o] = kk;
+                    p.ws_idx[o] = ii;
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+template <int NOP>
+static size_t tc_smem_bytes(uint32_t k) { return 1024 + tc::Smem<NOP>::heap + (size_t)k * tc::BM * 8; }
+constexpr size_t kSmemLimit = 232448;   // 227 KB per block
+
+bool tc_shape_ok(uint32_t N, uint32_t k) {
+    return (N % 128) == 0 && N >= 256 && N <= 8192 && k >= 1 && tc_smem_bytes<2>(k) <= kSmemLimit;
+}
+
+bool tc_supported(const uint32_t *Q, const uint32_t *DB, uint32_t N, uint32_t k) {
+    return tc_shape_ok(N, k) && (reinterpret_cast<uintptr_t>(Q) & 15u) == 0 &&
+           (reinterpret_cast<uintptr_t>(DB) & 15u) == 0;
+}
+
+// Database splits for the tensor-core top-k: the fewest (row block, split)
+// work items whose last wave of one-block-per-SM launches is at least 90%
+// full (else the best fill found), each split keeping at least 4 tiles.
+uint32_t tc_splits(uint32_t nQ, uint32_t nDB) {
+    const uint32_t rb = (nQ + tc::BM - 1) / tc::BM;
+    const uint32_t tiles = (nDB + tc::BN - 1) / tc::BN;
+    if (rb == 0 || tiles == 0) return 1;
+    const uint32_t sms = (uint32_t)sm_count();
+    const uint32_t s_max = tiles / 4 > 1 ? (tiles / 4 < 4096 ? tiles / 4 : 4096) : 1;
+    uint32_t best = 1;
+    double best_eff = -1.0;
+    for (uint32_t s = 1; s <= s_max; ++s) {
+        const uint32_t per = (tiles + s - 1) / s;
+        if ((tiles + per - 1) / per != s) continue;     // only exact split counts
+        const double waves = (double)rb * s / sms;
+        const double eff = waves / ceil(waves);
+        if (eff >= 0.9) return s;
+        if (eff > best_eff) { best_eff = eff; best = s; }
+    }
+    return best;
+}
+
+size_t tc_tiled_bytes(uint32_t n, uint32_t N) {
+    return (size_t)((n + 127) / 128) * 128 * (N / 8);
+}
+
+bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
+                  const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
+                  int exclude_self, float *score, uint32_t *idx, float *ws_key, uint32_t *ws_idx,
+                  uint32_t splits, void *tiled, unsigned int *err, cudaStream_t stream) {
+    const uint32_t W = N / 32;
+    const uint32_t nKc = W / tc::KCW;
+    // k-chunk-tiled copies of the operands (one copy when Q and DB coincide)
+    uint4 *tQ = reinterpret_cast<uint4 *>(tiled);
+    uint4 *tDB = tQ;
+    const bool same = (Q == DB && nQ == nDB);
+    {
+        dim3 g((nQ + 127) / 128, (nKc + 7) / 8);
+        tc::tile_kchunks_kernel<<<g, 256, 0, stream>>>(reinterpret_cast<const uint4 *>(Q), nQ, nKc, tQ);
+    }
+    if (!same) {
+        tDB = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(tiled) + tc_tiled_bytes(nQ, N));
+        dim3 g((nDB + 127) / 128, (nKc + 7) / 8);
+        tc::tile_kchunks_kernel<<<g, 256, 0, stream>>>(reinterpret_cast<const uint4 *>(DB), nDB, nKc, tDB);
+    }
+    if (cudaGetLastError() != cudaSuccess) return BS_ERR_CUDA;
+    tc::Args p = {};
+    p.Q = tQ; p.DB = tDB;
+    p.pcQ = pcQ; p.pcDB = pcDB; p.nQ = nQ; p.nDB = nDB; p.N = N; p.W = W;
+    p.nKc = nKc;
+    p.nSl = (nKc + 1) / 2;
+    p.k = k; p.exclude_self = exclude_self; p.splits = splits;
+    const uint32_t tiles = (nDB + tc::BN - 1) / tc::BN;
+    p.tiles_per_split = (tiles + splits - 1) / splits;
+    p.invL = (float)(1.0 / log1p(-1.0 / (double)N));
+    p.log2N = (float)log2((double)N);
+    p.lnN = (float)log((double)N);
+    p.score = score; p.idx = idx; p.ws_key = ws_key; p.ws_idx = ws_idx; p.err = err;
+    dim3 grid((nQ + tc::BM - 1) / tc::BM, splits);
+    // three operand slots when the heap leaves room, else two
+    const bool deep = tc_smem_bytes<3>(k) <= kSmemLimit;
+    const size_t smem = deep ? tc_smem_bytes<3>(k) : tc_smem_bytes<2>(k);
+    cudaError_t ce = cudaSuccess;
+    auto go = [&](auto kern) {
+        ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (ce == cudaSuccess) kern<<<grid, tc::THREADS, smem, stream>>>(p);
+    };
+    switch (measure) {
+        case M_IP: deep ? go(tc::pair_tc_kernel<M_IP, 3>) : go(tc::pair_tc_kernel<M_IP, 2>); break;
+        case M_HAM: deep ? go(tc::pair_tc_kernel<M_HAM, 3>) : go(tc::pair_tc_kernel<M_HAM, 2>); break;
+        case M_JS: deep ? go(tc::pair_tc_kernel<M_JS, 3>) : go(tc::pair_tc_kernel<M_JS, 2>); break;
+        default: deep ? go(tc::pair_tc_kernel<M_COS, 3>) : go(tc::pair_tc_kernel<M_COS, 2>); break;
+    }
+    if (ce != cudaSuccess) return BS_ERR_CUDA;
+    return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+}
+
+}  // namespace bs

@@ -170,29 +170,35 @@ def test_estimates_measure_subsets_and_counts_only(tiny):
 
 # ------------------------------------------------------------------------ top-k
 
+@pytest.mark.parametrize("variant", ["popc", "tc"])
 @pytest.mark.parametrize("by,m", [("js", 2), ("cos", 3), ("ip", 0), ("ham", 1)])
-@pytest.mark.parametrize("k", [1, 20, 50, 128])
-def test_topk_all_pairs_tiny(tiny, by, m, k):
+@pytest.mark.parametrize("k", [1, 20, 50, 100, 128])
+def test_topk_all_pairs_tiny(tiny, by, m, k, variant):
     N = 1024
+    if variant == "tc" and k > 100:
+        pytest.skip("tensor-core top-k keeps k <= 100 rows in shared memory")
     sk, pc = _gpu_sketch(tiny, N, 0)
-    score, idx = api.topk(sk, pc, sk, pc, N, k, by=by, exclude_self=True)
+    score, idx = api.topk(sk, pc, sk, pc, N, k, by=by, exclude_self=True, variant=variant)
     oest, _ = oracle.estimate_pairs(u32(sk), u32(sk), N)
     s, ix = score.cpu().numpy(), u32(idx)
     for q in range(tiny.n):
         check_topk_row(s[q], ix[q], oest[m, q], k, m, exclude_q=q)
 
 
-def test_topk_fewer_db_rows_than_k(tiny):
+@pytest.mark.parametrize("variant", ["popc", "tc"])
+def test_topk_fewer_db_rows_than_k(tiny, variant):
     N = 1024
     sk, pc = _gpu_sketch(tiny, N, 0)
-    score, idx = api.topk(sk[:40], pc[:40], sk[:30], pc[:30], N, 50, by="js")
+    score, idx = api.topk(sk[:40], pc[:40], sk[:30], pc[:30], N, 50, by="js", variant=variant)
     oest, _ = oracle.estimate_pairs(u32(sk[:40]), u32(sk[:30]), N)
     for q in range(40):
         check_topk_row(score[q].cpu().numpy(), u32(idx[q]), oest[2, q], 50, 2)
 
 
-@pytest.mark.parametrize("N,by,m", [(4096, "js", 2), (1024, "cos", 3), (256, "ham", 1)])
-def test_topk_split_database_merge(N, by, m):
+@pytest.mark.parametrize("variant", ["popc", "tc"])
+@pytest.mark.parametrize("N,by,m", [(4096, "js", 2), (1024, "cos", 3), (256, "ham", 1),
+                                    (8192, "ip", 0)])
+def test_topk_split_database_merge(N, by, m, variant):
     # few queries against a large database: the database is split across
     # blocks and the per-split lists are merged by a second kernel
     db = inputs.random_csr(11, 20_000, 1_000_000, 1, 400)
@@ -200,11 +206,41 @@ def test_topk_split_database_merge(N, by, m):
     dsk, dpc = _gpu_sketch(db, N, 2)
     qsk, qpc = _gpu_sketch(q, N, 2)
     assert B.bs_topk_workspace_bytes(37, 20_000, N, 100) > 0
-    score, idx = api.topk(qsk, qpc, dsk, dpc, N, 100, by=by)
+    score, idx = api.topk(qsk, qpc, dsk, dpc, N, 100, by=by, variant=variant)
     oest, _ = oracle.estimate_pairs(u32(qsk), u32(dsk), N)
     s, ix = score.cpu().numpy(), u32(idx)
     for r in range(37):
         check_topk_row(s[r], ix[r], oest[m, r], 100, m)
+
+
+@pytest.mark.parametrize("N,by,m", [(256, "ip", 0), (1024, "js", 2), (8192, "cos", 3)])
+def test_topk_tc_dense_and_saturated(N, by, m):
+    # counts up to N: the FP8 products must still sum exactly in FP32
+    c = inputs.uniform_csr(3, 300, 100_000, N // 4, 4 * N)
+    f = inputs.uniform_csr(4, 6, 100_000, 20 * N, 20 * N)
+    rp = np.concatenate([c.row_ptr, f.row_ptr[1:] + c.row_ptr[-1]]).astype(np.uint64)
+    c = inputs.CSR(rp, np.concatenate([c.col, f.col]), c.d)
+    sk, pc = _gpu_sketch(c, N, 8)
+    oest, _ = oracle.estimate_pairs(u32(sk), u32(sk), N)
+    for variant in ("tc", "popc"):
+        score, idx = api.topk(sk, pc, sk, pc, N, 30, by=by, exclude_self=True, variant=variant)
+        s, ix = score.cpu().numpy(), u32(idx)
+        for q in range(c.n):
+            check_topk_row(s[q], ix[q], oest[m, q], 30, m, exclude_q=q)
+
+
+def test_topk_tc_rejects_unsupported_shapes(tiny):
+    sk, pc = _gpu_sketch(tiny, 96, 0)
+    score = torch.empty((10, 5), dtype=torch.float32, device="cuda")
+    idx = torch.empty((10, 5), dtype=torch.int32, device="cuda")
+    with pytest.raises(B.BinSketchError) as e:     # N = 96: not a multiple of 128
+        B.bs_topk_ex(sk, pc, 10, sk, pc, 100, 96, B.BS_JS, 5, 0, score, idx, None, 0, B.BS_VARIANT_TC)
+    assert e.value.code == 7
+    # the automatic choice falls back to the CUDA-core kernel and still works
+    s2, i2 = api.topk(sk[:10], pc[:10], sk[:100], pc[:100], 96, 5, by="js")
+    oest, _ = oracle.estimate_pairs(u32(sk[:10]), u32(sk[:100]), 96)
+    for q in range(10):
+        check_topk_row(s2[q].cpu().numpy(), u32(i2[q]), oest[2, q], 5, 2)
 
 
 def test_topk_rejects_small_workspace():
@@ -212,13 +248,14 @@ def test_topk_rejects_small_workspace():
     db = inputs.random_csr(1, 5000, 100_000, 1, 100)
     dsk, dpc = _gpu_sketch(db, N, 0)
     need = B.bs_topk_workspace_bytes(3, 5000, N, 10)
-    assert need > 0
+    assert need > 16
     score = torch.empty((3, 10), dtype=torch.float32, device="cuda")
     idx = torch.empty((3, 10), dtype=torch.int32, device="cuda")
-    ws = torch.empty((need - 16,), dtype=torch.uint8, device="cuda")
-    with pytest.raises(B.BinSketchError) as e:
-        B.bs_topk(dsk, dpc, 3, dsk, dpc, 5000, N, B.BS_JS, 10, 0, score, idx, ws, need - 16)
-    assert e.value.code == 5
+    ws = torch.empty((16,), dtype=torch.uint8, device="cuda")
+    for variant in (B.BS_VARIANT_AUTO, B.BS_VARIANT_POPC, B.BS_VARIANT_TC):
+        with pytest.raises(B.BinSketchError) as e:
+            B.bs_topk_ex(dsk, dpc, 3, dsk, dpc, 5000, N, B.BS_JS, 10, 0, score, idx, ws, 16, variant)
+        assert e.value.code == 5
 
 
 # --------------------------------------------- full text-BoW workload (sampled)
@@ -243,6 +280,11 @@ def test_bow_scale_sketch_and_topk50_sampled(bow):
     score, idx = api.topk(sk, pc, sk, pc, N, k, by="js", exclude_self=True)
     assert B.bs_get_async_error() == 0
     s, ix = score.cpu().numpy(), u32(idx)
+    # both counting kernels feed identical integer counts to identical FP32
+    # arithmetic, so the two variants must agree exactly
+    s_p, i_p = api.topk(sk, pc, sk, pc, N, k, by="js", exclude_self=True, variant="popc")
+    assert np.array_equal(u32(i_p), ix)
+    assert np.array_equal(s_p.cpu().numpy(), s)
     q = rows[:24]
     oest, _ = oracle.estimate_pairs(got_sk[q], got_sk, N)
     for t, r in enumerate(q):
