@@ -13,8 +13,8 @@
 // j, j+8, j+16, j+24), identically for both operands, which a dot product
 // does not see.
 //
-// Block (288 threads, one per SM; work item = 128 query rows x a range of
-// 256-row database tiles):
+// Block (288 or 416 threads, one per SM; work item = 128 query rows x a range
+// of 256-row database tiles):
 //   warp 0     TMEM owner (512 columns) and single-thread MMA issuer:
 //              4 x tcgen05.mma.kind::f8f6f4 (M=128, N=256, K=32) per 128-bit
 //              k-chunk, into one of two TMEM accumulators
@@ -25,13 +25,20 @@
 //              (128 rows x 16 bytes contiguous per k-chunk, made by
 //              tile_kchunks_kernel), so a warp's load is 512 contiguous bytes;
 //              four k-chunks are in flight per thread.
-//   warps 5-8  epilogue: one query row per thread, 32 TMEM columns per
-//              tcgen05.ld; a closed-form bound on the union count admits only
-//              pairs that can beat the row's current k-th best, whose exact
-//              FP32 estimate then enters a per-row heap in shared memory
+//   warps 5+   epilogue, one or two groups of 4 warps: one query row per
+//              thread, 32 TMEM columns per tcgen05.ld; a closed-form bound on
+//              the union count admits only pairs that can beat the row's
+//              current k-th best, whose exact FP32 estimate then enters a
+//              per-row heap in shared memory.  With two groups each takes
+//              half of every tile's columns into its own heap; the groups
+//              publish their k-th best to each other (a pair below either is
+//              out of the final list) and merge the two heaps at the end.
 // All waits are bounded (mbarrier try_wait with a wall-clock budget); a
 // timeout raises BS_ERR_TIMEOUT and the block drains instead of hanging.
 #include <math.h>
+#include <stdlib.h>
+
+#include <type_traits>
 
 #include "bs_internal.cuh"
 
@@ -41,7 +48,8 @@ namespace tc {
 constexpr int BM = 128;                    // query rows per block (UMMA M, TMEM lanes)
 constexpr int BN = 256;                    // database rows per tile (UMMA N)
 constexpr int KCW = 4;                     // packed words per k-chunk (128 bits)
-constexpr int THREADS = 288;
+// threads per block with NG epilogue groups
+__host__ __device__ constexpr int threads_for(int NG) { return 32 * (5 + 4 * NG); }
 constexpr int OP_A = BM * 128;             // 16 KB of FP8
 constexpr int OP_B = BN * 128;             // 32 KB of FP8
 constexpr int OP_BYTES = OP_A + OP_B;      // 48 KB per operand slot (one k-chunk)
@@ -54,13 +62,15 @@ constexpr uint32_t NO_IDX = 0xFFFFFFFFu;
 // letting through almost none that fall a full count short.
 constexpr float FILTER_SLACK = 0.99987793f;
 
-// Shared-memory layout for NOP operand slots (offsets from the 1024-aligned base).
-template <int NOP>
+// Shared-memory layout for NOP operand slots and NG epilogue groups (offsets
+// from the 1024-aligned base); the NG heaps of k entries per row follow.
+template <int NOP, int NG>
 struct Smem {
     static constexpr int op = 0;
     static constexpr int col = op + NOP * OP_BYTES;             // 2 x 2 x 256 floats
     static constexpr int bars = col + 2 * 2 * BN * 4;
-    static constexpr int heap = bars + 256;
+    static constexpr int thr = bars + 256;                      // [NG][BM] key, idx, size
+    static constexpr int heap = thr + NG * BM * 12;
     static_assert((2 * NOP + 4) * 8 + 8 <= 256, "barrier area");
 };
 static_assert(OP_BYTES % 1024 == 0 && OP_A % 1024 == 0, "alignment");
@@ -323,33 +333,32 @@ __device__ __forceinline__ bool admit(const RowFilter &f, float U, float f0) {
 
 // Running state of one query row in the epilogue.
 struct RowState {
-    RowFilter filt;
-    float thr_k;       // key and index of the current k-th best (root of the heap)
-    uint32_t thr_i;
+    float thr_k;       // key and index of the heap root once the heap is full,
+    uint32_t thr_i;    // else (-inf, none)
     int size;          // entries in the heap
 };
 
 // A pair that passed the bound: exact FP32 key, then the heap.  Kept out of
 // line -- it runs for a small fraction of the pairs.
+// (eff_k, eff_i) is the better of this heap's root (when full) and the other
+// group's; a pair not ranking above it cannot reach the final list.
 template <int M>
 __device__ __noinline__ RowState consider(RowState st, float *hkey, uint32_t *hix, int t, uint32_t col,
-                                          uint32_t c, uint32_t b, uint32_t a, float lnA, float rc,
-                                          uint32_t N, float invL, float log2N, int cap) {
+                                          uint32_t c, uint32_t b, uint32_t a, float lnA,
+                                          float eff_k, uint32_t eff_i, uint32_t N, float invL,
+                                          int cap) {
     const float lnB = M == M_COS ? row_log(b, N) : 0.0f;
     const float key = rank_key<M>(a, b, c, N, lnA, lnB, invL);
+    if (!better(key, col, eff_k, eff_i)) return st;
     Heap h;
-    h.key = hkey; h.ix = hix; h.t = t; h.size = st.size; h.cap = cap; h.levels = heap_levels(cap);
+    h.key = hkey; h.ix = hix; h.t = t; h.size = st.size; h.cap = cap;
     if (h.size < h.cap) {
         h.push(key, col);
         st.size = h.size;
-        if (h.size == h.cap) {
-            st.thr_k = h.k_at(0); st.thr_i = h.i_at(0);
-            st.filt = make_filter<M>(st.thr_k, rc, invL, log2N);
-        }
-    } else if (better(key, col, st.thr_k, st.thr_i)) {
+        if (h.size == h.cap) { st.thr_k = h.k_at(0); st.thr_i = h.i_at(0); }
+    } else {
         h.replace_root(key, col);
         st.thr_k = h.k_at(0); st.thr_i = h.i_at(0);
-        st.filt = make_filter<M>(st.thr_k, rc, invL, log2N);
     }
     return st;
 }
@@ -368,10 +377,10 @@ __device__ __forceinline__ uint32_t select32(const uint32_t (&v)[32], uint32_t j
     return (j & 1) ? t2[1] : t2[0];
 }
 
-template <int M, int NOP>
-__global__ void __launch_bounds__(THREADS, 1)
+template <int M, int NOP, int NG>
+__global__ void __launch_bounds__(threads_for(NG), 1)
     pair_tc_kernel(const Args p) {
-    using Smem = tc::Smem<NOP>;
+    using Smem = tc::Smem<NOP, NG>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -382,8 +391,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint64_t *acc_full = bars + 2 * NOP, *acc_empty = acc_full + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-    float *heap_key = reinterpret_cast<float *>(base + Smem::heap);   // [k][BM]
-    uint32_t *heap_ix = reinterpret_cast<uint32_t *>(heap_key + (size_t)p.k * BM);
+    float *thr_key = reinterpret_cast<float *>(base + Smem::thr);     // [NG][BM]
+    uint32_t *thr_idx = reinterpret_cast<uint32_t *>(thr_key + NG * BM);
+    int *heap_size = reinterpret_cast<int *>(thr_idx + NG * BM);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t row0 = blockIdx.x * BM;
@@ -400,7 +410,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&acc_full[i], 1);
-            mbar_init(&acc_empty[i], 4);
+            mbar_init(&acc_empty[i], 4 * NG);
         }
         *abort_flag = 0;
         fence_mbar_init();
@@ -408,6 +418,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (warp == 0) {
         tmem_alloc(tmem_slot, TMEM_COLS);
         tmem_relinquish();
+    }
+    for (int i = tid; i < NG * BM; i += blockDim.x) {   // published thresholds start empty
+        thr_key[i] = -INFINITY;
+        thr_idx[i] = NO_IDX;
     }
     tc_fence_before();
     __syncthreads();
@@ -493,7 +507,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
     } else {
         // ------------------------------ epilogue ------------------------------
-        const int e = tid - 160;                   // 0..127
+        const int grp = (warp - 5) >> 2;           // epilogue group
+        const int e = tid - 160 - 128 * grp;       // 0..127 within the group
         const int quarter = warp & 3;              // TMEM lanes this warp may access
         const int r = quarter * 32 + lane;         // row within the block
         const uint32_t q = row0 + r;
@@ -502,15 +517,22 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint32_t a_cl = a < p.N - 1 ? a : p.N - 1;
         const float rc = row_const<M>((float)(p.N - a_cl), p.N);   // from A' >= 1
         const float lnA = row_log(a, p.N);
+        const float Na = (float)(p.N - a);         // N - a (raw)
+        float *hkey = reinterpret_cast<float *>(base + Smem::heap) + (size_t)grp * p.k * BM * 2;
+        uint32_t *hix = reinterpret_cast<uint32_t *>(hkey + (size_t)p.k * BM);
+        constexpr int COLS = BN / NG;              // tile columns of this group
         RowState st;
-        st.filt.all = true; st.filt.c0 = st.filt.c1 = 0.f;
         st.thr_k = -INFINITY; st.thr_i = NO_IDX; st.size = 0;
+        float eff_k = -INFINITY;                   // threshold the filter was built from
+        uint32_t eff_i = NO_IDX;
+        RowFilter filt;
+        filt.all = true; filt.c0 = filt.c1 = 0.f;
 
         for (uint32_t t = 0; t < n_my_tiles; ++t) {
             const uint32_t tile = t_begin + t;
             float *cv = colv + (t & 1) * 2 * BN;
-            // per-column values of this tile (two columns per thread)
-            for (int j = e; j < BN; j += 128) {
+            // per-column values of this group's columns (one per thread)
+            for (int j = grp * COLS + e; j < (grp + 1) * COLS; j += 128) {
                 const uint32_t col = tile * BN + j;
                 const uint32_t b = col < p.nDB ? __ldg(p.pcDB + col) : 0u;
                 const uint32_t b_cl = b < p.N - 1 ? b : p.N - 1;
@@ -523,16 +545,33 @@ __global__ void __launch_bounds__(THREADS, 1)
                 cv[j] = (float)b;         // raw count: U' is formed from the raw a, b, c
                 cv[BN + j] = f0;
             }
-            named_sync(2, 128);
+            named_sync(2 + grp, 128);
             const uint32_t ab = t & 1;
             wait(&acc_full[ab], (t >> 1) & 1);
             tc_fence_after();
-            const float Na = (float)(p.N - a);      // N - a (raw)
             const uint32_t col0 = tile * BN;
             // every lane stays in the loops below (they vote); dead rows admit nothing
             const bool live = row_ok && !*abort_flag;
-            auto score_chunk = [&](const uint32_t (&v)[32], int ch) {
-                // pass 1: which of these 32 pairs can beat the row's k-th best
+            const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + ab * BN;
+#pragma unroll 1
+            for (int ch = grp * (COLS / 32); ch < (grp + 1) * (COLS / 32); ++ch) {
+                uint32_t v[32];
+                tmem_ld32_async(trow + ch * 32, v);
+                // the threshold to beat: this heap's root or the other group's
+                float tk = st.thr_k;
+                uint32_t ti = st.thr_i;
+                if (NG == 2) {
+                    const float ok = thr_key[(1 - grp) * BM + r];
+                    const uint32_t oi = thr_idx[(1 - grp) * BM + r];
+                    if (better(ok, oi, tk, ti)) { tk = ok; ti = oi; }
+                }
+                if (tk != eff_k || ti != eff_i) {
+                    eff_k = tk; eff_i = ti;
+                    if (ti == NO_IDX) { filt.all = true; }
+                    else filt = make_filter<M>(tk, rc, p.invL, p.log2N);
+                }
+                tmem_wait();
+                // pass 1: which of these 32 pairs can beat the threshold
                 uint32_t mask = 0;
 #pragma unroll
                 for (int jj = 0; jj < 32; ++jj) {
@@ -540,7 +579,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     const float cf = __uint_as_float(v[jj]) * 4096.0f;   // exact count
                     // U' = N - min(a + b - c, N - 1) = max(N - a - b + c, 1), exact in FP32
                     const float U = fmaxf(Na - cv[j] + cf, 1.0f);
-                    if (admit<M>(st.filt, U, cv[BN + j])) mask |= 1u << jj;
+                    if (admit<M>(filt, U, cv[BN + j])) mask |= 1u << jj;
                 }
                 // columns past the database end and the self pair never rank
                 const uint32_t col_c = col0 + ch * 32;
@@ -550,44 +589,59 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (!live) mask = 0;
                 // pass 2: exact keys for the admitted pairs; the warp loops only as
                 // often as its busiest row needs
+                const int size_before = st.size;
+                const uint32_t root_before = st.thr_i;
+                const float rootk_before = st.thr_k;
                 while (__any_sync(0xffffffffu, mask != 0)) {
                     if (mask) {
                         const uint32_t jj = __ffs(mask) - 1;
                         mask &= mask - 1;
                         const uint32_t c = (uint32_t)(__uint_as_float(select32(v, jj)) * 4096.0f);
                         const int j = ch * 32 + (int)jj;
-                        st = consider<M>(st, heap_key, heap_ix, r, col_c + jj, c, (uint32_t)cv[j], a,
-                                         lnA, rc, p.N, p.invL, p.log2N, (int)p.k);
+                        st = consider<M>(st, hkey, hix, r, col_c + jj, c, (uint32_t)cv[j], a, lnA,
+                                         eff_k, eff_i, p.N, p.invL, (int)p.k);
+                        if (st.thr_i != NO_IDX && better(st.thr_k, st.thr_i, eff_k, eff_i)) {
+                            eff_k = st.thr_k; eff_i = st.thr_i;
+                        }
                     }
                 }
-            };
-            // TMEM loads double-buffered: chunk ch + 1 is in flight while ch is scored
-            const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + ab * BN;
-            uint32_t va[32], vb[32];
-            tmem_ld32_async(trow, va);
-            tmem_wait();
-#pragma unroll 1
-            for (int ch = 0; ch < BN / 32; ch += 2) {
-                tmem_ld32_async(trow + (ch + 1) * 32, vb);
-                score_chunk(va, ch);
-                tmem_wait();
-                if (ch + 2 < BN / 32) tmem_ld32_async(trow + (ch + 2) * 32, va);
-                score_chunk(vb, ch + 1);
-                tmem_wait();
+                // publish a changed root to the other group
+                if (NG == 2 && (st.size != size_before || st.thr_i != root_before ||
+                                st.thr_k != rootk_before)) {
+                    thr_key[grp * BM + r] = st.thr_k;
+                    thr_idx[grp * BM + r] = st.thr_i;
+                }
+                if (eff_i != NO_IDX) filt = make_filter<M>(eff_k, rc, p.invL, p.log2N);
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[ab]);
         }
-        // write this row's list, best first
-        if (row_ok) {
-            Heap h;
-            h.key = heap_key; h.ix = heap_ix; h.t = r; h.size = st.size; h.cap = (int)p.k;
-            h.levels = heap_levels((int)p.k);
-            h.sort_best_first();
+        // sort each heap best first; with two groups the first merges both lists
+        Heap h;
+        h.key = hkey; h.ix = hix; h.t = r; h.size = st.size; h.cap = (int)p.k;
+        if (row_ok) h.sort_best_first();
+        if (NG == 2) {
+            heap_size[grp * BM + r] = st.size;
+            named_sync(4, 128 * NG);
+        }
+        if (grp == 0 && row_ok) {
+            const float *k1 = reinterpret_cast<float *>(base + Smem::heap) + (size_t)p.k * BM * 2;
+            const uint32_t *i1 = reinterpret_cast<const uint32_t *>(k1 + (size_t)p.k * BM);
+            const int n0 = st.size, n1 = NG == 2 ? heap_size[BM + r] : 0;
+            int x = 0, y = 0;
             for (int s = 0; s < (int)p.k; ++s) {
-                const float kk = s < h.size ? h.k_at(s) : -INFINITY;
-                const uint32_t ii = s < h.size ? h.i_at(s) : NO_IDX;
+                float kk = -INFINITY;
+                uint32_t ii = NO_IDX;
+                const bool hx = x < n0, hy = y < n1;
+                if (hx || hy) {
+                    const float xk = hx ? h.k_at(x) : -INFINITY;
+                    const uint32_t xi = hx ? h.i_at(x) : NO_IDX;
+                    const float yk = hy ? k1[y * BM + r] : -INFINITY;
+                    const uint32_t yi = hy ? i1[y * BM + r] : NO_IDX;
+                    if (hx && (!hy || better(xk, xi, yk, yi))) { kk = xk; ii = xi; ++x; }
+                    else { kk = yk; ii = yi; ++y; }
+                }
                 if (p.splits == 1) {
                     const size_t o = (size_t)q * p.k + s;
                     p.score[o] = M == M_HAM ? -kk : kk;
@@ -615,12 +669,14 @@ __global__ void __launch_bounds__(THREADS, 1)
 // host side
 // ---------------------------------------------------------------------------
 
-template <int NOP>
-static size_t tc_smem_bytes(uint32_t k) { return 1024 + tc::Smem<NOP>::heap + (size_t)k * tc::BM * 8; }
+template <int NOP, int NG>
+static size_t tc_smem_bytes(uint32_t k) {
+    return 1024 + tc::Smem<NOP, NG>::heap + (size_t)NG * k * tc::BM * 8;
+}
 constexpr size_t kSmemLimit = 232448;   // 227 KB per block
 
 bool tc_shape_ok(uint32_t N, uint32_t k) {
-    return (N % 128) == 0 && N >= 256 && N <= 8192 && k >= 1 && tc_smem_bytes<2>(k) <= kSmemLimit;
+    return (N % 128) == 0 && N >= 256 && N <= 8192 && k >= 1 && tc_smem_bytes<2, 1>(k) <= kSmemLimit;
 }
 
 bool tc_supported(const uint32_t *Q, const uint32_t *DB, uint32_t N, uint32_t k) {
@@ -687,19 +743,34 @@ bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uin
     p.lnN = (float)log((double)N);
     p.score = score; p.idx = idx; p.ws_key = ws_key; p.ws_idx = ws_idx; p.err = err;
     dim3 grid((nQ + tc::BM - 1) / tc::BM, splits);
-    // three operand slots when the heap leaves room, else two
-    const bool deep = tc_smem_bytes<3>(k) <= kSmemLimit;
-    const size_t smem = deep ? tc_smem_bytes<3>(k) : tc_smem_bytes<2>(k);
+    // two epilogue groups when two heaps per row fit, three operand slots
+    // when there is room left (configuration order: most parallel first)
+    int cfg;
+    if (tc_smem_bytes<3, 2>(k) <= kSmemLimit) cfg = 0;
+    else if (tc_smem_bytes<2, 2>(k) <= kSmemLimit) cfg = 1;
+    else if (tc_smem_bytes<3, 1>(k) <= kSmemLimit) cfg = 2;
+    else cfg = 3;
+    if (const char *f = getenv("BS_TC_CONFIG")) cfg = atoi(f) & 3;
     cudaError_t ce = cudaSuccess;
-    auto go = [&](auto kern) {
+    auto go = [&](auto kern, size_t smem, int threads) {
+        if (smem > kSmemLimit) { ce = cudaErrorInvalidConfiguration; return; }
         ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (ce == cudaSuccess) kern<<<grid, tc::THREADS, smem, stream>>>(p);
+        if (ce == cudaSuccess) kern<<<grid, threads, smem, stream>>>(p);
+    };
+    auto launch = [&](auto mtag) {
+        constexpr int MM = decltype(mtag)::value;
+        switch (cfg) {
+            case 0: go(tc::pair_tc_kernel<MM, 3, 2>, tc_smem_bytes<3, 2>(k), tc::threads_for(2)); break;
+            case 1: go(tc::pair_tc_kernel<MM, 2, 2>, tc_smem_bytes<2, 2>(k), tc::threads_for(2)); break;
+            case 2: go(tc::pair_tc_kernel<MM, 3, 1>, tc_smem_bytes<3, 1>(k), tc::threads_for(1)); break;
+            default: go(tc::pair_tc_kernel<MM, 2, 1>, tc_smem_bytes<2, 1>(k), tc::threads_for(1)); break;
+        }
     };
     switch (measure) {
-        case M_IP: deep ? go(tc::pair_tc_kernel<M_IP, 3>) : go(tc::pair_tc_kernel<M_IP, 2>); break;
-        case M_HAM: deep ? go(tc::pair_tc_kernel<M_HAM, 3>) : go(tc::pair_tc_kernel<M_HAM, 2>); break;
-        case M_JS: deep ? go(tc::pair_tc_kernel<M_JS, 3>) : go(tc::pair_tc_kernel<M_JS, 2>); break;
-        default: deep ? go(tc::pair_tc_kernel<M_COS, 3>) : go(tc::pair_tc_kernel<M_COS, 2>); break;
+        case M_IP: launch(std::integral_constant<int, M_IP>()); break;
+        case M_HAM: launch(std::integral_constant<int, M_HAM>()); break;
+        case M_JS: launch(std::integral_constant<int, M_JS>()); break;
+        default: launch(std::integral_constant<int, M_COS>()); break;
     }
     if (ce != cudaSuccess) return BS_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
