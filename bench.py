@@ -208,7 +208,8 @@ def run_ours(args, rank, world, dist):
     idx = torch.empty((n, k), dtype=torch.int32, device=dev)
     wsb = B.bs_topk_workspace_bytes(n, n, N, k)
     ws = torch.empty((max(wsb, 16),), dtype=torch.uint8, device=dev)
-    launches_per_step = 2 + (1 if wsb else 0)   # sketch, count+top-k, merge (when split)
+    use_tc, splits, topk_launches = B.bs_topk_plan(n, n, N, k, B.BS_VARIANT_AUTO, True)
+    launches_per_step = 1 + topk_launches       # sketch + (re-layout, count+top-k, merge)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty((256 << 20,), dtype=torch.uint8, device=dev)   # > 129 MB L2
 
@@ -302,7 +303,6 @@ def run_ours(args, rank, world, dist):
     pk = measured_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max_mhz = pk.get("sm_max_mhz", 2070.0)
-    use_tc = N % 128 == 0 and 256 <= N <= 8192 and k <= 100
     if use_tc:
         # dense 0/1 contraction on the FP8 tensor pipe: 2 flops per (pair, bit)
         flops = 2.0 * pairs * N
@@ -340,6 +340,7 @@ def run_ours(args, rank, world, dist):
             "topk_ms": tk_mean * 1e3, "topk_ms_min": t_tk_sorted[0] * 1e3,
             "topk_pair_estimates_per_s": pairs / tk_mean,
             "topk_variant": "tensor cores (tcgen05)" if use_tc else "CUDA cores (POPC)",
+            "topk_db_splits": splits,
             "popc_variant_topk_ms": t_popc * 1e3 if t_popc else None,
             "wall_s_timed_region": wall},
         "e2e": {"value": e2e_value, "unit": "pair-estimates/s", "h2d_bytes_per_step": h2d,

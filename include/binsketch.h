@@ -174,6 +174,17 @@ bs_status bs_topk_ex(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
                      bs_stream_t stream);
 
 /*
+ * bs_topk_plan -- how bs_topk_ex would run this shape, without running it:
+ * *uses_tc = 1 when the tensor-core kernel is chosen, *splits = database
+ * splits (a merge kernel runs when > 1), *launches = kernels launched per
+ * call.  same_matrix != 0 when Q and DB will be the same array (the
+ * tensor-core path then re-lays out one matrix instead of two).  Any output
+ * pointer may be NULL.  Host only; Q/DB alignment is assumed to be 16 bytes.
+ */
+bs_status bs_topk_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, uint32_t variant,
+                       int same_matrix, uint32_t *uses_tc, uint32_t *splits, uint32_t *launches);
+
+/*
  * bs_topk_noalloc -- bs_topk for callers that may not allocate GPU memory
  * (a serving process whose arena owns the whole device, a plugin living in
  * another framework's allocator, a request path that must not pay for an

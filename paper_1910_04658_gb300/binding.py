@@ -39,6 +39,8 @@ SIGNATURES = [
                        _sz, _vp]),
     ("bs_topk_ex", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, _i32, _vp, _vp, _vp,
                           _sz, _u32, _vp]),
+    ("bs_topk_plan", _i32, [_u32, _u32, _u32, _u32, _u32, _i32, ctypes.POINTER(_u32),
+                            ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
     ("bs_topk_noalloc", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, _i32, _vp, _vp,
                                _vp]),
     ("bs_get_async_error", _i32, [_vp]),
@@ -125,6 +127,14 @@ def bs_topk_ex(Q, pcQ, nQ, DB, pcDB, nDB, N, by, k, exclude_self, score, idx, wo
     _check(lib().bs_topk_ex(_p(Q), _p(pcQ), nQ, _p(DB), _p(pcDB), nDB, N, by, k, int(exclude_self),
                             _p(score), _p(idx), _p(workspace), workspace_bytes, variant,
                             _s(stream)), "bs_topk_ex")
+
+
+def bs_topk_plan(nQ, nDB, N, k, variant=0, same_matrix=False):
+    """(uses_tc, splits, launches) of a bs_topk_ex call of this shape."""
+    u, s, l = _u32(), _u32(), _u32()
+    _check(lib().bs_topk_plan(nQ, nDB, N, k, variant, int(same_matrix), ctypes.byref(u),
+                              ctypes.byref(s), ctypes.byref(l)), "bs_topk_plan")
+    return bool(u.value), int(s.value), int(l.value)
 
 
 def bs_topk_noalloc(Q, pcQ, nQ, DB, pcDB, nDB, N, by, k, exclude_self, score, idx, stream=None):

@@ -638,6 +638,26 @@ bs_status bs_topk_ex(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const 
     return launch_merge(m, ws_key, ws_idx, nQ, k, splits, score, idx, st);
 }
 
+bs_status bs_topk_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, uint32_t variant,
+                       int same_matrix, uint32_t *uses_tc, uint32_t *splits, uint32_t *launches) {
+    if (!valid_N(N) || k == 0 || k > BS_TOPK_K_MAX || variant > BS_VARIANT_TC)
+        return BS_ERR_INVALID_ARG;
+    bool tc = false;
+    if (variant == BS_VARIANT_TC) {
+        if (nDB == 0 || !tc_shape_ok(N, k)) return BS_ERR_UNSUPPORTED;
+        tc = true;
+    } else if (variant == BS_VARIANT_AUTO) {
+        tc = nDB > 0 && tc_shape_ok(N, k);
+    }
+    const uint32_t s = (nQ == 0) ? 0 : (tc ? tc_splits(nQ, nDB) : popc_splits(nQ, nDB));
+    uint32_t l = 0;
+    if (nQ > 0) l = 1 + (s > 1 ? 1 : 0) + (tc ? (same_matrix ? 1 : 2) : 0);
+    if (uses_tc) *uses_tc = tc ? 1 : 0;
+    if (splits) *splits = s;
+    if (launches) *launches = l;
+    return BS_OK;
+}
+
 bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
                   const uint32_t *pcDB, uint32_t nDB, uint32_t N, uint32_t by, uint32_t k,
                   int exclude_self, float *score, uint32_t *idx, void *workspace,
