@@ -185,6 +185,31 @@ bs_status bs_topk_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, uint32
                        int same_matrix, uint32_t *uses_tc, uint32_t *splits, uint32_t *launches);
 
 /*
+ * bs_tiled_bytes / bs_tile_sketches -- keep a sketch database in the layout
+ * the tensor-core kernel reads (row blocks of 128, 16-byte k-chunks of a
+ * block contiguous), so repeated searches against it skip the re-layout.
+ *  sketch  uint32[n_rows][N/32] in (16-byte aligned), N % 128 == 0
+ *  tiled   bs_tiled_bytes(n_rows, N) bytes out (16-byte aligned); rows
+ *          rounded up to 128 are zero.  Same paper content as the sketches.
+ */
+size_t bs_tiled_bytes(uint32_t n_rows, uint32_t N);
+bs_status bs_tile_sketches(const uint32_t *sketch, uint32_t n_rows, uint32_t N, void *tiled,
+                           bs_stream_t stream);
+
+/*
+ * bs_topk_pretiled -- bs_topk (tensor-core kernel) of nQ row-major query
+ * sketches against a database kept tiled by bs_tile_sketches: the ranking of
+ * Experiment 2 (Sec. 4) for a query stream against a resident corpus.
+ * Requires N % 128 == 0, 256 <= N <= 8192, k <= 100 (BS_ERR_UNSUPPORTED
+ * otherwise); no self-exclusion.  Workspace: bs_topk_pretiled_workspace_bytes.
+ */
+size_t bs_topk_pretiled_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k);
+bs_status bs_topk_pretiled(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const void *DB_tiled,
+                           const uint32_t *pcDB, uint32_t nDB, uint32_t N, uint32_t by, uint32_t k,
+                           float *score, uint32_t *idx, void *workspace, size_t workspace_bytes,
+                           bs_stream_t stream);
+
+/*
  * bs_topk_noalloc -- bs_topk for callers that may not allocate GPU memory
  * (a serving process whose arena owns the whole device, a plugin living in
  * another framework's allocator, a request path that must not pay for an

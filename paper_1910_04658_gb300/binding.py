@@ -41,6 +41,11 @@ SIGNATURES = [
                           _sz, _u32, _vp]),
     ("bs_topk_plan", _i32, [_u32, _u32, _u32, _u32, _u32, _i32, ctypes.POINTER(_u32),
                             ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
+    ("bs_tiled_bytes", _sz, [_u32, _u32]),
+    ("bs_tile_sketches", _i32, [_vp, _u32, _u32, _vp, _vp]),
+    ("bs_topk_pretiled_workspace_bytes", _sz, [_u32, _u32, _u32, _u32]),
+    ("bs_topk_pretiled", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, _vp, _vp, _vp,
+                                _sz, _vp]),
     ("bs_topk_noalloc", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, _i32, _vp, _vp,
                                _vp]),
     ("bs_get_async_error", _i32, [_vp]),
@@ -135,6 +140,25 @@ def bs_topk_plan(nQ, nDB, N, k, variant=0, same_matrix=False):
     _check(lib().bs_topk_plan(nQ, nDB, N, k, variant, int(same_matrix), ctypes.byref(u),
                               ctypes.byref(s), ctypes.byref(l)), "bs_topk_plan")
     return bool(u.value), int(s.value), int(l.value)
+
+
+def bs_tiled_bytes(n_rows, N) -> int:
+    return int(lib().bs_tiled_bytes(n_rows, N))
+
+
+def bs_tile_sketches(sketch, n_rows, N, tiled, stream=None):
+    _check(lib().bs_tile_sketches(_p(sketch), n_rows, N, _p(tiled), _s(stream)), "bs_tile_sketches")
+
+
+def bs_topk_pretiled_workspace_bytes(nQ, nDB, N, k) -> int:
+    return int(lib().bs_topk_pretiled_workspace_bytes(nQ, nDB, N, k))
+
+
+def bs_topk_pretiled(Q, pcQ, nQ, DB_tiled, pcDB, nDB, N, by, k, score, idx, workspace=None,
+                     workspace_bytes=0, stream=None):
+    _check(lib().bs_topk_pretiled(_p(Q), _p(pcQ), nQ, _p(DB_tiled), _p(pcDB), nDB, N, by, k,
+                                  _p(score), _p(idx), _p(workspace), workspace_bytes, _s(stream)),
+           "bs_topk_pretiled")
 
 
 def bs_topk_noalloc(Q, pcQ, nQ, DB, pcDB, nDB, N, by, k, exclude_self, score, idx, stream=None):

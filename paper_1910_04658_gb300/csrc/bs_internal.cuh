@@ -225,7 +225,10 @@ size_t tc_tiled_bytes(uint32_t n, uint32_t N);
 bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
                   const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
                   int exclude_self, float *score, uint32_t *idx, float *ws_key, uint32_t *ws_idx,
-                  uint32_t splits, void *tiled, unsigned int *err, cudaStream_t stream);
+                  uint32_t splits, void *tiled, const void *db_tiled, unsigned int *err,
+                  cudaStream_t stream);
 bool tc_shape_ok(uint32_t N, uint32_t k);
+// row-major sketches [n][N/32] -> k-chunk tiles (N % 128 == 0)
+bs_status tile_sketches(const uint32_t *sk, uint32_t n, uint32_t N, void *tiled, cudaStream_t stream);
 
 }  // namespace bs

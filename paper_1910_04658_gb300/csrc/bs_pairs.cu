@@ -631,7 +631,7 @@ bs_status bs_topk_ex(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const 
         tiled = w + align256(ws_bytes(splits, nQ, k));
     }
     bs_status s1 = use_tc ? topk_tc(Q, pcQ, nQ, DB, pcDB, nDB, N, m, k, exclude_self, score, idx,
-                                    ws_key, ws_idx, splits, tiled, err, st)
+                                    ws_key, ws_idx, splits, tiled, nullptr, err, st)
                           : topk_popc(Q, pcQ, nQ, DB, pcDB, nDB, N, m, k, exclude_self, score, idx,
                                       ws_key, ws_idx, splits, err, st);
     if (s1 != BS_OK || splits <= 1) return s1;
@@ -656,6 +656,60 @@ bs_status bs_topk_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, uint32
     if (splits) *splits = s;
     if (launches) *launches = l;
     return BS_OK;
+}
+
+size_t bs_tiled_bytes(uint32_t n, uint32_t N) {
+    if (!valid_N(N) || (N % 128) != 0) return 0;
+    return tc_tiled_bytes(n, N);
+}
+
+bs_status bs_tile_sketches(const uint32_t *sketch, uint32_t n_rows, uint32_t N, void *tiled,
+                           bs_stream_t stream) {
+    if (!valid_N(N) || (N % 128) != 0) return BS_ERR_INVALID_ARG;
+    if (n_rows == 0) return BS_OK;
+    if (!sketch || !tiled) return BS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(sketch) & 15u) || (reinterpret_cast<uintptr_t>(tiled) & 15u))
+        return BS_ERR_INVALID_ARG;
+    return tile_sketches(sketch, n_rows, N, tiled, (cudaStream_t)stream);
+}
+
+size_t bs_topk_pretiled_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k) {
+    if (nQ == 0 || nDB == 0 || !valid_N(N) || !tc_shape_ok(N, k)) return 0;
+    return align256(ws_bytes(tc_splits(nQ, nDB), nQ, k)) + align256(tc_tiled_bytes(nQ, N));
+}
+
+bs_status bs_topk_pretiled(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const void *DB_tiled,
+                           const uint32_t *pcDB, uint32_t nDB, uint32_t N, uint32_t by, uint32_t k,
+                           float *score, uint32_t *idx, void *workspace, size_t workspace_bytes,
+                           bs_stream_t stream) {
+    if (!valid_N(N)) return BS_ERR_INVALID_ARG;
+    if (k == 0 || k > BS_TOPK_K_MAX) return BS_ERR_INVALID_ARG;
+    const int m = measure_code(by);
+    if (m < 0) return BS_ERR_INVALID_ARG;
+    if (nQ == 0) return BS_OK;
+    if (!tc_shape_ok(N, k) || nDB == 0) return BS_ERR_UNSUPPORTED;
+    if (!Q || !pcQ || !DB_tiled || !pcDB || !score || !idx) return BS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(Q) & 15u) || (reinterpret_cast<uintptr_t>(DB_tiled) & 15u))
+        return BS_ERR_INVALID_ARG;
+    unsigned int *err = error_word();
+    if (!err) return BS_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t splits = tc_splits(nQ, nDB);
+    const size_t need = align256(ws_bytes(splits, nQ, k)) + align256(tc_tiled_bytes(nQ, N));
+    if (!workspace || workspace_bytes < need) return BS_ERR_NO_MEMORY;
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return BS_ERR_INVALID_ARG;
+    uint8_t *w = reinterpret_cast<uint8_t *>(workspace);
+    float *ws_key = nullptr;
+    uint32_t *ws_idx = nullptr;
+    if (splits > 1) {
+        ws_key = reinterpret_cast<float *>(w);
+        ws_idx = reinterpret_cast<uint32_t *>(ws_key + (size_t)splits * nQ * k);
+    }
+    void *tiled = w + align256(ws_bytes(splits, nQ, k));
+    bs_status s1 = topk_tc(Q, pcQ, nQ, nullptr, pcDB, nDB, N, m, k, 0, score, idx, ws_key, ws_idx,
+                           splits, tiled, DB_tiled, err, st);
+    if (s1 != BS_OK || splits <= 1) return s1;
+    return launch_merge(m, ws_key, ws_idx, nQ, k, splits, score, idx, st);
 }
 
 bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,

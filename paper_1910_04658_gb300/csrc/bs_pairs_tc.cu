@@ -710,21 +710,33 @@ size_t tc_tiled_bytes(uint32_t n, uint32_t N) {
     return (size_t)((n + 127) / 128) * 128 * (N / 8);
 }
 
+bs_status tile_sketches(const uint32_t *sk, uint32_t n, uint32_t N, void *tiled, cudaStream_t stream) {
+    const uint32_t nKc = N / 128;
+    dim3 g((n + 127) / 128, (nKc + 7) / 8);
+    tc::tile_kchunks_kernel<<<g, 256, 0, stream>>>(reinterpret_cast<const uint4 *>(sk), n, nKc,
+                                                   reinterpret_cast<uint4 *>(tiled));
+    return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+}
+
 bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
                   const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
                   int exclude_self, float *score, uint32_t *idx, float *ws_key, uint32_t *ws_idx,
-                  uint32_t splits, void *tiled, unsigned int *err, cudaStream_t stream) {
+                  uint32_t splits, void *tiled, const void *db_tiled, unsigned int *err,
+                  cudaStream_t stream) {
     const uint32_t W = N / 32;
     const uint32_t nKc = W / tc::KCW;
-    // k-chunk-tiled copies of the operands (one copy when Q and DB coincide)
+    // k-chunk-tiled copies of the operands (one copy when Q and DB coincide;
+    // none for DB when the caller keeps it tiled)
     uint4 *tQ = reinterpret_cast<uint4 *>(tiled);
     uint4 *tDB = tQ;
-    const bool same = (Q == DB && nQ == nDB);
+    const bool same = (Q == DB && nQ == nDB && !db_tiled);
     {
         dim3 g((nQ + 127) / 128, (nKc + 7) / 8);
         tc::tile_kchunks_kernel<<<g, 256, 0, stream>>>(reinterpret_cast<const uint4 *>(Q), nQ, nKc, tQ);
     }
-    if (!same) {
+    if (db_tiled) {
+        tDB = const_cast<uint4 *>(reinterpret_cast<const uint4 *>(db_tiled));
+    } else if (!same) {
         tDB = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(tiled) + tc_tiled_bytes(nQ, N));
         dim3 g((nDB + 127) / 128, (nKc + 7) / 8);
         tc::tile_kchunks_kernel<<<g, 256, 0, stream>>>(reinterpret_cast<const uint4 *>(DB), nDB, nKc, tDB);

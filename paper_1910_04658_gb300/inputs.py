@@ -20,6 +20,7 @@ generators stand in for them:
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass
 
 import numpy as np
@@ -206,3 +207,35 @@ def random_sketches(seed: int, n: int, N: int, density: float = 0.5) -> np.ndarr
     rng = np.random.default_rng(seed)
     bits = rng.random((n, N)) < density
     return np.packbits(bits, axis=1, bitorder="little").view(np.uint32).reshape(n, N // 32)
+
+
+def bow_corpus_device(seed: int, n: int, d: int, median: float = 200.0, sigma: float = 1.0,
+                      lo: int = 1, hi: int = 5000, device="cuda", s: float = 1.0):
+    """A large text-BoW-shaped corpus drawn directly on the GPU (torch RNG).
+
+    Same shape as bow_corpus -- log-normal nnz per row clipped to [lo, hi],
+    Zipf(s) columns through a seeded rank -> id permutation -- but columns are
+    drawn with replacement (a repeated column is harmless: OR is idempotent)
+    and no near-duplicate children are planted.  Returns device tensors
+    (row_ptr int64 [n + 1], col int32 [nnz]) holding uint64 offsets and
+    uint32 ids."""
+    import torch
+    g = torch.Generator().manual_seed(seed)
+    ln = torch.randn(n, generator=g, dtype=torch.float64) * sigma + math.log(median)
+    nnz = torch.clamp(torch.round(torch.exp(ln)), lo, hi).to(torch.int64)
+    row_ptr = torch.zeros(n + 1, dtype=torch.int64)
+    row_ptr[1:] = torch.cumsum(nnz, 0)
+    total = int(row_ptr[-1])
+    perm = torch.randperm(d, generator=g).to(torch.int32).to(device)
+    w = 1.0 / torch.arange(1, d + 1, dtype=torch.float64, device=device) ** s
+    cdf = torch.cumsum(w, 0)
+    cdf /= cdf[-1].clone()
+    gd = torch.Generator(device=device).manual_seed(seed + 1)
+    col = torch.empty(total, dtype=torch.int32, device=device)
+    step = 1 << 26
+    for a in range(0, total, step):
+        b = min(total, a + step)
+        u = torch.rand(b - a, generator=gd, dtype=torch.float64, device=device)
+        r = torch.searchsorted(cdf, u, right=True).clamp_(max=d - 1)
+        col[a:b] = perm[r]
+    return row_ptr.to(device), col
