@@ -239,3 +239,14 @@ def bow_corpus_device(seed: int, n: int, d: int, median: float = 200.0, sigma: f
         r = torch.searchsorted(cdf, u, right=True).clamp_(max=d - 1)
         col[a:b] = perm[r]
     return row_ptr.to(device), col
+
+
+def query_batch(rng: np.random.Generator, q: int, zipf: "ZipfColumns", median: float = 200.0,
+                sigma: float = 1.0, lo: int = 1, hi: int = 5000):
+    """q query vectors shaped like bow_corpus rows (log-normal nnz, Zipf
+    columns, drawn with replacement).  Returns (row_ptr uint64, col uint32)."""
+    nnz = nnz_lognormal(rng, q, median, sigma, lo, hi)
+    row_ptr = np.zeros(q + 1, np.uint64)
+    row_ptr[1:] = np.cumsum(nnz).astype(np.uint64)
+    col = zipf.draw(rng, int(row_ptr[-1])).astype(np.uint32)
+    return row_ptr, col
