@@ -79,6 +79,31 @@ bs_status bs_sketch(const uint64_t *row_ptr, const uint32_t *col, uint32_t n_row
                     bs_stream_t stream);
 
 /*
+ * bs_sketch_batched -- sketch many independent CSR datasets, each with its own
+ * d, N and seed, in one persistent launch (one warp per row, grid-stride over
+ * all rows of all jobs).  Results are identical to one bs_sketch per job.
+ *  jobs    DEVICE array of n_jobs bs_sketch_job (all pointers device memory;
+ *          popcnt may be NULL)
+ *  max_N   upper bound of every job's N (sizes the per-warp shared buffer)
+ * Errors: BS_ERR_INVALID_ARG for a bad max_N; bad jobs (N > max_N, N not a
+ * multiple of 32, NULL arrays) and bad data are reported asynchronously.
+ */
+typedef struct {
+    const uint64_t *row_ptr;   /* [n_rows + 1] */
+    const uint32_t *col;       /* [nnz] */
+    uint64_t nnz;
+    uint64_t seed;
+    uint32_t n_rows;
+    uint32_t d;
+    uint32_t N;
+    uint32_t pad_;
+    uint32_t *sketch;          /* [n_rows][N/32] out */
+    uint32_t *popcnt;          /* [n_rows] out, may be NULL */
+} bs_sketch_job;
+bs_status bs_sketch_batched(const bs_sketch_job *jobs, uint32_t n_jobs, uint32_t max_N,
+                            bs_stream_t stream);
+
+/*
  * bs_sketch_parity -- the BCS sketch of the same batch (Definition "BCS",
  * Sec. 2): u_s[j] = sum_{i : pi(i) = j} u[i] mod 2, with the same mapping.
  * Arguments and errors as bs_sketch.  Rows must not repeat a column (a
@@ -164,9 +189,16 @@ bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
  *                    aligned Q and DB; BS_ERR_UNSUPPORTED otherwise;
  *   BS_VARIANT_AUTO  the tensor-core kernel where it applies, else POPC
  *                    (this is what bs_topk does).
- * bs_topk_workspace_bytes() covers every variant.
+ * For the tensor-core kernel, BS_VARIANT_TC_CFG(c) OR-ed into `variant` picks
+ * its block configuration c (an autotuner's knob; the default is the most
+ * parallel one whose shared memory fits):
+ *   c = 0: 2 epilogue groups, 3 operand slots   c = 1: 2 groups, 2 slots
+ *   c = 2: 1 epilogue group, 3 operand slots    c = 3: 1 group, 2 slots
+ * A configuration whose shared memory does not fit k returns
+ * BS_ERR_UNSUPPORTED.  bs_topk_workspace_bytes() covers every variant.
  */
 enum { BS_VARIANT_AUTO = 0, BS_VARIANT_POPC = 1, BS_VARIANT_TC = 2 };
+#define BS_VARIANT_TC_CFG(c) (((uint32_t)(c) + 1u) << 4)
 bs_status bs_topk_ex(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
                      const uint32_t *DB, const uint32_t *pcDB, uint32_t nDB, uint32_t N,
                      uint32_t by, uint32_t k, int exclude_self, float *score, uint32_t *idx,

@@ -17,6 +17,19 @@ LIB_PATH = os.path.join(PKG, "_build", "libbinsketch.so")
 BS_IP, BS_HAM, BS_JS, BS_COS = 1, 2, 4, 8
 BS_VARIANT_AUTO, BS_VARIANT_POPC, BS_VARIANT_TC = 0, 1, 2
 VARIANTS = {"auto": 0, "popc": 1, "tc": 2}
+
+
+def BS_VARIANT_TC_CFG(c: int) -> int:
+    """Bits selecting tensor-core block configuration c (0..3) in bs_topk_ex's variant."""
+    return (c + 1) << 4
+
+
+class bs_sketch_job(ctypes.Structure):
+    """Mirror of the C struct bs_sketch_job (include/binsketch.h)."""
+    _fields_ = [("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("nnz", ctypes.c_uint64),
+                ("seed", ctypes.c_uint64), ("n_rows", ctypes.c_uint32), ("d", ctypes.c_uint32),
+                ("N", ctypes.c_uint32), ("pad_", ctypes.c_uint32), ("sketch", ctypes.c_void_p),
+                ("popcnt", ctypes.c_void_p)]
 MEASURE_BITS = {"ip": BS_IP, "ham": BS_HAM, "js": BS_JS, "cos": BS_COS}
 BS_TOPK_K_MAX = 128
 BS_TOPK_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -32,6 +45,7 @@ _u32, _u64, _i32, _sz, _vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, cty
 SIGNATURES = [
     ("bs_sketch", _i32, [_vp, _vp, _u32, _u64, _u32, _u32, _u64, _vp, _vp, _vp]),
     ("bs_sketch_parity", _i32, [_vp, _vp, _u32, _u64, _u32, _u32, _u64, _vp, _vp, _vp]),
+    ("bs_sketch_batched", _i32, [_vp, _u32, _u32, _vp]),
     ("bs_popcount_rows", _i32, [_vp, _u32, _u32, _vp, _vp]),
     ("bs_estimate_pairs", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp]),
     ("bs_topk_workspace_bytes", _sz, [_u32, _u32, _u32, _u32]),
@@ -101,6 +115,11 @@ def _check(rc, where):
 def bs_sketch(row_ptr, col, n_rows, nnz, d, N, seed, sketch, popcnt=None, stream=None):
     _check(lib().bs_sketch(_p(row_ptr), _p(col), n_rows, nnz, d, N, seed, _p(sketch), _p(popcnt),
                            _s(stream)), "bs_sketch")
+
+
+def bs_sketch_batched(jobs_dev, n_jobs, max_N, stream=None):
+    """jobs_dev: device pointer (or tensor) to n_jobs packed bs_sketch_job structs."""
+    _check(lib().bs_sketch_batched(_p(jobs_dev), n_jobs, max_N, _s(stream)), "bs_sketch_batched")
 
 
 def bs_sketch_parity(row_ptr, col, n_rows, nnz, d, N, seed, sketch, popcnt=None, stream=None):

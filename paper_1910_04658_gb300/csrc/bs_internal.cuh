@@ -31,6 +31,12 @@ EncodeTiledFn encode_tiled();
 // SplitMix64-derived hash parameters (host).
 void hash_params(uint64_t seed, uint64_t *mult, uint64_t *add);
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device; the attribute is set once per (device, kernel, size), so
+// launches made later -- including inside a CUDA-graph capture -- do no
+// device-attribute calls.
+cudaError_t ensure_smem(const void *func, size_t bytes);
+
 // ---------------------------------------------------------------------------
 // Device helpers
 // ---------------------------------------------------------------------------
@@ -225,8 +231,12 @@ size_t tc_tiled_bytes(uint32_t n, uint32_t N);
 bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
                   const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
                   int exclude_self, float *score, uint32_t *idx, float *ws_key, uint32_t *ws_idx,
-                  uint32_t splits, void *tiled, const void *db_tiled, unsigned int *err,
-                  cudaStream_t stream);
+                  uint32_t splits, void *tiled, const void *db_tiled, int cfg,
+                  unsigned int *err, cudaStream_t stream);
+// tensor-core block configuration chosen for k when none is requested; -1 if
+// no configuration fits
+int tc_default_cfg(uint32_t k);
+bool tc_cfg_fits(int cfg, uint32_t k);
 bool tc_shape_ok(uint32_t N, uint32_t k);
 // row-major sketches [n][N/32] -> k-chunk tiles (N % 128 == 0)
 bs_status tile_sketches(const uint32_t *sk, uint32_t n, uint32_t N, void *tiled, cudaStream_t stream);

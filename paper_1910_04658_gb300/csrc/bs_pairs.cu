@@ -460,15 +460,11 @@ static bs_status launch_pairs(const PairArgs &p, dim3 grid, cudaStream_t stream)
     const size_t smem = pair_smem_bytes(MODE);
     if (use_tma) {
         auto kern = pair_kernel<MODE, M, true>;
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return BS_ERR_CUDA;
+        if (ensure_smem((const void *)kern, smem) != cudaSuccess) return BS_ERR_CUDA;
         kern<<<grid, THREADS, smem, stream>>>(mq, md, p);
     } else {
         auto kern = pair_kernel<MODE, M, false>;
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return BS_ERR_CUDA;
+        if (ensure_smem((const void *)kern, smem) != cudaSuccess) return BS_ERR_CUDA;
         kern<<<grid, THREADS, smem, stream>>>(mq, md, p);
     }
     return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
@@ -599,7 +595,9 @@ bs_status bs_topk_ex(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const 
     if (!valid_N(N)) return BS_ERR_INVALID_ARG;
     if (k == 0 || k > BS_TOPK_K_MAX) return BS_ERR_INVALID_ARG;
     const int m = measure_code(by);
-    if (m < 0 || variant > BS_VARIANT_TC) return BS_ERR_INVALID_ARG;
+    const int tc_cfg = (int)((variant >> 4) & 15u) - 1;   // -1: default configuration
+    variant &= 15u;
+    if (m < 0 || variant > BS_VARIANT_TC || tc_cfg > 3) return BS_ERR_INVALID_ARG;
     if (nQ == 0) return BS_OK;
     if (!Q || !pcQ || !score || !idx) return BS_ERR_INVALID_ARG;
     if (nDB > 0 && (!DB || !pcDB)) return BS_ERR_INVALID_ARG;
@@ -631,7 +629,7 @@ bs_status bs_topk_ex(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const 
         tiled = w + align256(ws_bytes(splits, nQ, k));
     }
     bs_status s1 = use_tc ? topk_tc(Q, pcQ, nQ, DB, pcDB, nDB, N, m, k, exclude_self, score, idx,
-                                    ws_key, ws_idx, splits, tiled, nullptr, err, st)
+                                    ws_key, ws_idx, splits, tiled, nullptr, tc_cfg, err, st)
                           : topk_popc(Q, pcQ, nQ, DB, pcDB, nDB, N, m, k, exclude_self, score, idx,
                                       ws_key, ws_idx, splits, err, st);
     if (s1 != BS_OK || splits <= 1) return s1;
@@ -640,6 +638,7 @@ bs_status bs_topk_ex(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const 
 
 bs_status bs_topk_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, uint32_t variant,
                        int same_matrix, uint32_t *uses_tc, uint32_t *splits, uint32_t *launches) {
+    variant &= 15u;
     if (!valid_N(N) || k == 0 || k > BS_TOPK_K_MAX || variant > BS_VARIANT_TC)
         return BS_ERR_INVALID_ARG;
     bool tc = false;
@@ -707,7 +706,7 @@ bs_status bs_topk_pretiled(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, 
     }
     void *tiled = w + align256(ws_bytes(splits, nQ, k));
     bs_status s1 = topk_tc(Q, pcQ, nQ, nullptr, pcDB, nDB, N, m, k, 0, score, idx, ws_key, ws_idx,
-                           splits, tiled, DB_tiled, err, st);
+                           splits, tiled, DB_tiled, -1, err, st);
     if (s1 != BS_OK || splits <= 1) return s1;
     return launch_merge(m, ws_key, ws_idx, nQ, k, splits, score, idx, st);
 }

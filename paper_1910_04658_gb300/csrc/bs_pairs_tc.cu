@@ -675,6 +675,22 @@ static size_t tc_smem_bytes(uint32_t k) {
 }
 constexpr size_t kSmemLimit = 232448;   // 227 KB per block
 
+bool tc_cfg_fits(int cfg, uint32_t k) {
+    switch (cfg) {
+        case 0: return tc_smem_bytes<3, 2>(k) <= kSmemLimit;
+        case 1: return tc_smem_bytes<2, 2>(k) <= kSmemLimit;
+        case 2: return tc_smem_bytes<3, 1>(k) <= kSmemLimit;
+        case 3: return tc_smem_bytes<2, 1>(k) <= kSmemLimit;
+    }
+    return false;
+}
+
+int tc_default_cfg(uint32_t k) {
+    for (int c = 0; c < 4; ++c)
+        if (tc_cfg_fits(c, k)) return c;
+    return -1;
+}
+
 bool tc_shape_ok(uint32_t N, uint32_t k) {
     return (N % 128) == 0 && N >= 256 && N <= 8192 && k >= 1 && tc_smem_bytes<2, 1>(k) <= kSmemLimit;
 }
@@ -721,8 +737,8 @@ bs_status tile_sketches(const uint32_t *sk, uint32_t n, uint32_t N, void *tiled,
 bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
                   const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
                   int exclude_self, float *score, uint32_t *idx, float *ws_key, uint32_t *ws_idx,
-                  uint32_t splits, void *tiled, const void *db_tiled, unsigned int *err,
-                  cudaStream_t stream) {
+                  uint32_t splits, void *tiled, const void *db_tiled, int cfg_req,
+                  unsigned int *err, cudaStream_t stream) {
     const uint32_t W = N / 32;
     const uint32_t nKc = W / tc::KCW;
     // k-chunk-tiled copies of the operands (one copy when Q and DB coincide;
@@ -757,16 +773,12 @@ bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uin
     dim3 grid((nQ + tc::BM - 1) / tc::BM, splits);
     // two epilogue groups when two heaps per row fit, three operand slots
     // when there is room left (configuration order: most parallel first)
-    int cfg;
-    if (tc_smem_bytes<3, 2>(k) <= kSmemLimit) cfg = 0;
-    else if (tc_smem_bytes<2, 2>(k) <= kSmemLimit) cfg = 1;
-    else if (tc_smem_bytes<3, 1>(k) <= kSmemLimit) cfg = 2;
-    else cfg = 3;
-    if (const char *f = getenv("BS_TC_CONFIG")) cfg = atoi(f) & 3;
+    const int cfg = cfg_req >= 0 ? cfg_req : tc_default_cfg(k);
+    if (cfg < 0 || !tc_cfg_fits(cfg, k)) return BS_ERR_UNSUPPORTED;
     cudaError_t ce = cudaSuccess;
     auto go = [&](auto kern, size_t smem, int threads) {
         if (smem > kSmemLimit) { ce = cudaErrorInvalidConfiguration; return; }
-        ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        ce = ensure_smem((const void *)kern, smem);
         if (ce == cudaSuccess) kern<<<grid, threads, smem, stream>>>(p);
     };
     auto launch = [&](auto mtag) {

@@ -7,7 +7,9 @@
 // finished row is written to HBM with 16-byte stores and its popcount |a_s|
 // is reduced across the warp on the way out.  HBM traffic per row is the
 // algorithmic minimum: the row's indices and offsets in, N/8 + 4 bytes out.
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "bs_internal.cuh"
 
@@ -42,6 +44,21 @@ int sm_count() {
         cnt[dev] = v > 0 ? v : 148;
     }
     return cnt[dev];
+}
+
+cudaError_t ensure_smem(const void *func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> done;
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> g(mu);
+    auto key = std::make_pair(dev, func);
+    auto it = done.find(key);
+    if (it != done.end() && it->second >= bytes) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done[key] = bytes;
+    return e;
 }
 
 EncodeTiledFn encode_tiled() {
@@ -204,11 +221,7 @@ static bs_status launch_sketch(const uint64_t *row_ptr, const uint32_t *col, uin
     hash_params(seed, &mult, &add);
     const size_t smem = (size_t)kSketchWarps * (N / 32) * sizeof(uint32_t);
     auto kern = sketch_kernel<PARITY>;
-    if (smem > 48 * 1024) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return BS_ERR_CUDA;
-    }
+    if (ensure_smem((const void *)kern, smem) != cudaSuccess) return BS_ERR_CUDA;
     const uint32_t want = (n_rows + kSketchWarps - 1) / kSketchWarps;
     const uint32_t cap = (uint32_t)sm_count() * 32u;
     const uint32_t grid = want < cap ? want : cap;

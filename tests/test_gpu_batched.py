@@ -1,0 +1,67 @@
+"""Batched datasets: the persistent batched sketch equals per-dataset sketches;
+the autotuned, graph-captured top-k equals the plain per-dataset calls."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1910_04658_gb300 import inputs
+from tests.helpers import check_topk_row, u32
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1910_04658_gb300 import api, binding as B  # noqa: E402
+from paper_1910_04658_gb300.batched import Autotuner, BatchedJob, make_datasets  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def datasets():
+    ds = make_datasets(3, n_datasets=7, n_lo=300, n_hi=3000, d_lo=1e3, d_hi=1e6,
+                       Ns=(96, 256, 1024, 4096, 8192), med_lo=20, med_hi=300)
+    return ds
+
+
+def test_batched_sketch_equals_single(datasets):
+    job = BatchedJob(datasets, k=20, by="cos")
+    job.sketch_all(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert B.bs_get_async_error() == 0
+    for j, d in enumerate(datasets):
+        sk, pc = api.sketch(d.row_ptr, d.col, d.d, d.N, d.seed)
+        assert torch.equal(sk, job.sk[j]) and torch.equal(pc, job.pc[j])
+
+
+def test_tuned_graph_equals_plain_topk(datasets, tmp_path):
+    tuner = Autotuner(cache_path=str(tmp_path / "tune.json"))
+    job = BatchedJob(datasets, k=20, by="cos", autotuner=tuner)
+    job.tune()
+    tuner.save()
+    assert len(Autotuner(cache_path=str(tmp_path / "tune.json")).table) >= 1
+    job.capture()
+    for _ in range(2):
+        job.replay()
+        torch.cuda.synchronize()
+        assert B.bs_get_async_error() == 0
+        for j, d in enumerate(datasets):
+            s_ref, i_ref = api.topk(job.sk[j], job.pc[j], job.sk[j], job.pc[j], d.N, 20, by="cos",
+                                    exclude_self=True)
+            s, i = job.results(j)
+            assert torch.equal(i, i_ref) and torch.equal(s, s_ref)
+
+
+def test_batched_results_match_oracle(datasets):
+    job = BatchedJob(datasets, k=20, by="cos")
+    job.run_eager()
+    torch.cuda.synchronize()
+    for j in (0, 3):
+        d = datasets[j]
+        sk = u32(job.sk[j])
+        rows = np.arange(0, d.n, max(1, d.n // 12))
+        oest, _ = oracle.estimate_pairs(sk[rows], sk, d.N)
+        s, i = job.results(j)
+        s, i = s.cpu().numpy(), u32(i)
+        for t, r in enumerate(rows):
+            check_topk_row(s[r], i[r], oest[3, t], 20, 3, exclude_q=int(r))
