@@ -519,6 +519,67 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------
+# learned estimator in the dense regime
+# ----------------------------------------------------------------------------
+
+LEARNED = dict(workload="learned estimator, dense regime", d=100_000, Ns=[256, 1024],
+               sizes="uniform [N/4, 4N]", train_pairs=10_000_000, heldout_pairs=1_000_000,
+               mlp="4-64-64-4 GELU, BF16 weights/activations, FP32 accumulation")
+
+
+def run_learned(args):
+    import torch
+
+    from paper_1910_04658_gb300 import binding as B, build
+    from paper_1910_04658_gb300 import learned as L
+
+    build.build()
+    B.lib()
+    torch.cuda.set_device(0)
+    per_n_train = args.train_pairs // 2
+    per_n_test = args.heldout_pairs // 2
+    t0 = time.perf_counter()
+    train = [L.dense_pairs(per_n_train, N, pair_seed=1 + i) for i, N in enumerate(LEARNED["Ns"])]
+    test = [L.dense_pairs(per_n_test, N, pair_seed=101 + i) for i, N in enumerate(LEARNED["Ns"])]
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    mlp = L.MLPEstimator(seed=0)
+    t0 = time.perf_counter()
+    hist = mlp.train(train, epochs=args.epochs, batch=8192, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    table = {}
+    infer_rates = []
+    for s in test:
+        exact = L.exact_similarities(s.sizes.cpu().numpy().view(np.uint32))
+        for name, fn in (("closed_form", L.closed_form), ("mlp", mlp.estimate)):
+            fn(s)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            est = fn(s)
+            e1.record()
+            e1.synchronize()
+            if name == "mlp":
+                infer_rates.append(s.n / (e0.elapsed_time(e1) / 1e3))
+            table[f"N={s.N} {name}"] = L.mse_table(est.cpu().numpy(), exact)
+    assert B.bs_get_async_error() == 0
+    better = {m: all(table[f"N={s.N} mlp"][m] <= table[f"N={s.N} closed_form"][m] for s in test)
+              for m in L.MEASURES}
+    line = {
+        "metric": METRIC, "value": float(np.mean(infer_rates)),
+        "unit": "pair-estimates/s (MLP inference from counts)", "n_gpus": 1,
+        "steps": args.epochs, "warmup": 0, "ms_per_step": train_s / max(args.epochs, 1) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32",
+        "data": "synthetic",
+        "config": dict(LEARNED, train_pairs=args.train_pairs, heldout_pairs=args.heldout_pairs,
+                       epochs=args.epochs),
+        "components": {"mse_heldout": table, "mlp_mse_at_or_below_closed_form": better,
+                       "train_loss_per_epoch": hist, "generate_s": gen_s, "train_s": train_s},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -531,7 +592,10 @@ def main():
                     help="skip the one-off CUDA-core variant launch reported for comparison")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"],
                     help="rows of the corpus (smaller only for profiling captures)")
-    ap.add_argument("--workload", choices=["bow", "serving", "batched"], default="bow")
+    ap.add_argument("--workload", choices=["bow", "serving", "batched", "learned"], default="bow")
+    ap.add_argument("--train-pairs", type=int, default=10_000_000)
+    ap.add_argument("--heldout-pairs", type=int, default=1_000_000)
+    ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--datasets", type=int, default=64)
     ap.add_argument("--db-rows", type=int, default=SERVING["db_rows"])
     ap.add_argument("--serving-requests", type=int, default=300)
@@ -542,6 +606,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args)
+        return
+    if args.workload == "learned":
+        run_learned(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

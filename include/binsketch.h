@@ -263,6 +263,59 @@ bs_status bs_topk_noalloc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
                           bs_stream_t stream);
 
 /*
+ * Learned estimator.  The paper estimates with the closed form of Alg. 1-4;
+ * near saturation (|a_s| close to N) that inversion loses accuracy.  These
+ * calls train and run a small MLP (4 -> 64 -> 64 -> 4, GELU, weights and
+ * activations rounded to BF16, FP32 accumulation) on sketch pairs that
+ * BinSketch itself produces, as an alternative estimator for that regime;
+ * the closed form stays the reference.
+ *
+ * bs_dense_pairs -- n_pairs synthetic set pairs and their sketch counts.
+ * Pair p draws |a|, |b| uniform in [size_lo, size_hi] and the overlap uniform
+ * in [0, min(|a|, |b|)] from pair_seed, takes |a| + |b| - overlap distinct
+ * columns of [0, d) from a keyed random permutation, and sketches both sets
+ * with the mapping of hash_seed at length N (Definition "BinSketch").
+ *  counts  uint32[n_pairs][3] out: |a_s|, |b_s|, <a_s, b_s>
+ *  sizes   uint32[n_pairs][3] out (may be NULL): |a|, |b|, |a AND b| (exact)
+ *  cols    uint32[n_pairs][max_cols] out (may be NULL): the columns in order
+ *          (first the overlap, then a only, then b only), for checking
+ * Errors: BS_ERR_INVALID_ARG unless 2 * size_hi <= d and N is valid.
+ */
+bs_status bs_dense_pairs(uint32_t n_pairs, uint32_t N, uint32_t d, uint32_t size_lo, uint32_t size_hi,
+                         uint64_t pair_seed, uint64_t hash_seed, uint32_t *counts, uint32_t *sizes,
+                         uint32_t *cols, uint32_t max_cols, bs_stream_t stream);
+
+/* bs_estimate_counts -- closed-form IP, Ham, JS, Cos (Alg. 1-4, as in
+ * bs_estimate_pairs) of n count triples counts[n][3]; out float[n][4]. */
+bs_status bs_estimate_counts(const uint32_t *counts, uint32_t n, uint32_t N, float *out,
+                             bs_stream_t stream);
+
+/* MLP parameters: BS_MLP_PARAMS floats laid out as W1[64][4], b1[64],
+ * W2[64][64], b2[64], W3[4][64], b3[4].  The MLP refines the closed form:
+ * inputs are the closed-form (n_a/4N, n_b/4N, IP/4N, log2(N)/16); outputs
+ * are corrections added to the closed-form (IP/4N, Ham/8N, JS, Cos), so a
+ * zero last layer reproduces Alg. 1-4 exactly. */
+enum { BS_MLP_PARAMS = 4740 };
+
+/* bs_mlp_prepare -- inputs x float[n][4] from counts[n][3], and (when sizes is
+ * given) the training targets t float[n][4]: scaled exact similarities from
+ * sizes[n][3] minus the scaled closed form. */
+bs_status bs_mlp_prepare(const uint32_t *counts, const uint32_t *sizes, uint32_t n, uint32_t N, float *x,
+                         float *t, bs_stream_t stream);
+
+/* bs_mlp_train_step -- one Adam step (beta 0.9 / 0.999, eps 1e-8) on the mean
+ * squared error of a batch: params, adam_m, adam_v, grad are float
+ * [BS_MLP_PARAMS] (grad must start at zero and is left at zero); step counts
+ * from 1; loss (may be NULL) receives the batch loss added to its value. */
+bs_status bs_mlp_train_step(float *params, float *adam_m, float *adam_v, float *grad, uint32_t step,
+                            float lr, const float *x, const float *t, uint32_t n, float *loss,
+                            bs_stream_t stream);
+
+/* bs_mlp_estimate -- the MLP's IP, Ham, JS, Cos of counts[n][3]; out float[n][4]. */
+bs_status bs_mlp_estimate(const float *params, const uint32_t *counts, uint32_t n, uint32_t N, float *out,
+                          bs_stream_t stream);
+
+/*
  * bs_get_async_error -- synchronise `stream`, return the first data error
  * raised by a kernel on the current device since the last call (BS_OK if
  * none) and clear it.  BS_ERR_CUDA if the synchronisation itself failed.

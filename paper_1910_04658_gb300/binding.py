@@ -62,6 +62,11 @@ SIGNATURES = [
                                 _sz, _vp]),
     ("bs_topk_noalloc", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, _i32, _vp, _vp,
                                _vp]),
+    ("bs_dense_pairs", _i32, [_u32, _u32, _u32, _u32, _u32, _u64, _u64, _vp, _vp, _vp, _u32, _vp]),
+    ("bs_estimate_counts", _i32, [_vp, _u32, _u32, _vp, _vp]),
+    ("bs_mlp_prepare", _i32, [_vp, _vp, _u32, _u32, _vp, _vp, _vp]),
+    ("bs_mlp_train_step", _i32, [_vp, _vp, _vp, _vp, _u32, ctypes.c_float, _vp, _vp, _u32, _vp, _vp]),
+    ("bs_mlp_estimate", _i32, [_vp, _vp, _u32, _u32, _vp, _vp]),
     ("bs_get_async_error", _i32, [_vp]),
     ("bs_hash_params", None, [_u64, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     ("bs_status_string", ctypes.c_char_p, [_i32]),
@@ -184,6 +189,34 @@ def bs_topk_noalloc(Q, pcQ, nQ, DB, pcDB, nDB, N, by, k, exclude_self, score, id
     _check(lib().bs_topk_noalloc(_p(Q), _p(pcQ), nQ, _p(DB), _p(pcDB), nDB, N, by, k,
                                  int(exclude_self), _p(score), _p(idx), _s(stream)),
            "bs_topk_noalloc")
+
+
+BS_MLP_PARAMS = 4740
+
+
+def bs_dense_pairs(n_pairs, N, d, size_lo, size_hi, pair_seed, hash_seed, counts, sizes=None,
+                   cols=None, max_cols=0, stream=None):
+    _check(lib().bs_dense_pairs(n_pairs, N, d, size_lo, size_hi, pair_seed, hash_seed, _p(counts),
+                                _p(sizes), _p(cols), max_cols, _s(stream)), "bs_dense_pairs")
+
+
+def bs_estimate_counts(counts, n, N, out, stream=None):
+    _check(lib().bs_estimate_counts(_p(counts), n, N, _p(out), _s(stream)), "bs_estimate_counts")
+
+
+def bs_mlp_prepare(counts, sizes, n, N, x, t=None, stream=None):
+    _check(lib().bs_mlp_prepare(_p(counts), _p(sizes), n, N, _p(x), _p(t), _s(stream)),
+           "bs_mlp_prepare")
+
+
+def bs_mlp_train_step(params, adam_m, adam_v, grad, step, lr, x, t, n, loss=None, stream=None):
+    _check(lib().bs_mlp_train_step(_p(params), _p(adam_m), _p(adam_v), _p(grad), step, lr, _p(x),
+                                   _p(t), n, _p(loss), _s(stream)), "bs_mlp_train_step")
+
+
+def bs_mlp_estimate(params, counts, n, N, out, stream=None):
+    _check(lib().bs_mlp_estimate(_p(params), _p(counts), n, N, _p(out), _s(stream)),
+           "bs_mlp_estimate")
 
 
 def bs_get_async_error(stream=None) -> int:
