@@ -206,6 +206,46 @@ bs_status bs_topk_ex(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
                      bs_stream_t stream);
 
 /*
+ * bs_topk_shard -- bs_topk_ex against one contiguous shard of a database that
+ * is split across GPUs or calls (rows db_offset .. db_offset + nDB - 1 of
+ * the whole database; the ranking of Experiment 2, Sec. 4, is unchanged).
+ * DB/pcDB point at the shard's own rows.  The returned indices are LOCAL to
+ * the shard (0 .. nDB-1); bs_topk_merge adds the shard offsets.
+ *  exclude_self non-zero: skip the pairs with q == db_offset + j, i.e. query
+ *               row q is row q of the whole database (all-pairs over a
+ *               sharded corpus); nQ may exceed nDB
+ * Everything else, including the workspace (bs_topk_workspace_bytes(nQ,
+ * nDB, N, k)) and `variant`, is as for bs_topk_ex.
+ * Errors: BS_ERR_INVALID_ARG when db_offset + nDB exceeds 2^32 - 1.
+ */
+bs_status bs_topk_shard(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
+                        const uint32_t *DB, const uint32_t *pcDB, uint32_t nDB,
+                        uint32_t db_offset, uint32_t N, uint32_t by, uint32_t k,
+                        int exclude_self, float *score, uint32_t *idx, void *workspace,
+                        size_t workspace_bytes, uint32_t variant, bs_stream_t stream);
+
+/*
+ * bs_topk_merge -- merge the top-k lists of `parts` database shards into the
+ * top-k of the whole database: for every query row, the k best of all the
+ * parts' entries in the order of bs_topk (score, then smaller global index).
+ * Because each shard's list holds its k best, the result equals bs_topk over
+ * the unsharded database, index for index and bit for bit.
+ *  score_parts  float[parts][nQ][k], idx_parts uint32[parts][nQ][k]: the
+ *               outputs of bs_topk_shard (device memory)
+ *  part_offset  HOST uint32[parts]: global index of each part's row 0, added
+ *               to its valid indices (NULL: all 0); unused slots (index
+ *               0xFFFFFFFF) stay unused
+ *  by           the measure the lists were ranked by
+ *  score, idx   float[nQ][k], uint32[nQ][k] output (device; must not alias
+ *               the inputs)
+ * Errors: BS_ERR_INVALID_ARG for parts == 0 or parts > BS_TOPK_MERGE_PARTS_MAX.
+ */
+#define BS_TOPK_MERGE_PARTS_MAX 256
+bs_status bs_topk_merge(const float *score_parts, const uint32_t *idx_parts, uint32_t parts,
+                        uint32_t nQ, uint32_t k, const uint32_t *part_offset, uint32_t by,
+                        float *score, uint32_t *idx, bs_stream_t stream);
+
+/*
  * bs_topk_plan -- how bs_topk_ex would run this shape, without running it:
  * *uses_tc = 1 when the tensor-core kernel is chosen, *splits = database
  * splits (a merge kernel runs when > 1), *launches = kernels launched per

@@ -32,6 +32,7 @@ class bs_sketch_job(ctypes.Structure):
                 ("popcnt", ctypes.c_void_p)]
 MEASURE_BITS = {"ip": BS_IP, "ham": BS_HAM, "js": BS_JS, "cos": BS_COS}
 BS_TOPK_K_MAX = 128
+BS_TOPK_MERGE_PARTS_MAX = 256
 BS_TOPK_NOALLOC_SCRATCH_BYTES = 16 << 20
 BS_N_MAX = 65536
 STATUS = {0: "BS_OK", 1: "BS_ERR_INVALID_ARG", 2: "BS_ERR_INDEX_RANGE", 3: "BS_ERR_ROWPTR",
@@ -53,6 +54,10 @@ SIGNATURES = [
                        _sz, _vp]),
     ("bs_topk_ex", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, _i32, _vp, _vp, _vp,
                           _sz, _u32, _vp]),
+    ("bs_topk_shard", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, _u32, _i32, _vp,
+                             _vp, _vp, _sz, _u32, _vp]),
+    ("bs_topk_merge", _i32, [_vp, _vp, _u32, _u32, _u32, ctypes.POINTER(_u32), _u32, _vp, _vp,
+                             _vp]),
     ("bs_topk_plan", _i32, [_u32, _u32, _u32, _u32, _u32, _i32, ctypes.POINTER(_u32),
                             ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
     ("bs_tiled_bytes", _sz, [_u32, _u32]),
@@ -156,6 +161,20 @@ def bs_topk_ex(Q, pcQ, nQ, DB, pcDB, nDB, N, by, k, exclude_self, score, idx, wo
     _check(lib().bs_topk_ex(_p(Q), _p(pcQ), nQ, _p(DB), _p(pcDB), nDB, N, by, k, int(exclude_self),
                             _p(score), _p(idx), _p(workspace), workspace_bytes, variant,
                             _s(stream)), "bs_topk_ex")
+
+
+def bs_topk_shard(Q, pcQ, nQ, DB, pcDB, nDB, db_offset, N, by, k, exclude_self, score, idx,
+                  workspace=None, workspace_bytes=0, variant=0, stream=None):
+    _check(lib().bs_topk_shard(_p(Q), _p(pcQ), nQ, _p(DB), _p(pcDB), nDB, db_offset, N, by, k,
+                               int(exclude_self), _p(score), _p(idx), _p(workspace),
+                               workspace_bytes, variant, _s(stream)), "bs_topk_shard")
+
+
+def bs_topk_merge(score_parts, idx_parts, parts, nQ, k, part_offset, by, score, idx, stream=None):
+    """part_offset: a sequence of `parts` ints (host), or None."""
+    offs = None if part_offset is None else (_u32 * parts)(*[int(o) for o in part_offset])
+    _check(lib().bs_topk_merge(_p(score_parts), _p(idx_parts), parts, nQ, k, offs, by, _p(score),
+                               _p(idx), _s(stream)), "bs_topk_merge")
 
 
 def bs_topk_plan(nQ, nDB, N, k, variant=0, same_matrix=False):

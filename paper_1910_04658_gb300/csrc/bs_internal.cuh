@@ -213,10 +213,11 @@ enum { VARIANT_AUTO = 0, VARIANT_POPC = 1, VARIANT_TC = 2 };
 
 // POPC variant (bs_pairs.cu)
 uint32_t popc_splits(uint32_t nQ, uint32_t nDB);
+// exclude_self drops the pairs with query index q == self_off + database index
 bs_status topk_popc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
                     const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
-                    int exclude_self, float *score, uint32_t *idx, float *ws_key, uint32_t *ws_idx,
-                    uint32_t splits, unsigned int *err, cudaStream_t stream);
+                    int exclude_self, uint32_t self_off, float *score, uint32_t *idx, float *ws_key,
+                    uint32_t *ws_idx, uint32_t splits, unsigned int *err, cudaStream_t stream);
 // merge per-split lists ws_key/ws_idx [splits][nQ][k] into score/idx
 bs_status launch_merge(int measure, const float *ws_key, const uint32_t *ws_idx, uint32_t nQ,
                        uint32_t k, uint32_t splits, float *score, uint32_t *idx, cudaStream_t stream);
@@ -230,8 +231,8 @@ size_t tc_tiled_bytes(uint32_t n, uint32_t N);
 // bytes (only the first part is used when Q and DB are the same matrix)
 bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
                   const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
-                  int exclude_self, float *score, uint32_t *idx, float *ws_key, uint32_t *ws_idx,
-                  uint32_t splits, void *tiled, const void *db_tiled, int cfg,
+                  int exclude_self, uint32_t self_off, float *score, uint32_t *idx, float *ws_key,
+                  uint32_t *ws_idx, uint32_t splits, void *tiled, const void *db_tiled, int cfg,
                   unsigned int *err, cudaStream_t stream);
 // tensor-core block configuration chosen for k when none is requested; -1 if
 // no configuration fits

@@ -2,8 +2,9 @@
 //
 // The closed form of Alg. 1-4 inverts E|a_s| = N (1 - (1 - 1/N)^|a|); as
 // |a_s| approaches N that inversion loses precision (and is capped at N - 1).
-// Here a small MLP maps (|a_s|, |b_s|, <a_s, b_s>, N) to the four similarities
-// instead.  It is trained on sketch pairs that BinSketch itself produces:
+// Here a small MLP learns a correction to the closed form from the
+// closed-form estimates themselves.  It is trained on sketch pairs that
+// BinSketch itself produces:
 //
 //  * bs_dense_pairs: one warp per pair draws |a|, |b| uniform in [lo, hi] and
 //    the overlap uniform in [0, min(|a|, |b|)], takes |a| + |b| - overlap

@@ -50,7 +50,8 @@ struct PairArgs {
     uint32_t *counts;
     // top-k mode
     uint32_t k;
-    int exclude_self;
+    int exclude_self;       // drop the pair q == self_off + c
+    uint32_t self_off;
     uint32_t splits;        // database splits (grid.y)
     uint32_t tiles_per_split;
     float *score;           // final output (splits == 1)
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const uint32_t c = col0 + tx + 16 * j;
-                    if (c >= p.nDB || (p.exclude_self && c == q)) continue;
+                    if (c >= p.nDB || (p.exclude_self && (uint64_t)c + p.self_off == q)) continue;
                     const float key = rank_key<M>(row_pc[r], bcnt[j], acc[i][j], p.N, row_ln[r],
                                                   lnB[j], p.invL);
                     if (better(key, c, tk, ti)) {
@@ -367,12 +368,20 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 }
 
+// Index offsets of the parts of a cross-shard merge (bs_topk_merge).
+struct PartOffsets {
+    uint32_t v[BS_TOPK_MERGE_PARTS_MAX];
+};
+
 // Merge the per-split top-k lists of each query row (one warp per row).
-template <int M>
+// Lists hold ranking keys (SCORES = false: split lists of one call) or output
+// scores (SCORES = true: the final lists of database shards, whose indices
+// are shifted by their shard's offset).
+template <int M, bool SCORES>
 __global__ void __launch_bounds__(256)
     merge_topk_kernel(const float *__restrict__ ws_key, const uint32_t *__restrict__ ws_idx,
                       uint32_t nQ, uint32_t k, uint32_t splits, float *__restrict__ score,
-                      uint32_t *__restrict__ idx) {
+                      uint32_t *__restrict__ idx, const __grid_constant__ PartOffsets offs) {
     __shared__ float skey[8][CAP];
     __shared__ uint32_t sidx[8][CAP];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -391,6 +400,10 @@ __global__ void __launch_bounds__(256)
                 if (t < k) {
                     kk = ws_key[o + t];
                     ii = ws_idx[o + t];
+                    if (SCORES) {
+                        if (M == M_HAM) kk = -kk;
+                        if (ii != NO_IDX) ii += offs.v[s];
+                    }
                 }
                 const bool take = t < k && ii != NO_IDX && better(kk, ii, tk, ti);
                 const uint32_t m = __ballot_sync(0xffffffffu, take);
@@ -490,27 +503,35 @@ uint32_t popc_splits(uint32_t nQ, uint32_t nDB) {
     return (tiles + per - 1) / per;
 }
 
-bs_status launch_merge(int measure, const float *ws_key, const uint32_t *ws_idx, uint32_t nQ,
-                       uint32_t k, uint32_t splits, float *score, uint32_t *idx, cudaStream_t st) {
+template <bool SCORES>
+static bs_status merge_lists(int measure, const float *key, const uint32_t *ix, uint32_t nQ,
+                             uint32_t k, uint32_t parts, float *score, uint32_t *idx,
+                             const PartOffsets &offs, cudaStream_t st) {
     const uint32_t blocks = (nQ + 7) / 8;
     switch (measure) {
-        case M_IP: merge_topk_kernel<M_IP><<<blocks, 256, 0, st>>>(ws_key, ws_idx, nQ, k, splits, score, idx); break;
-        case M_HAM: merge_topk_kernel<M_HAM><<<blocks, 256, 0, st>>>(ws_key, ws_idx, nQ, k, splits, score, idx); break;
-        case M_JS: merge_topk_kernel<M_JS><<<blocks, 256, 0, st>>>(ws_key, ws_idx, nQ, k, splits, score, idx); break;
-        default: merge_topk_kernel<M_COS><<<blocks, 256, 0, st>>>(ws_key, ws_idx, nQ, k, splits, score, idx); break;
+        case M_IP: merge_topk_kernel<M_IP, SCORES><<<blocks, 256, 0, st>>>(key, ix, nQ, k, parts, score, idx, offs); break;
+        case M_HAM: merge_topk_kernel<M_HAM, SCORES><<<blocks, 256, 0, st>>>(key, ix, nQ, k, parts, score, idx, offs); break;
+        case M_JS: merge_topk_kernel<M_JS, SCORES><<<blocks, 256, 0, st>>>(key, ix, nQ, k, parts, score, idx, offs); break;
+        default: merge_topk_kernel<M_COS, SCORES><<<blocks, 256, 0, st>>>(key, ix, nQ, k, parts, score, idx, offs); break;
     }
     return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
 }
 
+bs_status launch_merge(int measure, const float *ws_key, const uint32_t *ws_idx, uint32_t nQ,
+                       uint32_t k, uint32_t splits, float *score, uint32_t *idx, cudaStream_t st) {
+    static const PartOffsets zero = {};
+    return merge_lists<false>(measure, ws_key, ws_idx, nQ, k, splits, score, idx, zero, st);
+}
+
 bs_status topk_popc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
                     const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
-                    int exclude_self, float *score, uint32_t *idx, float *ws_key, uint32_t *ws_idx,
-                    uint32_t splits, unsigned int *err, cudaStream_t st) {
+                    int exclude_self, uint32_t self_off, float *score, uint32_t *idx, float *ws_key,
+                    uint32_t *ws_idx, uint32_t splits, unsigned int *err, cudaStream_t st) {
     PairArgs p = {};
     p.Q = Q; p.DB = DB; p.pcQ = pcQ; p.pcDB = pcDB;
     p.nQ = nQ; p.nDB = nDB; p.N = N; p.W = N / 32; p.nK = (p.W + KC - 1) / KC;
     p.invL = inv_ln_n(N);
-    p.k = k; p.exclude_self = exclude_self; p.err = err;
+    p.k = k; p.exclude_self = exclude_self; p.self_off = self_off; p.err = err;
     p.score = score; p.idx = idx;
     const uint32_t tiles = (nDB + BN - 1) / BN;
     p.splits = splits;
@@ -588,10 +609,11 @@ size_t bs_topk_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k
     return need;
 }
 
-bs_status bs_topk_ex(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
-                     const uint32_t *pcDB, uint32_t nDB, uint32_t N, uint32_t by, uint32_t k,
-                     int exclude_self, float *score, uint32_t *idx, void *workspace,
-                     size_t workspace_bytes, uint32_t variant, bs_stream_t stream) {
+static bs_status topk_impl(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
+                           const uint32_t *pcDB, uint32_t nDB, uint32_t N, uint32_t by, uint32_t k,
+                           int exclude_self, uint32_t self_off, float *score, uint32_t *idx,
+                           void *workspace, size_t workspace_bytes, uint32_t variant,
+                           cudaStream_t st) {
     if (!valid_N(N)) return BS_ERR_INVALID_ARG;
     if (k == 0 || k > BS_TOPK_K_MAX) return BS_ERR_INVALID_ARG;
     const int m = measure_code(by);
@@ -601,10 +623,8 @@ bs_status bs_topk_ex(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const 
     if (nQ == 0) return BS_OK;
     if (!Q || !pcQ || !score || !idx) return BS_ERR_INVALID_ARG;
     if (nDB > 0 && (!DB || !pcDB)) return BS_ERR_INVALID_ARG;
-    if (exclude_self && nQ > nDB) return BS_ERR_INVALID_ARG;
     unsigned int *err = error_word();
     if (!err) return BS_ERR_CUDA;
-    cudaStream_t st = (cudaStream_t)stream;
 
     bool use_tc = false;
     if (variant == BS_VARIANT_TC) {
@@ -628,12 +648,46 @@ bs_status bs_topk_ex(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const 
         }
         tiled = w + align256(ws_bytes(splits, nQ, k));
     }
-    bs_status s1 = use_tc ? topk_tc(Q, pcQ, nQ, DB, pcDB, nDB, N, m, k, exclude_self, score, idx,
-                                    ws_key, ws_idx, splits, tiled, nullptr, tc_cfg, err, st)
-                          : topk_popc(Q, pcQ, nQ, DB, pcDB, nDB, N, m, k, exclude_self, score, idx,
-                                      ws_key, ws_idx, splits, err, st);
+    bs_status s1 = use_tc ? topk_tc(Q, pcQ, nQ, DB, pcDB, nDB, N, m, k, exclude_self, self_off, score,
+                                    idx, ws_key, ws_idx, splits, tiled, nullptr, tc_cfg, err, st)
+                          : topk_popc(Q, pcQ, nQ, DB, pcDB, nDB, N, m, k, exclude_self, self_off,
+                                      score, idx, ws_key, ws_idx, splits, err, st);
     if (s1 != BS_OK || splits <= 1) return s1;
     return launch_merge(m, ws_key, ws_idx, nQ, k, splits, score, idx, st);
+}
+
+bs_status bs_topk_ex(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
+                     const uint32_t *pcDB, uint32_t nDB, uint32_t N, uint32_t by, uint32_t k,
+                     int exclude_self, float *score, uint32_t *idx, void *workspace,
+                     size_t workspace_bytes, uint32_t variant, bs_stream_t stream) {
+    if (exclude_self && nQ > nDB) return BS_ERR_INVALID_ARG;
+    return topk_impl(Q, pcQ, nQ, DB, pcDB, nDB, N, by, k, exclude_self, 0, score, idx, workspace,
+                     workspace_bytes, variant, (cudaStream_t)stream);
+}
+
+bs_status bs_topk_shard(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
+                        const uint32_t *pcDB, uint32_t nDB, uint32_t db_offset, uint32_t N,
+                        uint32_t by, uint32_t k, int exclude_self, float *score, uint32_t *idx,
+                        void *workspace, size_t workspace_bytes, uint32_t variant,
+                        bs_stream_t stream) {
+    if ((uint64_t)db_offset + nDB > 0xFFFFFFFFull) return BS_ERR_INVALID_ARG;
+    return topk_impl(Q, pcQ, nQ, DB, pcDB, nDB, N, by, k, exclude_self, db_offset, score, idx,
+                     workspace, workspace_bytes, variant, (cudaStream_t)stream);
+}
+
+bs_status bs_topk_merge(const float *score_parts, const uint32_t *idx_parts, uint32_t parts,
+                        uint32_t nQ, uint32_t k, const uint32_t *part_offset, uint32_t by,
+                        float *score, uint32_t *idx, bs_stream_t stream) {
+    const int m = measure_code(by);
+    if (m < 0 || k == 0 || k > BS_TOPK_K_MAX) return BS_ERR_INVALID_ARG;
+    if (parts == 0 || parts > BS_TOPK_MERGE_PARTS_MAX) return BS_ERR_INVALID_ARG;
+    if (nQ == 0) return BS_OK;
+    if (!score_parts || !idx_parts || !score || !idx) return BS_ERR_INVALID_ARG;
+    PartOffsets offs = {};
+    if (part_offset)
+        for (uint32_t i = 0; i < parts; ++i) offs.v[i] = part_offset[i];
+    return merge_lists<true>(m, score_parts, idx_parts, nQ, k, parts, score, idx, offs,
+                             (cudaStream_t)stream);
 }
 
 bs_status bs_topk_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, uint32_t variant,
@@ -705,8 +759,8 @@ bs_status bs_topk_pretiled(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, 
         ws_idx = reinterpret_cast<uint32_t *>(ws_key + (size_t)splits * nQ * k);
     }
     void *tiled = w + align256(ws_bytes(splits, nQ, k));
-    bs_status s1 = topk_tc(Q, pcQ, nQ, nullptr, pcDB, nDB, N, m, k, 0, score, idx, ws_key, ws_idx,
-                           splits, tiled, DB_tiled, -1, err, st);
+    bs_status s1 = topk_tc(Q, pcQ, nQ, nullptr, pcDB, nDB, N, m, k, 0, 0, score, idx, ws_key,
+                           ws_idx, splits, tiled, DB_tiled, -1, err, st);
     if (s1 != BS_OK || splits <= 1) return s1;
     return launch_merge(m, ws_key, ws_idx, nQ, k, splits, score, idx, st);
 }

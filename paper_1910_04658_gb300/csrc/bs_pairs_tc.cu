@@ -80,7 +80,8 @@ struct Args {
     const uint32_t *pcQ, *pcDB;
     uint32_t nQ, nDB, N, W, nKc, nSl;
     uint32_t k, tiles_per_split, splits;
-    int exclude_self;
+    int exclude_self;  // drop the pair q == self_off + j
+    uint32_t self_off;
     float invL;        // 1 / ln(1 - 1/N)
     float log2N, lnN;
     float *score;      // splits == 1
@@ -585,7 +586,10 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                 const uint32_t col_c = col0 + ch * 32;
                 if (col_c + 32 > p.nDB)
                     mask &= col_c >= p.nDB ? 0u : (0xFFFFFFFFu >> (32 - (p.nDB - col_c)));
-                if (p.exclude_self && q >= col_c && q < col_c + 32) mask &= ~(1u << (q - col_c));
+                if (p.exclude_self) {
+                    const long long qs = (long long)q - (long long)p.self_off - (long long)col_c;
+                    if (qs >= 0 && qs < 32) mask &= ~(1u << (uint32_t)qs);
+                }
                 if (!live) mask = 0;
                 // pass 2: exact keys for the admitted pairs; the warp loops only as
                 // often as its busiest row needs
@@ -736,8 +740,8 @@ bs_status tile_sketches(const uint32_t *sk, uint32_t n, uint32_t N, void *tiled,
 
 bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
                   const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
-                  int exclude_self, float *score, uint32_t *idx, float *ws_key, uint32_t *ws_idx,
-                  uint32_t splits, void *tiled, const void *db_tiled, int cfg_req,
+                  int exclude_self, uint32_t self_off, float *score, uint32_t *idx, float *ws_key,
+                  uint32_t *ws_idx, uint32_t splits, void *tiled, const void *db_tiled, int cfg_req,
                   unsigned int *err, cudaStream_t stream) {
     const uint32_t W = N / 32;
     const uint32_t nKc = W / tc::KCW;
@@ -763,7 +767,7 @@ bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uin
     p.pcQ = pcQ; p.pcDB = pcDB; p.nQ = nQ; p.nDB = nDB; p.N = N; p.W = W;
     p.nKc = nKc;
     p.nSl = (nKc + 1) / 2;
-    p.k = k; p.exclude_self = exclude_self; p.splits = splits;
+    p.k = k; p.exclude_self = exclude_self; p.self_off = self_off; p.splits = splits;
     const uint32_t tiles = (nDB + tc::BN - 1) / tc::BN;
     p.tiles_per_split = (tiles + splits - 1) / splits;
     p.invL = (float)(1.0 / log1p(-1.0 / (double)N));
