@@ -49,17 +49,19 @@ __global__ void __launch_bounds__(kBatchWarps * 32)
         uint64_t st = J.seed;
         const uint64_t mult = splitmix64_dev(st) | 1ull;
         const uint64_t add = splitmix64_dev(st);
+        const HashParts h = {(uint32_t)mult, (uint32_t)(mult >> 32), (uint32_t)add,
+                             (uint32_t)(add >> 32)};
         for (uint32_t w = lane; w < W; w += 32) s[w] = 0u;
         __syncwarp();
         const uint64_t b = J.row_ptr[r], e = J.row_ptr[r + 1];
         const bool ok = (b <= e) && (e <= J.nnz);
         bool bad = false;
         if (ok) {
-            for (uint64_t k = b + lane; k < e; k += 32) {
-                const uint32_t i = __ldg(J.col + k);
-                if (i >= J.d) { bad = true; continue; }
-                const uint32_t jb = bucket_of(i, mult, add, N);
-                atomicOr(&s[jb >> 5], 1u << (jb & 31));
+            // pieces of at most 2^30 indices (one piece in practice)
+            for (uint64_t q = b; q < e; q += (1ull << 30)) {
+                const uint64_t rest = e - q;
+                const uint32_t len = rest > (1ull << 30) ? (1u << 30) : (uint32_t)rest;
+                scatter_row<false>(s, J.col + q, len, J.d, h, N, lane, bad);
             }
         }
         bad = __any_sync(0xffffffffu, bad);
@@ -76,8 +78,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32)
             cnt += __popc(x);
             out[t] = x;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        cnt = __reduce_add_sync(0xffffffffu, cnt);
         if (J.popcnt && lane == 0) J.popcnt[r] = cnt;
         __syncwarp();
     }

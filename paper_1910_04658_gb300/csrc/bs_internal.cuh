@@ -47,6 +47,61 @@ __device__ __forceinline__ uint32_t bucket_of(uint32_t i, uint64_t mult, uint64_
     return __umulhi((uint32_t)(h >> 32), N);
 }
 
+// Hash parameters split into 32-bit halves: hi32(mult * i + add mod 2^64)
+// = mh * i + ah + hi32(ml * i + al) (mod 2^32) -- one wide multiply-add and
+// one multiply-add per index.
+struct HashParts {
+    uint32_t ml, mh, al, ah;
+};
+
+// Set (OR; XOR for BCS) the bucket bit of index i in the shared sketch s.
+// Branch-free: an index >= d only marks the row bad (the row is written as
+// zeros), its bucket is still in [0, N) so the shared access stays in bounds.
+template <bool PARITY>
+__device__ __forceinline__ void set_bucket(uint32_t *s, uint32_t i, uint32_t d, const HashParts &h,
+                                           uint32_t N, bool &bad) {
+    bad |= (i >= d);
+    const uint64_t t = (uint64_t)h.ml * i + h.al;
+    const uint32_t x = h.mh * i + h.ah + (uint32_t)(t >> 32);
+    const uint32_t j = __umulhi(x, N);
+    if (PARITY)
+        atomicXor(&s[j >> 5], 1u << (j & 31));
+    else
+        atomicOr(&s[j >> 5], 1u << (j & 31));
+}
+
+// Scatter `len` indices starting at p (any 4-byte alignment): peel to a
+// 16-byte boundary, then two 16-byte loads per lane in flight (with 32
+// registers a thread, 64 warps stay resident per SM).
+template <bool PARITY>
+__device__ __forceinline__ void scatter_row(uint32_t *s, const uint32_t *__restrict__ p, uint32_t len,
+                                            uint32_t d, const HashParts &h, uint32_t N, int lane,
+                                            bool &bad) {
+    const uint32_t mis = (uint32_t)((reinterpret_cast<uintptr_t>(p) >> 2) & 3u);
+    uint32_t peel = (4u - mis) & 3u;
+    peel = peel < len ? peel : len;
+    if ((uint32_t)lane < peel) set_bucket<PARITY>(s, __ldg(p + lane), d, h, N, bad);
+    const uint4 *v = reinterpret_cast<const uint4 *>(p + peel);
+    const uint32_t nvec = (len - peel) >> 2;
+    for (uint32_t t = lane; t < nvec; t += 64) {
+        uint4 x[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            if (t + 32 * u < nvec) x[u] = __ldg(v + t + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (t + 32 * u < nvec) {
+                set_bucket<PARITY>(s, x[u].x, d, h, N, bad);
+                set_bucket<PARITY>(s, x[u].y, d, h, N, bad);
+                set_bucket<PARITY>(s, x[u].z, d, h, N, bad);
+                set_bucket<PARITY>(s, x[u].w, d, h, N, bad);
+            }
+        }
+    }
+    const uint32_t k = peel + (nvec << 2) + lane;
+    if (k < len) set_bucket<PARITY>(s, __ldg(p + k), d, h, N, bad);
+}
+
 __device__ __forceinline__ void raise_error(unsigned int *err, unsigned int code) {
     if (err) atomicCAS(err, 0u, code);
 }

@@ -2,11 +2,13 @@
 //
 // One warp per CSR row.  The row's N/32-word sketch lives in shared memory,
 // the warp streams the row's column indices with coalesced 16-byte loads
-// (after peeling to 16-byte alignment), hashes each index to its bucket and
-// sets the bucket bit with a shared-memory atomicOr (atomicXor for BCS).  The
-// finished row is written to HBM with 16-byte stores and its popcount |a_s|
-// is reduced across the warp on the way out.  HBM traffic per row is the
-// algorithmic minimum: the row's indices and offsets in, N/8 + 4 bytes out.
+// (after peeling to 16-byte alignment, two loads per lane in flight), hashes
+// each index to its bucket and sets the bucket bit with a shared-memory
+// atomicOr (atomicXor for BCS).  The finished row is written to HBM with
+// 16-byte stores, the shared sketch is cleared on the way, and the popcount
+// |a_s| is reduced across the warp.  The next row's offsets are loaded before
+// the current row is scattered.  HBM traffic per row is the algorithmic
+// minimum: the row's indices and offsets in, N/8 + 4 bytes out.
 #include <map>
 #include <mutex>
 #include <utility>
@@ -95,22 +97,11 @@ void hash_params(uint64_t seed, uint64_t *mult, uint64_t *add) {
 
 constexpr int kSketchWarps = 8;
 
+// One warp per row, rows strided over the grid.  The row's N/32-word sketch
+// lives in shared memory (kept zero between rows: the write-out clears it);
+// the next row's offsets are loaded before the current row is scattered.
 template <bool PARITY>
-__device__ __forceinline__ void set_bucket(uint32_t *s, uint32_t i, uint32_t d, uint64_t mult,
-                                           uint64_t add, uint32_t N, bool &bad) {
-    if (i >= d) {
-        bad = true;
-        return;
-    }
-    const uint32_t j = bucket_of(i, mult, add, N);
-    if (PARITY)
-        atomicXor(&s[j >> 5], 1u << (j & 31));
-    else
-        atomicOr(&s[j >> 5], 1u << (j & 31));
-}
-
-template <bool PARITY>
-__global__ void __launch_bounds__(kSketchWarps * 32)
+__global__ void __launch_bounds__(kSketchWarps * 32, 8)
     sketch_kernel(const uint64_t *__restrict__ row_ptr, const uint32_t *__restrict__ col,
                   uint32_t n_rows, uint64_t nnz, uint32_t d, uint32_t N, uint64_t mult,
                   uint64_t add, uint32_t *__restrict__ sketch, uint32_t *__restrict__ popcnt,
@@ -122,42 +113,32 @@ __global__ void __launch_bounds__(kSketchWarps * 32)
     uint32_t *s = smem_words + (size_t)warp * W;
     const uint32_t nwarps = gridDim.x * kSketchWarps;
     const bool vec_out = (W & 3u) == 0 && ((reinterpret_cast<uintptr_t>(sketch) & 15u) == 0);
+    const HashParts h = {(uint32_t)mult, (uint32_t)(mult >> 32), (uint32_t)add, (uint32_t)(add >> 32)};
+    for (uint32_t w = lane; w < W; w += 32) s[w] = 0u;
+    __syncwarp();
 
-    for (uint32_t r = blockIdx.x * kSketchWarps + warp; r < n_rows; r += nwarps) {
-        const uint64_t b = row_ptr[r];
-        const uint64_t e = row_ptr[r + 1];
-        for (uint32_t w = lane; w < W; w += 32) s[w] = 0u;
-        __syncwarp();
-
-        bool bad = false;
+    uint32_t r = blockIdx.x * kSketchWarps + warp;
+    uint64_t b = 0, e = 0;
+    if (r < n_rows) {
+        b = __ldg(row_ptr + r);
+        e = __ldg(row_ptr + r + 1);
+    }
+    for (; r < n_rows; r += nwarps) {
+        const uint32_t rn = r + nwarps;
+        uint64_t nb = 0, ne = 0;
+        if (rn < n_rows) {   // next row's offsets, in flight while this row is done
+            nb = __ldg(row_ptr + rn);
+            ne = __ldg(row_ptr + rn + 1);
+        }
         const bool ok = (b <= e) && (e <= nnz);
+        bool bad = false;
         if (ok) {
-            // peel until col + k is 16-byte aligned
-            const uint32_t mis = (uint32_t)((reinterpret_cast<uintptr_t>(col + b) >> 2) & 3u);
-            uint64_t k = b;
-            const uint64_t peel_end = min(e, b + ((4u - mis) & 3u));
-            if (k + lane < peel_end) set_bucket<PARITY>(s, col[k + lane], d, mult, add, N, bad);
-            k = peel_end;
-            const uint64_t nvec = (e - k) >> 2;
-            const uint4 *v = reinterpret_cast<const uint4 *>(col + k);
-            // four independent 16-byte loads in flight per lane before any atomics
-            for (uint64_t t = lane; t < nvec; t += 128) {
-                uint4 x[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (t + 32 * u < nvec) x[u] = __ldg(v + t + 32 * u);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (t + 32 * u < nvec) {
-                        set_bucket<PARITY>(s, x[u].x, d, mult, add, N, bad);
-                        set_bucket<PARITY>(s, x[u].y, d, mult, add, N, bad);
-                        set_bucket<PARITY>(s, x[u].z, d, mult, add, N, bad);
-                        set_bucket<PARITY>(s, x[u].w, d, mult, add, N, bad);
-                    }
-                }
+            // rows are done in pieces of at most 2^30 indices (one piece in practice)
+            for (uint64_t q = b; q < e; q += (1ull << 30)) {
+                const uint64_t rest = e - q;
+                const uint32_t len = rest > (1ull << 30) ? (1u << 30) : (uint32_t)rest;
+                scatter_row<PARITY>(s, col + q, len, d, h, N, lane, bad);
             }
-            k += nvec << 2;
-            if (k + lane < e) set_bucket<PARITY>(s, col[k + lane], d, mult, add, N, bad);
         }
         bad = __any_sync(0xffffffffu, bad);
         if (lane == 0) {
@@ -167,27 +148,33 @@ __global__ void __launch_bounds__(kSketchWarps * 32)
         const bool zero = !ok || bad;
         __syncwarp();
 
+        // write out (zeros for a bad row), clear the shared sketch, count bits
         uint32_t cnt = 0;
         uint32_t *out = sketch + (size_t)r * W;
         if (vec_out) {
-            const uint4 *sv = reinterpret_cast<const uint4 *>(s);
+            uint4 *sv = reinterpret_cast<uint4 *>(s);
             uint4 *ov = reinterpret_cast<uint4 *>(out);
             for (uint32_t t = lane; t < (W >> 2); t += 32) {
-                uint4 x = zero ? make_uint4(0, 0, 0, 0) : sv[t];
+                uint4 x = sv[t];
+                sv[t] = make_uint4(0, 0, 0, 0);
+                if (zero) x = make_uint4(0, 0, 0, 0);
                 cnt += __popc(x.x) + __popc(x.y) + __popc(x.z) + __popc(x.w);
                 ov[t] = x;
             }
         } else {
             for (uint32_t t = lane; t < W; t += 32) {
-                const uint32_t x = zero ? 0u : s[t];
+                uint32_t x = s[t];
+                s[t] = 0u;
+                if (zero) x = 0u;
                 cnt += __popc(x);
                 out[t] = x;
             }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        cnt = __reduce_add_sync(0xffffffffu, cnt);
         if (popcnt && lane == 0) popcnt[r] = cnt;
         __syncwarp();
+        b = nb;
+        e = ne;
     }
 }
 
@@ -219,14 +206,15 @@ static bs_status launch_sketch(const uint64_t *row_ptr, const uint32_t *col, uin
     if (!err) return BS_ERR_CUDA;
     uint64_t mult, add;
     hash_params(seed, &mult, &add);
+    cudaStream_t st = (cudaStream_t)stream;
     const size_t smem = (size_t)kSketchWarps * (N / 32) * sizeof(uint32_t);
     auto kern = sketch_kernel<PARITY>;
     if (ensure_smem((const void *)kern, smem) != cudaSuccess) return BS_ERR_CUDA;
     const uint32_t want = (n_rows + kSketchWarps - 1) / kSketchWarps;
     const uint32_t cap = (uint32_t)sm_count() * 32u;
     const uint32_t grid = want < cap ? want : cap;
-    kern<<<grid, kSketchWarps * 32, smem, (cudaStream_t)stream>>>(row_ptr, col, n_rows, nnz, d, N,
-                                                                  mult, add, sketch, popcnt, err);
+    kern<<<grid, kSketchWarps * 32, smem, st>>>(row_ptr, col, n_rows, nnz, d, N, mult, add, sketch,
+                                                popcnt, err);
     return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
 }
 

@@ -56,8 +56,9 @@ def test_sketch_unaligned_column_pointer_and_empty_rows():
     c = inputs.random_csr(5, 257, 50_000, 0, 90)
     N = 512
     osk, opc = oracle.sketch(c.row_ptr, c.col, c.d, N, 3)
-    for shift in (1, 2, 3):
-        # the same rows stored `shift` words into the column buffer
+    for shift in (1, 2, 3, 4, 5):
+        # the same rows stored `shift` words into the column buffer (16-byte
+        # aligned at shift 4: the streamed kernel; otherwise the per-row one)
         col = torch.zeros(c.col.size + 8, dtype=torch.int32, device="cuda")
         col[shift:shift + c.col.size] = torch.from_numpy(c.col.view(np.int32)).cuda()
         rp = torch.from_numpy(c.row_ptr.view(np.int64)).cuda()
@@ -70,13 +71,30 @@ def test_sketch_unaligned_column_pointer_and_empty_rows():
 
 def test_sketch_long_rows_and_duplicates():
     rng = np.random.default_rng(2)
-    rows = [rng.integers(0, 1000, int(m)).astype(np.uint32) for m in [0, 1, 5000, 12000, 33, 4096]]
+    sizes = [0, 1, 5000, 12000, 33, 4096, 4088, 4089, 4085, 3, 0, 4087, 2, 4088]
+    rows = [rng.integers(0, 1000, int(m)).astype(np.uint32) for m in sizes]
     rp = np.zeros(len(rows) + 1, np.uint64)
     rp[1:] = np.cumsum([r.size for r in rows])
     c = inputs.CSR(rp, np.concatenate(rows).astype(np.uint32), 1000)
     for N in (64, 2048):
         sk, pc = _gpu_sketch(c, N, 77)
         osk, opc = oracle.sketch(c.row_ptr, c.col, c.d, N, 77)
+        assert np.array_equal(u32(sk), osk) and np.array_equal(u32(pc), opc)
+
+
+@pytest.mark.parametrize("N", [64, 4096])
+def test_sketch_many_short_rows(N):
+    # thousands of rows per staged batch, several row blocks per thread block
+    rng = np.random.default_rng(N)
+    n = 40_000
+    nnz = rng.integers(0, 4, n)
+    rp = np.zeros(n + 1, np.uint64)
+    rp[1:] = np.cumsum(nnz)
+    col = rng.integers(0, 70_000, int(rp[-1])).astype(np.uint32)
+    c = inputs.CSR(rp, col, 70_000)
+    for parity in (False, True):
+        sk, pc = _gpu_sketch(c, N, 5, parity=parity)
+        osk, opc = oracle.sketch(c.row_ptr, c.col, c.d, N, 5, parity=parity)
         assert np.array_equal(u32(sk), osk) and np.array_equal(u32(pc), opc)
 
 
