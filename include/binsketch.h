@@ -190,10 +190,14 @@ bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
  *   BS_VARIANT_AUTO  the tensor-core kernel where it applies, else POPC
  *                    (this is what bs_topk does).
  * For the tensor-core kernel, BS_VARIANT_TC_CFG(c) OR-ed into `variant` picks
- * its block configuration c (an autotuner's knob; the default is the most
- * parallel one whose shared memory fits):
- *   c = 0: 2 epilogue groups, 3 operand slots   c = 1: 2 groups, 2 slots
- *   c = 2: 1 epilogue group, 3 operand slots    c = 3: 1 group, 2 slots
+ * its block configuration c (an autotuner's knob): epilogue groups, operand
+ * slots, and K bytes per row in a slot (128: one 128-bit k-chunk per slot;
+ * 64 / 32: half / quarter k-chunks, so more slots fit the same memory):
+ *   c = 0: 2 groups, 3 slots x 128    c = 1: 2 groups, 2 slots x 128
+ *   c = 2: 1 group,  3 slots x 128    c = 3: 1 group,  2 slots x 128
+ *   c = 4: 2 groups, 4 slots x 64     c = 5: 2 groups, 8 slots x 32
+ *   c = 6: 1 group,  6 slots x 64     c = 7: 1 group,  4 slots x 64
+ * The default is the first that fits in the order 0, 1, ..., 7.
  * A configuration whose shared memory does not fit k returns
  * BS_ERR_UNSUPPORTED.  bs_topk_workspace_bytes() covers every variant.
  */

@@ -11,7 +11,7 @@ top-k).  The job runs as:
 
 and the whole sequence is captured once into a CUDA graph, so one graph
 launch replays the job.  The autotuner times the candidate kernels
-(CUDA-core POPC, tensor-core configurations 0-3) on the dataset itself and
+(CUDA-core POPC, tensor-core configurations 0-7) on the dataset itself and
 caches the winner per (GPU, N, log2 n, k, measure) in a JSON file.  The
 candidates compute identical estimates, so tuning changes speed, never
 results.
@@ -63,7 +63,7 @@ class Autotuner:
     @staticmethod
     def candidates():
         return [("popc", B.BS_VARIANT_POPC)] + [
-            (f"tc{c}", B.BS_VARIANT_TC | B.BS_VARIANT_TC_CFG(c)) for c in range(4)]
+            (f"tc{c}", B.BS_VARIANT_TC | B.BS_VARIANT_TC_CFG(c)) for c in range(B.BS_TC_CONFIGS)]
 
     @staticmethod
     def key(gpu: str, N: int, n: int, k: int, by: str) -> str:

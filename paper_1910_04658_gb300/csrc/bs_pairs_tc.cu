@@ -50,9 +50,22 @@ constexpr int BN = 256;                    // database rows per tile (UMMA N)
 constexpr int KCW = 4;                     // packed words per k-chunk (128 bits)
 // threads per block with NG epilogue groups
 __host__ __device__ constexpr int threads_for(int NG) { return 32 * (5 + 4 * NG); }
-constexpr int OP_A = BM * 128;             // 16 KB of FP8
-constexpr int OP_B = BN * 128;             // 32 KB of FP8
-constexpr int OP_BYTES = OP_A + OP_B;      // 48 KB per operand slot (one k-chunk)
+// Operand slot geometry for SK bytes of K per row (SK = 128: one whole
+// 128-bit k-chunk per slot, 128-byte swizzle; SK = 64 / 32: half / quarter
+// k-chunks with the 64- / 32-byte swizzle, so the same shared memory holds 2x
+// / 4x as many slots and a refill has more queued MMA work to hide behind).
+template <int SK>
+struct Geo {
+    static_assert(SK == 128 || SK == 64 || SK == 32, "slot width");
+    static constexpr int A = BM * SK;                       // query operand bytes
+    static constexpr int B = BN * SK;                       // database operand bytes
+    static constexpr int BYTES = A + B;                     // per slot
+    static constexpr int MMAS = SK / 32;                    // K = 32 MMAs per slot
+    static constexpr int SPK = 128 / SK;                    // slots per k-chunk
+    static constexpr int SHIFT = SK == 128 ? 0 : (SK == 64 ? 1 : 2);
+    static constexpr uint64_t LAYOUT = SK == 128 ? 2 : (SK == 64 ? 4 : 6);   // descriptor swizzle code
+    static_assert(BYTES % (8 * SK) == 0 && A % (8 * SK) == 0, "swizzle atom alignment");
+};
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t NO_IDX = 0xFFFFFFFFu;
 // Admit when U' >= bound * (1 - 2^-13).  U' is an exact integer and the bound
@@ -64,16 +77,15 @@ constexpr float FILTER_SLACK = 0.99987793f;
 
 // Shared-memory layout for NOP operand slots and NG epilogue groups (offsets
 // from the 1024-aligned base); the NG heaps of k entries per row follow.
-template <int NOP, int NG>
+template <int NOP, int NG, int SK>
 struct Smem {
     static constexpr int op = 0;
-    static constexpr int col = op + NOP * OP_BYTES;             // 2 x 2 x 256 floats
+    static constexpr int col = op + NOP * Geo<SK>::BYTES;       // 2 x 2 x 256 floats
     static constexpr int bars = col + 2 * 2 * BN * 4;
     static constexpr int thr = bars + 256;                      // [NG][BM] key, idx, size
     static constexpr int heap = thr + NG * BM * 12;
     static_assert((2 * NOP + 4) * 8 + 8 <= 256, "barrier area");
 };
-static_assert(OP_BYTES % 1024 == 0 && OP_A % 1024 == 0, "alignment");
 
 struct Args {
     const uint4 *Q, *DB;        // k-chunk-tiled sketches [ceil(n/128)][nKc][128] x 16 bytes
@@ -136,46 +148,48 @@ __device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32
 }
 __device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (SBO), leading offset unused for this layout (1).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major, SK-byte swizzle, 8-row groups
+// 8 * SK bytes apart (SBO), leading offset unused for this layout (1).
+template <int SK>
+__device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1 << 16;                 // LBO (ignored for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;       // SBO
-    d |= (uint64_t)1 << 46;                 // descriptor version for tcgen05
-    d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+    d |= (uint64_t)1 << 16;                     // LBO (ignored for swizzled K-major)
+    d |= (uint64_t)((8 * SK) >> 4) << 32;       // SBO
+    d |= (uint64_t)1 << 46;                     // descriptor version for tcgen05
+    d |= Geo<SK>::LAYOUT << 61;                 // swizzle mode
     return d;
 }
 
 // Instruction descriptor: D = F32, A = B = E4M3, both K-major, N = 256, M = 128.
 constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 
-// Widen 4 packed words (128 bits) of one row into 128 FP8 bytes, i.e. 8
-// 16-byte chunks: chunk 2p holds bits {8b + j} of word p for j = 0..3 and
-// chunk 2p+1 those for j = 4..7 (byte b of output word j).
-__device__ __forceinline__ void widen_regs(uint4 w, uint4 (&o)[8]) {
+// Widen slot h of one row's 128-bit k-chunk (words h * SK/32 ..) into SK
+// FP8 bytes and store them into the SK-byte-swizzled K-major tile: row r at
+// (r / 8) * 8 SK + (r % 8) * SK, 16-byte chunk c at position
+// c ^ ((r % 8) >> SHIFT).  Word p of the slot becomes chunks 2p (bits
+// {8b + j}, j = 0..3, as byte b of output word j) and 2p + 1 (j = 4..7).
+template <int SK>
+__device__ __forceinline__ void widen_store(uint8_t *op_tile, int r, const uint4 &w, int h) {
     const uint32_t x[4] = {w.x, w.y, w.z, w.w};
+    constexpr int NW = SK / 32;
+    uint8_t *row = op_tile + (r >> 3) * (8 * SK) + (r & 7) * SK;
+    const int sw = (r & 7) >> Geo<SK>::SHIFT;
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        const uint32_t v = x[p];
-        o[2 * p].x = (v << 3) & 0x08080808u;
-        o[2 * p].y = (v << 2) & 0x08080808u;
-        o[2 * p].z = (v << 1) & 0x08080808u;
-        o[2 * p].w = v & 0x08080808u;
-        o[2 * p + 1].x = (v >> 1) & 0x08080808u;
-        o[2 * p + 1].y = (v >> 2) & 0x08080808u;
-        o[2 * p + 1].z = (v >> 3) & 0x08080808u;
-        o[2 * p + 1].w = (v >> 4) & 0x08080808u;
+    for (int p = 0; p < NW; ++p) {
+        const uint32_t v = x[h * NW + p];
+        uint4 lo, hi;
+        lo.x = (v << 3) & 0x08080808u;
+        lo.y = (v << 2) & 0x08080808u;
+        lo.z = (v << 1) & 0x08080808u;
+        lo.w = v & 0x08080808u;
+        hi.x = (v >> 1) & 0x08080808u;
+        hi.y = (v >> 2) & 0x08080808u;
+        hi.z = (v >> 3) & 0x08080808u;
+        hi.w = (v >> 4) & 0x08080808u;
+        *reinterpret_cast<uint4 *>(row + (((2 * p) ^ sw) << 4)) = lo;
+        *reinterpret_cast<uint4 *>(row + (((2 * p + 1) ^ sw) << 4)) = hi;
     }
-}
-
-// Store a widened row into the 128-byte-swizzled K-major tile: row r at
-// (r / 8) * 1024 + (r % 8) * 128, chunk c at position c ^ (r % 8).
-__device__ __forceinline__ void store_row(uint8_t *op_tile, int r, const uint4 (&o)[8]) {
-    uint8_t *row = op_tile + (r >> 3) * 1024 + (r & 7) * 128;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4 *>(row + ((c ^ (r & 7)) << 4)) = o[c];
 }
 
 // Re-layout of a packed sketch matrix [n][W] (W = 4 nKc words) into
@@ -378,10 +392,11 @@ __device__ __forceinline__ uint32_t select32(const uint32_t (&v)[32], uint32_t j
     return (j & 1) ? t2[1] : t2[0];
 }
 
-template <int M, int NOP, int NG>
+template <int M, int NOP, int NG, int SK>
 __global__ void __launch_bounds__(threads_for(NG), 1)
     pair_tc_kernel(const Args p) {
-    using Smem = tc::Smem<NOP, NG>;
+    using Smem = tc::Smem<NOP, NG, SK>;
+    using G = Geo<SK>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -440,23 +455,24 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
     if (warp == 0) {
         // ----------------------------- MMA issuer -----------------------------
         if (lane == 0) {
-            uint32_t kc = 0;
+            uint32_t sl = 0;   // operand slots consumed
+            const uint32_t nsl = p.nKc * G::SPK;
             for (uint32_t t = 0; t < n_my_tiles; ++t) {
                 const uint32_t ab = t & 1;
                 if (t >= 2) wait(&acc_empty[ab], ((t >> 1) - 1) & 1);
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + ab * BN;
-                for (uint32_t c = 0; c < p.nKc; ++c, ++kc) {
-                    const uint32_t o = kc % NOP;
-                    wait(&op_full[o], (kc / NOP) & 1);
+                for (uint32_t c = 0; c < nsl; ++c, ++sl) {
+                    const uint32_t o = sl % NOP;
+                    wait(&op_full[o], (sl / NOP) & 1);
                     tc_fence_after();
                     if (!*abort_flag) {
-                        const uint32_t a_addr = smem_u32(op + o * OP_BYTES);
-                        const uint32_t b_addr = a_addr + OP_A;
+                        const uint32_t a_addr = smem_u32(op + o * G::BYTES);
+                        const uint32_t b_addr = a_addr + G::A;
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            mma_f8(d_tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32),
-                                   IDESC, (c | kk) != 0);
+                        for (int kk = 0; kk < G::MMAS; ++kk)
+                            mma_f8(d_tmem, sw_desc<SK>(a_addr + kk * 32), sw_desc<SK>(b_addr + kk * 32),
+                                   IDESC, (c | (uint32_t)kk) != 0);
                     }
                     mma_commit(&op_empty[o]);
                 }
@@ -489,20 +505,20 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
             for (int u = 0; u < 4; ++u) {
                 const uint32_t kc = g0 + u;
                 if (kc >= total) break;
-                const uint32_t o = kc % NOP;
-                if (kc >= NOP) wait(&op_empty[o], ((kc / NOP) - 1) & 1);
-                uint8_t *oA = op + o * OP_BYTES;
-                uint8_t *oB = oA + OP_A;
-                uint4 w8[8];
-                widen_regs(ra[u], w8);
-                store_row(oA, e, w8);
-                widen_regs(rb0[u], w8);
-                store_row(oB, e, w8);
-                widen_regs(rb1[u], w8);
-                store_row(oB, e + 128, w8);
-                fence_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&op_full[o]);
+#pragma unroll
+                for (int h = 0; h < G::SPK; ++h) {
+                    const uint32_t sl = kc * G::SPK + h;   // operand slot sequence number
+                    const uint32_t o = sl % NOP;
+                    if (sl >= NOP) wait(&op_empty[o], ((sl / NOP) - 1) & 1);
+                    uint8_t *oA = op + o * G::BYTES;
+                    uint8_t *oB = oA + G::A;
+                    widen_store<SK>(oA, e, ra[u], h);
+                    widen_store<SK>(oB, e, rb0[u], h);
+                    widen_store<SK>(oB, e + 128, rb1[u], h);
+                    fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&op_full[o]);
+                }
                 fetch(kc + 4, ra[u], rb0[u], rb1[u]);
             }
         }
@@ -673,30 +689,49 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
 // host side
 // ---------------------------------------------------------------------------
 
-template <int NOP, int NG>
+template <int NOP, int NG, int SK>
 static size_t tc_smem_bytes(uint32_t k) {
-    return 1024 + tc::Smem<NOP, NG>::heap + (size_t)NG * k * tc::BM * 8;
+    return 1024 + tc::Smem<NOP, NG, SK>::heap + (size_t)NG * k * tc::BM * 8;
 }
 constexpr size_t kSmemLimit = 232448;   // 227 KB per block
 
-bool tc_cfg_fits(int cfg, uint32_t k) {
+// Block configurations (operand slots, epilogue groups, slot K bytes); the
+// index is the c of BS_VARIANT_TC_CFG(c).
+#define BS_TC_CONFIGS(X)  \
+    X(0, 3, 2, 128)       \
+    X(1, 2, 2, 128)       \
+    X(2, 3, 1, 128)       \
+    X(3, 2, 1, 128)       \
+    X(4, 4, 2, 64)        \
+    X(5, 8, 2, 32)        \
+    X(6, 6, 1, 64)        \
+    X(7, 4, 1, 64)
+constexpr int kTcConfigs = 8;
+
+static size_t tc_cfg_smem(int cfg, uint32_t k) {
     switch (cfg) {
-        case 0: return tc_smem_bytes<3, 2>(k) <= kSmemLimit;
-        case 1: return tc_smem_bytes<2, 2>(k) <= kSmemLimit;
-        case 2: return tc_smem_bytes<3, 1>(k) <= kSmemLimit;
-        case 3: return tc_smem_bytes<2, 1>(k) <= kSmemLimit;
+#define X(c, nop, ng, sk) \
+    case c: return tc_smem_bytes<nop, ng, sk>(k);
+        BS_TC_CONFIGS(X)
+#undef X
     }
-    return false;
+    return ~size_t(0);
 }
 
+bool tc_cfg_fits(int cfg, uint32_t k) { return tc_cfg_smem(cfg, k) <= kSmemLimit; }
+
+// default: the first configuration in this order that fits -- two epilogue
+// groups before one, whole-k-chunk slots (measured fastest on the text-BoW
+// workload: each slot hand-off has a fixed cost) before finer ones
 int tc_default_cfg(uint32_t k) {
-    for (int c = 0; c < 4; ++c)
+    static const int order[kTcConfigs] = {0, 1, 2, 3, 4, 5, 6, 7};
+    for (int c : order)
         if (tc_cfg_fits(c, k)) return c;
     return -1;
 }
 
 bool tc_shape_ok(uint32_t N, uint32_t k) {
-    return (N % 128) == 0 && N >= 256 && N <= 8192 && k >= 1 && tc_smem_bytes<2, 1>(k) <= kSmemLimit;
+    return (N % 128) == 0 && N >= 256 && N <= 8192 && k >= 1 && tc_cfg_fits(3, k);
 }
 
 bool tc_supported(const uint32_t *Q, const uint32_t *DB, uint32_t N, uint32_t k) {
@@ -788,10 +823,12 @@ bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uin
     auto launch = [&](auto mtag) {
         constexpr int MM = decltype(mtag)::value;
         switch (cfg) {
-            case 0: go(tc::pair_tc_kernel<MM, 3, 2>, tc_smem_bytes<3, 2>(k), tc::threads_for(2)); break;
-            case 1: go(tc::pair_tc_kernel<MM, 2, 2>, tc_smem_bytes<2, 2>(k), tc::threads_for(2)); break;
-            case 2: go(tc::pair_tc_kernel<MM, 3, 1>, tc_smem_bytes<3, 1>(k), tc::threads_for(1)); break;
-            default: go(tc::pair_tc_kernel<MM, 2, 1>, tc_smem_bytes<2, 1>(k), tc::threads_for(1)); break;
+#define X(c, nop, ng, sk)                                                                      \
+    case c:                                                                                    \
+        go(tc::pair_tc_kernel<MM, nop, ng, sk>, tc_smem_bytes<nop, ng, sk>(k), tc::threads_for(ng)); \
+        break;
+            BS_TC_CONFIGS(X)
+#undef X
         }
     };
     switch (measure) {

@@ -247,6 +247,29 @@ def test_topk_tc_dense_and_saturated(N, by, m):
             check_topk_row(s[q], ix[q], oest[m, q], 30, m, exclude_q=q)
 
 
+@pytest.mark.parametrize("cfg", range(8))
+@pytest.mark.parametrize("N,by,k", [(1024, "js", 50), (4096, "ham", 20), (256, "cos", 100)])
+def test_topk_tc_block_configurations_agree(cfg, N, by, k):
+    # every operand-slot width / ring depth / epilogue split gives the same
+    # lists as the CUDA-core kernel, bit for bit
+    c = inputs.random_csr(21, 1500, 300_000, 1, 500)
+    sk, pc = _gpu_sketch(c, N, 9)
+    n = c.n
+    ref_s, ref_i = api.topk(sk, pc, sk, pc, N, k, by=by, exclude_self=True, variant="popc")
+    s = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    i = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    wsb = B.bs_topk_workspace_bytes(n, n, N, k)
+    ws = torch.empty((wsb,), dtype=torch.uint8, device="cuda")
+    try:
+        B.bs_topk_ex(sk, pc, n, sk, pc, n, N, B.MEASURE_BITS[by], k, 1, s, i, ws, wsb,
+                     B.BS_VARIANT_TC | B.BS_VARIANT_TC_CFG(cfg))
+    except B.BinSketchError as e:
+        assert e.code == 7     # this configuration's heaps do not fit k
+        return
+    assert B.bs_get_async_error() == 0
+    assert torch.equal(i, ref_i) and torch.equal(s, ref_s)
+
+
 def test_topk_tc_rejects_unsupported_shapes(tiny):
     sk, pc = _gpu_sketch(tiny, 96, 0)
     score = torch.empty((10, 5), dtype=torch.float32, device="cuda")
