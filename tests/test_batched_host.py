@@ -14,5 +14,7 @@ def test_autotuner_cache_roundtrip(tmp_path):
     t.save()
     assert json.load(open(p)) == {key: 34}
     assert Autotuner(cache_path=str(p)).table == {key: 34}
-    names = [n for n, _ in Autotuner.candidates()]
-    assert names == ["popc", "tc0", "tc1", "tc2", "tc3"]
+    cands = Autotuner.candidates()
+    assert [n for n, _ in cands] == ["popc"] + [f"tc{c}" for c in range(8)]
+    # variant codes: POPC, then TC with configuration bits (c + 1) << 4
+    assert cands[0][1] == 1 and [v for _, v in cands[1:]] == [2 | ((c + 1) << 4) for c in range(8)]
