@@ -593,6 +593,62 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------
+# ranking-quality evaluation (Experiment 2): thresholded retrieval vs exact
+# ----------------------------------------------------------------------------
+
+RANKING = dict(workload="ranking quality (Experiment 2): 90/10 split of the text-BoW corpus",
+               n=100_000, d=1_000_000, query_frac=0.1, Ns=[512, 1024, 2048, 4096],
+               measures=["js", "cos", "ip"])
+
+
+def run_ranking(args):
+    import torch
+
+    from paper_1910_04658_gb300 import binding as B, build, inputs, ranking
+
+    build.build()
+    B.lib()
+    torch.cuda.set_device(0)
+    csr = inputs.bow_corpus(seed=0, n=args.n)
+    ev_t0 = torch.cuda.Event(enable_timing=True)
+    ev_t1 = torch.cuda.Event(enable_timing=True)
+    ev_t0.record()
+    ev = ranking.Evaluation(csr, seed=0, query_frac=RANKING["query_frac"])
+    ev_t1.record()
+    ev_t1.synchronize()
+    exact_ms = ev_t0.elapsed_time(ev_t1)
+    pairs = ev.nq * ev.ndb
+    table, times = {}, {}
+    for N in RANKING["Ns"]:
+        ev.evaluate(N, RANKING["measures"])           # warm-up (kernel attributes, allocations)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        res = ev.evaluate(N, RANKING["measures"])
+        e1.record()
+        e1.synchronize()
+        times[N] = e0.elapsed_time(e1)
+        for m in RANKING["measures"]:
+            table[f"N={N} {m}"] = [
+                {"threshold": round(th, 4), "f1": r["f1"], "precision": r["precision"], "recall": r["recall"],
+                 "accuracy": r["accuracy"], "pooled_f1": r["pooled_f1"], "truth_pairs": r["truth_pairs"],
+                 "queries_with_truth": r["queries_with_truth"]}
+                for th, r in zip(res[m]["thresholds"], res[m]["metrics"])]
+    assert B.bs_get_async_error() == 0
+    N0 = RANKING["Ns"][-1]
+    value = pairs / (times[N0] / 1e3)
+    line = {
+        "metric": METRIC, "value": value,
+        "unit": "query x training pairs evaluated per second (sketch + 3 estimates + threshold sets)",
+        "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": times[N0], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32+f32 (exact side f64)", "data": "synthetic",
+        "config": dict(RANKING, n=csr.n, queries=ev.nq, training=ev.ndb, pairs=pairs),
+        "components": {"exact_counts_ms": exact_ms, "evaluate_ms_per_N": times,
+                       "max_inner_product": ev.max_inner_product(), "by_N_and_measure": table},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -605,7 +661,8 @@ def main():
                     help="skip the one-off CUDA-core variant launch reported for comparison")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"],
                     help="rows of the corpus (smaller only for profiling captures)")
-    ap.add_argument("--workload", choices=["bow", "serving", "batched", "learned"], default="bow")
+    ap.add_argument("--workload", choices=["bow", "serving", "batched", "learned", "ranking"],
+                    default="bow")
     ap.add_argument("--train-pairs", type=int, default=10_000_000)
     ap.add_argument("--heldout-pairs", type=int, default=1_000_000)
     ap.add_argument("--epochs", type=int, default=8)
@@ -622,6 +679,9 @@ def main():
         return
     if args.workload == "learned":
         run_learned(args)
+        return
+    if args.workload == "ranking":
+        run_ranking(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

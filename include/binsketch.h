@@ -334,6 +334,44 @@ bs_status bs_dense_pairs(uint32_t n_pairs, uint32_t N, uint32_t d, uint32_t size
 bs_status bs_estimate_counts(const uint32_t *counts, uint32_t n, uint32_t N, float *out,
                              bs_stream_t stream);
 
+/*
+ * Ranking-quality evaluation (Experiment 2, Sec. 4 "Ranking"): the ground
+ * truth of the uncompressed vectors and the retrieval sets at thresholds.
+ *
+ * bs_exact_counts -- exact |a AND b| for every pair (query row q, database row
+ * j) of two CSR batches (same layout as bs_sketch's input):
+ *  counts    uint32[nq][ndb] (device)
+ *  q_sizes   uint32[nq] distinct indices of each query row (may be NULL)
+ *  db_sizes  uint32[ndb] indices of each database row (may be NULL)
+ * Database rows must not repeat an index (query rows may).  d <=
+ * BS_EXACT_D_MAX: a query row is held as a d-bit bitmap in shared memory.
+ * Indices >= d and malformed offsets are reported as by bs_sketch.
+ */
+#define BS_EXACT_D_MAX 1572864u
+bs_status bs_exact_counts(const uint64_t *q_row_ptr, const uint32_t *q_col, uint32_t nq, uint64_t q_nnz,
+                          const uint64_t *db_row_ptr, const uint32_t *db_col, uint32_t ndb,
+                          uint64_t db_nnz, uint32_t d, uint32_t *counts, uint32_t *q_sizes,
+                          uint32_t *db_sizes, bs_stream_t stream);
+
+/*
+ * bs_threshold_eval -- for every query row q and threshold thr[t] (host
+ * array, 1 <= n_thresholds <= BS_EVAL_THRESHOLDS_MAX):
+ *   out[q][t][0] = |O|      database rows whose exact similarity `by` is at
+ *                           least thr[t] (BS_HAM: a distance at most thr[t])
+ *   out[q][t][1] = |O'|     rows whose estimate est[q][j] passes the same test
+ *   out[q][t][2] = |O n O'|
+ * The exact similarity is formed in FP64 from counts / q_sizes / db_sizes
+ * (IP = c, Ham = a + b - 2c, JS = c / (a + b - c) or 0 for an empty union,
+ * Cos = c / sqrt(a b) or 0), the estimate is widened to FP64, and both are
+ * compared with thr[t] in FP64.  est float[nq][ndb], counts uint32[nq][ndb]
+ * (device), out uint32[nq][n_thresholds][3] (device).
+ */
+#define BS_EVAL_THRESHOLDS_MAX 16
+bs_status bs_threshold_eval(const float *est, const uint32_t *counts, const uint32_t *q_sizes,
+                            const uint32_t *db_sizes, uint32_t nq, uint32_t ndb, uint32_t by,
+                            const double *thresholds, uint32_t n_thresholds, uint32_t *out,
+                            bs_stream_t stream);
+
 /* MLP parameters: BS_MLP_PARAMS floats laid out as W1[64][4], b1[64],
  * W2[64][64], b2[64], W3[4][64], b3[4].  The MLP refines the closed form:
  * inputs are the closed-form (n_a/4N, n_b/4N, IP/4N, log2(N)/16); outputs

@@ -3,7 +3,8 @@
 A plain restatement of BinSketch (arXiv 1910.04658) used to check the CUDA
 library: sketching (Definition "BinSketch", Sec. 3), the sketch counts and the
 estimators of Alg. 1-4 (Sec. 3.1-3.4), the ranking of Experiment 2 (Sec. 4) as
-a top-k, and exact similarities as ground truth.  Only ``tests/``, the smoke
+a top-k and as thresholded retrieval sets, and exact similarities as ground
+truth.  Only ``tests/``, the smoke
 check and the CPU-baseline leg of the benchmark may import this package; the
 product path never does.  It shares no code with the CUDA library.
 
@@ -193,6 +194,25 @@ def exact_pairs(row_ptr, col, pa, pb) -> np.ndarray:
     lib().bso_exact_pairs(_ptr(row_ptr, ctypes.c_uint64), _ptr(col, ctypes.c_uint32),
                           _ptr(pa, ctypes.c_uint32), _ptr(pb, ctypes.c_uint32), pa.shape[0],
                           _ptr(out, ctypes.c_double))
+    return out
+
+
+def threshold_sets(est, exact, thresholds, distance: bool = False) -> np.ndarray:
+    """Experiment 2 (Sec. 4, "Ranking"): for each query row q and threshold
+    thr, the ground-truth set O = {j : exact[q, j] >= thr} (a distance: <=),
+    the retrieved set O' = {j : est[q, j] >= thr} (<=), and their overlap.
+    Returns counts [nq][T][3] = (|O|, |O'|, |O n O'|); both sides are compared
+    with thr in FP64."""
+    est = np.asarray(est, np.float64)
+    exact = np.asarray(exact, np.float64)
+    out = np.zeros((est.shape[0], len(thresholds), 3), np.int64)
+    for t, thr in enumerate(thresholds):
+        thr = float(thr)
+        O = exact <= thr if distance else exact >= thr
+        R = est <= thr if distance else est >= thr
+        out[:, t, 0] = O.sum(1)
+        out[:, t, 1] = R.sum(1)
+        out[:, t, 2] = (O & R).sum(1)
     return out
 
 

@@ -36,6 +36,8 @@ class bs_sketch_job(ctypes.Structure):
 MEASURE_BITS = {"ip": BS_IP, "ham": BS_HAM, "js": BS_JS, "cos": BS_COS}
 BS_TOPK_K_MAX = 128
 BS_TOPK_MERGE_PARTS_MAX = 256
+BS_EXACT_D_MAX = 1572864
+BS_EVAL_THRESHOLDS_MAX = 16
 BS_TOPK_NOALLOC_SCRATCH_BYTES = 16 << 20
 BS_N_MAX = 65536
 STATUS = {0: "BS_OK", 1: "BS_ERR_INVALID_ARG", 2: "BS_ERR_INDEX_RANGE", 3: "BS_ERR_ROWPTR",
@@ -70,6 +72,9 @@ SIGNATURES = [
                                 _sz, _vp]),
     ("bs_topk_noalloc", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, _i32, _vp, _vp,
                                _vp]),
+    ("bs_exact_counts", _i32, [_vp, _vp, _u32, _u64, _vp, _vp, _u32, _u64, _u32, _vp, _vp, _vp, _vp]),
+    ("bs_threshold_eval", _i32, [_vp, _vp, _vp, _vp, _u32, _u32, _u32, ctypes.POINTER(ctypes.c_double),
+                                 _u32, _vp, _vp]),
     ("bs_dense_pairs", _i32, [_u32, _u32, _u32, _u32, _u32, _u64, _u64, _vp, _vp, _vp, _u32, _vp]),
     ("bs_estimate_counts", _i32, [_vp, _u32, _u32, _vp, _vp]),
     ("bs_mlp_prepare", _i32, [_vp, _vp, _u32, _u32, _vp, _vp, _vp]),
@@ -178,6 +183,20 @@ def bs_topk_merge(score_parts, idx_parts, parts, nQ, k, part_offset, by, score, 
     offs = None if part_offset is None else (_u32 * parts)(*[int(o) for o in part_offset])
     _check(lib().bs_topk_merge(_p(score_parts), _p(idx_parts), parts, nQ, k, offs, by, _p(score),
                                _p(idx), _s(stream)), "bs_topk_merge")
+
+
+def bs_exact_counts(q_row_ptr, q_col, nq, q_nnz, db_row_ptr, db_col, ndb, db_nnz, d, counts,
+                    q_sizes=None, db_sizes=None, stream=None):
+    _check(lib().bs_exact_counts(_p(q_row_ptr), _p(q_col), nq, q_nnz, _p(db_row_ptr), _p(db_col), ndb,
+                                 db_nnz, d, _p(counts), _p(q_sizes), _p(db_sizes), _s(stream)),
+           "bs_exact_counts")
+
+
+def bs_threshold_eval(est, counts, q_sizes, db_sizes, nq, ndb, by, thresholds, out, stream=None):
+    """thresholds: a sequence of floats (host)."""
+    th = (ctypes.c_double * len(thresholds))(*[float(t) for t in thresholds])
+    _check(lib().bs_threshold_eval(_p(est), _p(counts), _p(q_sizes), _p(db_sizes), nq, ndb, by, th,
+                                   len(thresholds), _p(out), _s(stream)), "bs_threshold_eval")
 
 
 def bs_topk_plan(nQ, nDB, N, k, variant=0, same_matrix=False):
