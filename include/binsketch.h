@@ -335,6 +335,23 @@ bs_status bs_estimate_counts(const uint32_t *counts, uint32_t n, uint32_t N, flo
                              bs_stream_t stream);
 
 /*
+ * bs_onehot_csr -- categorical front end (Sec. 1, "Extension for
+ * categorical data compression"): one-hot encoding of label-encoded rows into
+ * the CSR layout bs_sketch reads.
+ *  labels    uint32[n][F] (device): labels[i][f] in 0 .. m_f - 1
+ *  offsets   uint32[F + 1] (device), non-decreasing: feature f owns columns
+ *            offsets[f] .. offsets[f + 1] - 1 (m_f = offsets[f+1] - offsets[f]);
+ *            the binary dimension is d = offsets[F]
+ *  row_ptr   uint64[n + 1] out: row i starts at i * F
+ *  col       uint32[n * F] out: col[i * F + f] = offsets[f] + labels[i][f]
+ * The Hamming distance of two encoded rows is twice the number of features
+ * on which they differ.  A label >= m_f is written as 0 and reported
+ * (BS_ERR_INDEX_RANGE through bs_get_async_error).
+ */
+bs_status bs_onehot_csr(const uint32_t *labels, uint32_t n, uint32_t F, const uint32_t *offsets,
+                        uint64_t *row_ptr, uint32_t *col, bs_stream_t stream);
+
+/*
  * Ranking-quality evaluation (Experiment 2, Sec. 4 "Ranking"): the ground
  * truth of the uncompressed vectors and the retrieval sets at thresholds.
  *

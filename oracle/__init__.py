@@ -3,8 +3,8 @@
 A plain restatement of BinSketch (arXiv 1910.04658) used to check the CUDA
 library: sketching (Definition "BinSketch", Sec. 3), the sketch counts and the
 estimators of Alg. 1-4 (Sec. 3.1-3.4), the ranking of Experiment 2 (Sec. 4) as
-a top-k and as thresholded retrieval sets, and exact similarities as ground
-truth.  Only ``tests/``, the smoke
+a top-k and as thresholded retrieval sets, the categorical front end, and
+exact similarities as ground truth.  Only ``tests/``, the smoke
 check and the CPU-baseline leg of the benchmark may import this package; the
 product path never does.  It shares no code with the CUDA library.
 
@@ -214,6 +214,30 @@ def threshold_sets(est, exact, thresholds, distance: bool = False) -> np.ndarray
         out[:, t, 1] = R.sum(1)
         out[:, t, 2] = (O & R).sum(1)
     return out
+
+
+def categorical_distance(u, v) -> int:
+    """Sec. 1, categorical extension: the number of features on which the
+    categorical rows u and v differ (the sum over features of 1[u_i != v_i])."""
+    return sum(1 for a, b in zip(u, v) if a != b)
+
+
+def onehot(labels, cardinalities):
+    """One-hot encoding of label-encoded rows (Sec. 1, categorical extension):
+    feature f, label l -> binary column (m_0 + ... + m_{f-1}) + l.  Returns
+    (row_ptr, col, d) as a CSR batch."""
+    labels = np.asarray(labels)
+    n, F = labels.shape
+    starts = [0]
+    for m in cardinalities:
+        starts.append(starts[-1] + int(m))
+    row_ptr = np.zeros(n + 1, np.uint64)
+    cols = []
+    for i in range(n):
+        for f in range(F):
+            cols.append(starts[f] + int(labels[i, f]))
+        row_ptr[i + 1] = len(cols)
+    return row_ptr, np.array(cols, np.uint32), starts[-1]
 
 
 def theorem1_N(psi: float, rho: float) -> float:

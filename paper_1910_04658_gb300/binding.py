@@ -72,6 +72,7 @@ SIGNATURES = [
                                 _sz, _vp]),
     ("bs_topk_noalloc", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, _i32, _vp, _vp,
                                _vp]),
+    ("bs_onehot_csr", _i32, [_vp, _u32, _u32, _vp, _vp, _vp, _vp]),
     ("bs_exact_counts", _i32, [_vp, _vp, _u32, _u64, _vp, _vp, _u32, _u64, _u32, _vp, _vp, _vp, _vp]),
     ("bs_threshold_eval", _i32, [_vp, _vp, _vp, _vp, _u32, _u32, _u32, ctypes.POINTER(ctypes.c_double),
                                  _u32, _vp, _vp]),
@@ -183,6 +184,11 @@ def bs_topk_merge(score_parts, idx_parts, parts, nQ, k, part_offset, by, score, 
     offs = None if part_offset is None else (_u32 * parts)(*[int(o) for o in part_offset])
     _check(lib().bs_topk_merge(_p(score_parts), _p(idx_parts), parts, nQ, k, offs, by, _p(score),
                                _p(idx), _s(stream)), "bs_topk_merge")
+
+
+def bs_onehot_csr(labels, n, F, offsets, row_ptr, col, stream=None):
+    _check(lib().bs_onehot_csr(_p(labels), n, F, _p(offsets), _p(row_ptr), _p(col), _s(stream)),
+           "bs_onehot_csr")
 
 
 def bs_exact_counts(q_row_ptr, q_col, nq, q_nnz, db_row_ptr, db_col, ndb, db_nnz, d, counts,
