@@ -197,7 +197,10 @@ bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
  *   c = 2: 1 group,  3 slots x 128    c = 3: 1 group,  2 slots x 128
  *   c = 4: 2 groups, 4 slots x 64     c = 5: 2 groups, 8 slots x 32
  *   c = 6: 1 group,  6 slots x 64     c = 7: 1 group,  4 slots x 64
- * The default is the first that fits in the order 0, 1, ..., 7.
+ *   c = 8: 2 groups, 3 slots x 128, one heap per row shared by the groups
+ *   c = 9: 2 groups, 2 slots x 128, shared heap
+ * (otherwise each group keeps its own heap for its half of the columns).
+ * The default is the first that fits in the order 0, 1, ..., 9.
  * A configuration whose shared memory does not fit k returns
  * BS_ERR_UNSUPPORTED.  bs_topk_workspace_bytes() covers every variant.
  */

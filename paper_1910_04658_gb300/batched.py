@@ -11,7 +11,7 @@ top-k).  The job runs as:
 
 and the whole sequence is captured once into a CUDA graph, so one graph
 launch replays the job.  The autotuner times the candidate kernels
-(CUDA-core POPC, tensor-core configurations 0-7) on the dataset itself and
+(CUDA-core POPC, tensor-core configurations 0-9) on the dataset itself and
 caches the winner per (GPU, N, log2 n, k, measure) in a JSON file.  The
 candidates compute identical estimates, so tuning changes speed, never
 results.

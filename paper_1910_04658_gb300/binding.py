@@ -19,11 +19,11 @@ BS_VARIANT_AUTO, BS_VARIANT_POPC, BS_VARIANT_TC = 0, 1, 2
 VARIANTS = {"auto": 0, "popc": 1, "tc": 2}
 
 
-BS_TC_CONFIGS = 8
+BS_TC_CONFIGS = 10
 
 
 def BS_VARIANT_TC_CFG(c: int) -> int:
-    """Bits selecting tensor-core block configuration c (0..7) in bs_topk_ex's variant."""
+    """Bits selecting tensor-core block configuration c (0..9) in bs_topk_ex's variant."""
     return (c + 1) << 4
 
 

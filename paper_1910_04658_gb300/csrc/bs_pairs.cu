@@ -619,7 +619,7 @@ static bs_status topk_impl(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, 
     const int m = measure_code(by);
     const int tc_cfg = (int)((variant >> 4) & 15u) - 1;   // -1: default configuration
     variant &= 15u;
-    if (m < 0 || variant > BS_VARIANT_TC || tc_cfg > 7) return BS_ERR_INVALID_ARG;
+    if (m < 0 || variant > BS_VARIANT_TC || tc_cfg > 9) return BS_ERR_INVALID_ARG;
     if (nQ == 0) return BS_OK;
     if (!Q || !pcQ || !score || !idx) return BS_ERR_INVALID_ARG;
     if (nDB > 0 && (!DB || !pcDB)) return BS_ERR_INVALID_ARG;

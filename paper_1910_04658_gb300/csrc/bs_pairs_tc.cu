@@ -13,8 +13,11 @@
 // j, j+8, j+16, j+24), identically for both operands, which a dot product
 // does not see.
 //
-// Block (288 or 416 threads, one per SM; work item = 128 query rows x a range
-// of 256-row database tiles):
+// Block (288 or 416 threads, one per SM, persistent): the (128-row query
+// block, 256-row database tile) pairs are numbered row block by row block and
+// every block takes an equal contiguous range of them, so the work is even
+// across SMs whatever the shape; a row block cut between two blocks yields two
+// partial lists, merged by merge_topk_kernel.
 //   warp 0     TMEM owner (512 columns) and single-thread MMA issuer:
 //              4 x tcgen05.mma.kind::f8f6f4 (M=128, N=256, K=32) per 128-bit
 //              k-chunk, into one of two TMEM accumulators
@@ -83,7 +86,8 @@ struct Smem {
     static constexpr int col = op + NOP * Geo<SK>::BYTES;       // 2 x 2 x 256 floats
     static constexpr int bars = col + 2 * 2 * BN * 4;
     static constexpr int thr = bars + 256;                      // [NG][BM] key, idx, size
-    static constexpr int heap = thr + NG * BM * 12;
+    static constexpr int lock = thr + NG * BM * 12;             // [BM] shared-heap row locks
+    static constexpr int heap = lock + BM * 4;
     static_assert((2 * NOP + 4) * 8 + 8 <= 256, "barrier area");
 };
 
@@ -91,7 +95,8 @@ struct Args {
     const uint4 *Q, *DB;        // k-chunk-tiled sketches [ceil(n/128)][nKc][128] x 16 bytes
     const uint32_t *pcQ, *pcDB;
     uint32_t nQ, nDB, N, W, nKc, nSl;
-    uint32_t k, tiles_per_split, splits;
+    uint32_t k, splits;   // splits: parts of a row's list (merged after)
+    uint64_t units;    // row blocks x database tiles; block c covers [c U / G, (c + 1) U / G)
     int exclude_self;  // drop the pair q == self_off + j
     uint32_t self_off;
     float invL;        // 1 / ln(1 - 1/N)
@@ -378,6 +383,46 @@ __device__ __noinline__ RowState consider(RowState st, float *hkey, uint32_t *hi
     return st;
 }
 
+// Shared-heap variant: both epilogue groups insert into one heap per row,
+// serialised by a per-row lock (the two threads of a row sit in different
+// warps; within a warp every lane has its own row).  The root key is
+// published for the filters outside the lock: it only ever improves, so a
+// stale value admits more pairs, never fewer, and the exact test against the
+// root is repeated under the lock.  Returns the root key once the heap is
+// full, else -inf.
+template <int M>
+__device__ __noinline__ float consider_shared(float *hkey, uint32_t *hix, float *root_key, int *hsize,
+                                              unsigned int *lock, int t, uint32_t col, uint32_t c,
+                                              uint32_t b, uint32_t a, float lnA, float eff_k,
+                                              uint32_t N, float invL, int cap, unsigned int *err) {
+    const float lnB = M == M_COS ? row_log(b, N) : 0.0f;
+    const float key = rank_key<M>(a, b, c, N, lnA, lnB, invL);
+    if (!(key >= eff_k)) return eff_k;            // below the row's known root: cannot enter
+    uint32_t spins = 0;
+    while (atomicCAS(&lock[t], 0u, 1u) != 0u) {
+        if (++spins > (1u << 22)) {               // never expected: report, drop the pair
+            raise_error(err, BS_ERR_TIMEOUT);
+            return eff_k;
+        }
+    }
+    __threadfence_block();
+    Heap h;
+    h.key = hkey; h.ix = hix; h.t = t; h.size = hsize[t]; h.cap = cap;
+    float root = -INFINITY;
+    if (h.size < cap) {
+        h.push(key, col);
+        hsize[t] = h.size;
+        if (h.size == cap) root = h.k_at(0);
+    } else {
+        if (better(key, col, h.k_at(0), h.i_at(0))) h.replace_root(key, col);
+        root = h.k_at(0);
+    }
+    if (root != -INFINITY) *reinterpret_cast<volatile float *>(&root_key[t]) = root;
+    __threadfence_block();
+    atomicExch(&lock[t], 0u);
+    return root;
+}
+
 // v[j] for a per-lane index j, by a select tree over registers (no local memory)
 __device__ __forceinline__ uint32_t select32(const uint32_t (&v)[32], uint32_t j) {
     uint32_t t16[16], t8[8], t4[4], t2[2];
@@ -392,7 +437,7 @@ __device__ __forceinline__ uint32_t select32(const uint32_t (&v)[32], uint32_t j
     return (j & 1) ? t2[1] : t2[0];
 }
 
-template <int M, int NOP, int NG, int SK>
+template <int M, int NOP, int NG, int SK, bool SHARED>
 __global__ void __launch_bounds__(threads_for(NG), 1)
     pair_tc_kernel(const Args p) {
     using Smem = tc::Smem<NOP, NG, SK>;
@@ -410,14 +455,17 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
     float *thr_key = reinterpret_cast<float *>(base + Smem::thr);     // [NG][BM]
     uint32_t *thr_idx = reinterpret_cast<uint32_t *>(thr_key + NG * BM);
     int *heap_size = reinterpret_cast<int *>(thr_idx + NG * BM);
+    unsigned int *row_lock = reinterpret_cast<unsigned int *>(base + Smem::lock);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t row0 = blockIdx.x * BM;
+    // Persistent schedule: the (row block, database tile) pairs are numbered
+    // u = row_block * n_tiles + tile, and block c takes the contiguous range
+    // [c U / G, (c + 1) U / G).  A row block split between blocks yields one
+    // partial list per block ("part"), merged afterwards.
     const uint32_t n_tiles = (p.nDB + BN - 1) / BN;
-    uint32_t t_begin = blockIdx.y * p.tiles_per_split;
-    uint32_t t_end = min(n_tiles, t_begin + p.tiles_per_split);
-    if (t_begin > t_end) t_begin = t_end;
-    const uint32_t n_my_tiles = t_end - t_begin;
+    const uint64_t u_lo = p.units * blockIdx.x / gridDim.x;
+    const uint64_t u_hi = p.units * (blockIdx.x + 1) / gridDim.x;
+    const uint32_t n_my_tiles = (uint32_t)(u_hi - u_lo);
 
     if (tid == 0) {
         for (int i = 0; i < NOP; ++i) {
@@ -438,7 +486,9 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
     for (int i = tid; i < NG * BM; i += blockDim.x) {   // published thresholds start empty
         thr_key[i] = -INFINITY;
         thr_idx[i] = NO_IDX;
+        heap_size[i] = 0;
     }
+    for (int i = tid; i < BM; i += blockDim.x) row_lock[i] = 0u;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -487,11 +537,18 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
         const uint4 z = make_uint4(0, 0, 0, 0);
         const uint32_t total = n_my_tiles * p.nKc;
         // k-chunk g of this block's sweep: three 16-byte pieces
+        // fetch cursor (row block, tile, k-chunk) of the next k-chunk; fetch()
+        // is called for g = 0, 1, 2, ... in order, so it only ever steps
+        uint32_t f_rb = (uint32_t)(u_lo / n_tiles), f_tile = (uint32_t)(u_lo % n_tiles), f_kc = 0;
         auto fetch = [&](uint32_t g, uint4 &a_, uint4 &b0_, uint4 &b1_) {
             if (g < total) {
-                const uint32_t t = g / p.nKc, kc = g % p.nKc;
-                const uint32_t bb = 2 * (t_begin + t);
-                a_ = __ldg(p.Q + ((size_t)blockIdx.x * p.nKc + kc) * 128 + e);
+                const uint32_t rb = f_rb, kc = f_kc;
+                const uint32_t bb = 2 * f_tile;
+                if (++f_kc == p.nKc) {
+                    f_kc = 0;
+                    if (++f_tile == n_tiles) { f_tile = 0; ++f_rb; }
+                }
+                a_ = __ldg(p.Q + ((size_t)rb * p.nKc + kc) * 128 + e);
                 b0_ = bb < nblk_db ? __ldg(p.DB + ((size_t)bb * p.nKc + kc) * 128 + e) : z;
                 b1_ = bb + 1 < nblk_db ? __ldg(p.DB + ((size_t)(bb + 1) * p.nKc + kc) * 128 + e) : z;
             }
@@ -528,14 +585,11 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
         const int e = tid - 160 - 128 * grp;       // 0..127 within the group
         const int quarter = warp & 3;              // TMEM lanes this warp may access
         const int r = quarter * 32 + lane;         // row within the block
-        const uint32_t q = row0 + r;
-        const bool row_ok = q < p.nQ;
-        const uint32_t a = row_ok ? __ldg(p.pcQ + q) : 0u;
-        const uint32_t a_cl = a < p.N - 1 ? a : p.N - 1;
-        const float rc = row_const<M>((float)(p.N - a_cl), p.N);   // from A' >= 1
-        const float lnA = row_log(a, p.N);
-        const float Na = (float)(p.N - a);         // N - a (raw)
-        float *hkey = reinterpret_cast<float *>(base + Smem::heap) + (size_t)grp * p.k * BM * 2;
+        // row constants of the current row block (set at each segment start)
+        uint32_t q = 0, a = 0, rb = 0;
+        bool row_ok = false;
+        float rc = 0.0f, lnA = 0.0f, Na = 0.0f;
+        float *hkey = reinterpret_cast<float *>(base + Smem::heap) + (size_t)(SHARED ? 0 : grp) * p.k * BM * 2;
         uint32_t *hix = reinterpret_cast<uint32_t *>(hkey + (size_t)p.k * BM);
         constexpr int COLS = BN / NG;              // tile columns of this group
         RowState st;
@@ -545,8 +599,32 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
         RowFilter filt;
         filt.all = true; filt.c0 = filt.c1 = 0.f;
 
+        uint32_t tile = (uint32_t)(u_lo % n_tiles);   // tile of unit u_lo + t
+        rb = (uint32_t)(u_lo / n_tiles);
         for (uint32_t t = 0; t < n_my_tiles; ++t) {
-            const uint32_t tile = t_begin + t;
+            const uint64_t u = u_lo + t;
+            if (t > 0 && ++tile == n_tiles) { tile = 0; ++rb; }
+            if (t == 0 || tile == 0) {
+                // a new row block: its row constants, empty heaps, empty
+                // published thresholds (the other group reads them after the
+                // barrier below)
+                q = rb * BM + r;
+                row_ok = q < p.nQ;
+                a = row_ok ? __ldg(p.pcQ + q) : 0u;
+                const uint32_t a_cl = a < p.N - 1 ? a : p.N - 1;
+                rc = row_const<M>((float)(p.N - a_cl), p.N);   // from A' >= 1
+                lnA = row_log(a, p.N);
+                Na = (float)(p.N - a);                         // N - a (raw)
+                st.thr_k = -INFINITY; st.thr_i = NO_IDX; st.size = 0;
+                eff_k = -INFINITY; eff_i = NO_IDX;
+                filt.all = true; filt.c0 = filt.c1 = 0.f;
+                if (!SHARED || grp == 0) {
+                    thr_key[(SHARED ? 0 : grp) * BM + r] = -INFINITY;
+                    thr_idx[(SHARED ? 0 : grp) * BM + r] = NO_IDX;
+                    heap_size[(SHARED ? 0 : grp) * BM + r] = 0;
+                }
+                if (NG == 2) named_sync(5, 128 * NG);
+            }
             float *cv = colv + (t & 1) * 2 * BN;
             // per-column values of this group's columns (one per thread)
             for (int j = grp * COLS + e; j < (grp + 1) * COLS; j += 128) {
@@ -575,9 +653,13 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                 uint32_t v[32];
                 tmem_ld32_async(trow + ch * 32, v);
                 // the threshold to beat: this heap's root or the other group's
+                // (shared heap: the published root key, ties admitted)
                 float tk = st.thr_k;
                 uint32_t ti = st.thr_i;
-                if (NG == 2) {
+                if (SHARED) {
+                    tk = *reinterpret_cast<volatile float *>(&thr_key[r]);
+                    ti = tk == -INFINITY ? NO_IDX : 0xFFFFFFFEu;
+                } else if (NG == 2) {
                     const float ok = thr_key[(1 - grp) * BM + r];
                     const uint32_t oi = thr_idx[(1 - grp) * BM + r];
                     if (better(ok, oi, tk, ti)) { tk = ok; ti = oi; }
@@ -618,16 +700,23 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                         mask &= mask - 1;
                         const uint32_t c = (uint32_t)(__uint_as_float(select32(v, jj)) * 4096.0f);
                         const int j = ch * 32 + (int)jj;
-                        st = consider<M>(st, hkey, hix, r, col_c + jj, c, (uint32_t)cv[j], a, lnA,
-                                         eff_k, eff_i, p.N, p.invL, (int)p.k);
-                        if (st.thr_i != NO_IDX && better(st.thr_k, st.thr_i, eff_k, eff_i)) {
-                            eff_k = st.thr_k; eff_i = st.thr_i;
+                        if (SHARED) {
+                            const float root = consider_shared<M>(hkey, hix, thr_key, heap_size, row_lock, r,
+                                                                  col_c + jj, c, (uint32_t)cv[j], a, lnA, eff_k,
+                                                                  p.N, p.invL, (int)p.k, p.err);
+                            if (root > eff_k) { eff_k = root; eff_i = 0xFFFFFFFEu; }
+                        } else {
+                            st = consider<M>(st, hkey, hix, r, col_c + jj, c, (uint32_t)cv[j], a, lnA,
+                                             eff_k, eff_i, p.N, p.invL, (int)p.k);
+                            if (st.thr_i != NO_IDX && better(st.thr_k, st.thr_i, eff_k, eff_i)) {
+                                eff_k = st.thr_k; eff_i = st.thr_i;
+                            }
                         }
                     }
                 }
                 // publish a changed root to the other group
-                if (NG == 2 && (st.size != size_before || st.thr_i != root_before ||
-                                st.thr_k != rootk_before)) {
+                if (!SHARED && NG == 2 && (st.size != size_before || st.thr_i != root_before ||
+                                           st.thr_k != rootk_before)) {
                     thr_key[grp * BM + r] = st.thr_k;
                     thr_idx[grp * BM + r] = st.thr_i;
                 }
@@ -636,42 +725,61 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[ab]);
-        }
-        // sort each heap best first; with two groups the first merges both lists
-        Heap h;
-        h.key = hkey; h.ix = hix; h.t = r; h.size = st.size; h.cap = (int)p.k;
-        if (row_ok) h.sort_best_first();
-        if (NG == 2) {
-            heap_size[grp * BM + r] = st.size;
-            named_sync(4, 128 * NG);
-        }
-        if (grp == 0 && row_ok) {
-            const float *k1 = reinterpret_cast<float *>(base + Smem::heap) + (size_t)p.k * BM * 2;
-            const uint32_t *i1 = reinterpret_cast<const uint32_t *>(k1 + (size_t)p.k * BM);
-            const int n0 = st.size, n1 = NG == 2 ? heap_size[BM + r] : 0;
-            int x = 0, y = 0;
-            for (int s = 0; s < (int)p.k; ++s) {
-                float kk = -INFINITY;
-                uint32_t ii = NO_IDX;
-                const bool hx = x < n0, hy = y < n1;
-                if (hx || hy) {
-                    const float xk = hx ? h.k_at(x) : -INFINITY;
-                    const uint32_t xi = hx ? h.i_at(x) : NO_IDX;
-                    const float yk = hy ? k1[y * BM + r] : -INFINITY;
-                    const uint32_t yi = hy ? i1[y * BM + r] : NO_IDX;
-                    if (hx && (!hy || better(xk, xi, yk, yi))) { kk = xk; ii = xi; ++x; }
-                    else { kk = yk; ii = yi; ++y; }
+            if (t + 1 < n_my_tiles && tile + 1 < n_tiles) continue;
+            // ---- end of this row block's segment: its list for part `part`
+            const uint64_t x0 = u - tile;   // first unit of this row block
+            const uint32_t part = blockIdx.x - (uint32_t)(((x0 + 1) * gridDim.x - 1) / p.units);
+            // sort each heap best first; with two groups the first merges both lists
+            // (shared heap: one list, sorted by the first group once both are done)
+            if (SHARED && NG == 2) named_sync(4, 128 * NG);
+            if (SHARED) st.size = heap_size[r];
+            Heap h;
+            h.key = hkey; h.ix = hix; h.t = r; h.size = st.size; h.cap = (int)p.k;
+            if (row_ok && (!SHARED || grp == 0)) h.sort_best_first();
+            if (!SHARED && NG == 2) {
+                heap_size[grp * BM + r] = st.size;
+                named_sync(4, 128 * NG);
+            }
+            if (grp == 0 && row_ok) {
+                const float *k1 = reinterpret_cast<float *>(base + Smem::heap) + (size_t)p.k * BM * 2;
+                const uint32_t *i1 = reinterpret_cast<const uint32_t *>(k1 + (size_t)p.k * BM);
+                const int n0 = st.size, n1 = (!SHARED && NG == 2) ? heap_size[BM + r] : 0;
+                int x = 0, y = 0;
+                for (int s = 0; s < (int)p.k; ++s) {
+                    float kk = -INFINITY;
+                    uint32_t ii = NO_IDX;
+                    const bool hx = x < n0, hy = y < n1;
+                    if (hx || hy) {
+                        const float xk = hx ? h.k_at(x) : -INFINITY;
+                        const uint32_t xi = hx ? h.i_at(x) : NO_IDX;
+                        const float yk = hy ? k1[y * BM + r] : -INFINITY;
+                        const uint32_t yi = hy ? i1[y * BM + r] : NO_IDX;
+                        if (hx && (!hy || better(xk, xi, yk, yi))) { kk = xk; ii = xi; ++x; }
+                        else { kk = yk; ii = yi; ++y; }
+                    }
+                    if (p.splits == 1) {
+                        const size_t o = (size_t)q * p.k + s;
+                        p.score[o] = M == M_HAM ? -kk : kk;
+                        p.idx[o] = ii;
+                    } else {
+                        const size_t o = ((size_t)part * p.nQ + q) * p.k + s;
+                        p.ws_key[o] = kk;
+                        p.ws_idx[o] = ii;
+                    }
                 }
-                if (p.splits == 1) {
-                    const size_t o = (size_t)q * p.k + s;
-                    p.score[o] = M == M_HAM ? -kk : kk;
-                    p.idx[o] = ii;
-                } else {
-                    const size_t o = ((size_t)blockIdx.y * p.nQ + q) * p.k + s;
-                    p.ws_key[o] = kk;
-                    p.ws_idx[o] = ii;
+                // the block holding a row block's last tile also writes empty
+                // lists for the part slots this row block does not use
+                if (p.splits > 1 && tile + 1 == n_tiles) {
+                    for (uint32_t pp = part + 1; pp < p.splits; ++pp)
+                        for (int s = 0; s < (int)p.k; ++s) {
+                            const size_t o = ((size_t)pp * p.nQ + q) * p.k + s;
+                            p.ws_key[o] = -INFINITY;
+                            p.ws_idx[o] = NO_IDX;
+                        }
                 }
             }
+            // every heap read of this segment is done before the next one resets them
+            if (NG == 2) named_sync(6, 128 * NG);
         }
     }
 
@@ -689,29 +797,32 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
 // host side
 // ---------------------------------------------------------------------------
 
-template <int NOP, int NG, int SK>
+template <int NOP, int NG, int SK, bool SH>
 static size_t tc_smem_bytes(uint32_t k) {
-    return 1024 + tc::Smem<NOP, NG, SK>::heap + (size_t)NG * k * tc::BM * 8;
+    return 1024 + tc::Smem<NOP, NG, SK>::heap + (size_t)(SH ? 1 : NG) * k * tc::BM * 8;
 }
 constexpr size_t kSmemLimit = 232448;   // 227 KB per block
 
-// Block configurations (operand slots, epilogue groups, slot K bytes); the
-// index is the c of BS_VARIANT_TC_CFG(c).
-#define BS_TC_CONFIGS(X)  \
-    X(0, 3, 2, 128)       \
-    X(1, 2, 2, 128)       \
-    X(2, 3, 1, 128)       \
-    X(3, 2, 1, 128)       \
-    X(4, 4, 2, 64)        \
-    X(5, 8, 2, 32)        \
-    X(6, 6, 1, 64)        \
-    X(7, 4, 1, 64)
-constexpr int kTcConfigs = 8;
+// Block configurations (operand slots, epilogue groups, slot K bytes, one
+// heap per row shared by the groups); the index is the c of
+// BS_VARIANT_TC_CFG(c).
+#define BS_TC_CONFIGS(X)         \
+    X(0, 3, 2, 128, false)       \
+    X(1, 2, 2, 128, false)       \
+    X(2, 3, 1, 128, false)       \
+    X(3, 2, 1, 128, false)       \
+    X(4, 4, 2, 64, false)        \
+    X(5, 8, 2, 32, false)        \
+    X(6, 6, 1, 64, false)        \
+    X(7, 4, 1, 64, false)        \
+    X(8, 3, 2, 128, true)        \
+    X(9, 2, 2, 128, true)
+constexpr int kTcConfigs = 10;
 
 static size_t tc_cfg_smem(int cfg, uint32_t k) {
     switch (cfg) {
-#define X(c, nop, ng, sk) \
-    case c: return tc_smem_bytes<nop, ng, sk>(k);
+#define X(c, nop, ng, sk, sh) \
+    case c: return tc_smem_bytes<nop, ng, sk, sh>(k);
         BS_TC_CONFIGS(X)
 #undef X
     }
@@ -724,7 +835,7 @@ bool tc_cfg_fits(int cfg, uint32_t k) { return tc_cfg_smem(cfg, k) <= kSmemLimit
 // groups before one, whole-k-chunk slots (measured fastest on the text-BoW
 // workload: each slot hand-off has a fixed cost) before finer ones
 int tc_default_cfg(uint32_t k) {
-    static const int order[kTcConfigs] = {0, 1, 2, 3, 4, 5, 6, 7};
+    static const int order[kTcConfigs] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9};
     for (int c : order)
         if (tc_cfg_fits(c, k)) return c;
     return -1;
@@ -739,26 +850,28 @@ bool tc_supported(const uint32_t *Q, const uint32_t *DB, uint32_t N, uint32_t k)
            (reinterpret_cast<uintptr_t>(DB) & 15u) == 0;
 }
 
-// Database splits for the tensor-core top-k: the fewest (row block, split)
-// work items whose last wave of one-block-per-SM launches is at least 90%
-// full (else the best fill found), each split keeping at least 4 tiles.
+// Persistent schedule of the tensor-core top-k: one block per SM (at most one
+// per unit), block c taking units [c U / G, (c + 1) U / G) of the U = row
+// blocks x database tiles.  Returns the most blocks any row block is spread
+// over: the number of partial lists per row to merge (1: none).
+static uint32_t tc_blocks(uint64_t units) {
+    const uint64_t sms = (uint64_t)sm_count();
+    return (uint32_t)(units < sms ? units : sms);
+}
+
 uint32_t tc_splits(uint32_t nQ, uint32_t nDB) {
-    const uint32_t rb = (nQ + tc::BM - 1) / tc::BM;
-    const uint32_t tiles = (nDB + tc::BN - 1) / tc::BN;
-    if (rb == 0 || tiles == 0) return 1;
-    const uint32_t sms = (uint32_t)sm_count();
-    const uint32_t s_max = tiles / 4 > 1 ? (tiles / 4 < 4096 ? tiles / 4 : 4096) : 1;
-    uint32_t best = 1;
-    double best_eff = -1.0;
-    for (uint32_t s = 1; s <= s_max; ++s) {
-        const uint32_t per = (tiles + s - 1) / s;
-        if ((tiles + per - 1) / per != s) continue;     // only exact split counts
-        const double waves = (double)rb * s / sms;
-        const double eff = waves / ceil(waves);
-        if (eff >= 0.9) return s;
-        if (eff > best_eff) { best_eff = eff; best = s; }
+    const uint64_t rbs = (nQ + tc::BM - 1) / tc::BM;
+    const uint64_t T = (nDB + tc::BN - 1) / tc::BN;
+    const uint64_t U = rbs * T;
+    if (U == 0) return 1;
+    const uint64_t G = tc_blocks(U);
+    auto first = [&](uint64_t x) { return ((x + 1) * G - 1) / U; };   // block holding unit x
+    uint64_t parts = 1;
+    for (uint64_t rb = 0; rb < rbs; ++rb) {
+        const uint64_t n = first(rb * T + T - 1) - first(rb * T) + 1;
+        if (n > parts) parts = n;
     }
-    return best;
+    return (uint32_t)parts;
 }
 
 size_t tc_tiled_bytes(uint32_t n, uint32_t N) {
@@ -804,12 +917,13 @@ bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uin
     p.nSl = (nKc + 1) / 2;
     p.k = k; p.exclude_self = exclude_self; p.self_off = self_off; p.splits = splits;
     const uint32_t tiles = (nDB + tc::BN - 1) / tc::BN;
-    p.tiles_per_split = (tiles + splits - 1) / splits;
+    p.units = (uint64_t)((nQ + tc::BM - 1) / tc::BM) * tiles;
     p.invL = (float)(1.0 / log1p(-1.0 / (double)N));
     p.log2N = (float)log2((double)N);
     p.lnN = (float)log((double)N);
     p.score = score; p.idx = idx; p.ws_key = ws_key; p.ws_idx = ws_idx; p.err = err;
-    dim3 grid((nQ + tc::BM - 1) / tc::BM, splits);
+    if (p.units == 0) return BS_OK;
+    dim3 grid(tc_blocks(p.units));
     // two epilogue groups when two heaps per row fit, three operand slots
     // when there is room left (configuration order: most parallel first)
     const int cfg = cfg_req >= 0 ? cfg_req : tc_default_cfg(k);
@@ -823,9 +937,9 @@ bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uin
     auto launch = [&](auto mtag) {
         constexpr int MM = decltype(mtag)::value;
         switch (cfg) {
-#define X(c, nop, ng, sk)                                                                      \
-    case c:                                                                                    \
-        go(tc::pair_tc_kernel<MM, nop, ng, sk>, tc_smem_bytes<nop, ng, sk>(k), tc::threads_for(ng)); \
+#define X(c, nop, ng, sk, sh)                                                                      \
+    case c:                                                                                        \
+        go(tc::pair_tc_kernel<MM, nop, ng, sk, sh>, tc_smem_bytes<nop, ng, sk, sh>(k), tc::threads_for(ng)); \
         break;
             BS_TC_CONFIGS(X)
 #undef X

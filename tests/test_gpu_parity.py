@@ -247,8 +247,8 @@ def test_topk_tc_dense_and_saturated(N, by, m):
             check_topk_row(s[q], ix[q], oest[m, q], 30, m, exclude_q=q)
 
 
-@pytest.mark.parametrize("cfg", range(8))
-@pytest.mark.parametrize("N,by,k", [(1024, "js", 50), (4096, "ham", 20), (256, "cos", 100)])
+@pytest.mark.parametrize("cfg", range(10))
+@pytest.mark.parametrize("N,by,k", [(1024, "js", 50), (4096, "ham", 20), (256, "cos", 100), (2048, "ip", 1)])
 def test_topk_tc_block_configurations_agree(cfg, N, by, k):
     # every operand-slot width / ring depth / epilogue split gives the same
     # lists as the CUDA-core kernel, bit for bit
