@@ -201,6 +201,10 @@ bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
  *   c = 9: 2 groups, 2 slots x 128, shared heap
  * (otherwise each group keeps its own heap for its half of the columns).
  * The default is the first that fits in the order 0, 1, ..., 9.
+ * Environment: for calls that pass BS_VARIANT_AUTO (bs_topk among them) the
+ * variable BS_VARIANT, read once, overrides the choice: "popc" forces the
+ * CUDA-core kernel, "tc<c>" selects configuration c wherever the tensor-core
+ * kernel applies and c fits k.
  * A configuration whose shared memory does not fit k returns
  * BS_ERR_UNSUPPORTED.  bs_topk_workspace_bytes() covers every variant.
  */

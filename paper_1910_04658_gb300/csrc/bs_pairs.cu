@@ -15,6 +15,10 @@
 // reaches HBM.  When few query tiles exist the database is split across
 // blocks and a second kernel merges the per-split top-k lists.
 #include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
 
 #include "bs_internal.cuh"
 
@@ -609,6 +613,23 @@ size_t bs_topk_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k
     return need;
 }
 
+// Kernel choice forced by the environment for calls that leave it to the
+// library (BS_VARIANT_AUTO): BS_VARIANT=popc forces the CUDA-core kernel,
+// BS_VARIANT=tc<c> (c = 0..9) picks tensor-core configuration c where the
+// tensor-core kernel applies.  Read once.  Returns -2: not set, -1: POPC,
+// c >= 0: configuration c.
+static int env_variant() {
+    static std::once_flag once;
+    static int v = -2;
+    std::call_once(once, [] {
+        const char *e = getenv("BS_VARIANT");
+        if (!e) return;
+        if (!strcmp(e, "popc")) v = -1;
+        else if (e[0] == 't' && e[1] == 'c' && e[2] >= '0' && e[2] <= '9' && e[3] == 0) v = e[2] - '0';
+    });
+    return v;
+}
+
 static bs_status topk_impl(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
                            const uint32_t *pcDB, uint32_t nDB, uint32_t N, uint32_t by, uint32_t k,
                            int exclude_self, uint32_t self_off, float *score, uint32_t *idx,
@@ -617,9 +638,14 @@ static bs_status topk_impl(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, 
     if (!valid_N(N)) return BS_ERR_INVALID_ARG;
     if (k == 0 || k > BS_TOPK_K_MAX) return BS_ERR_INVALID_ARG;
     const int m = measure_code(by);
-    const int tc_cfg = (int)((variant >> 4) & 15u) - 1;   // -1: default configuration
+    int tc_cfg = (int)((variant >> 4) & 15u) - 1;   // -1: default configuration
     variant &= 15u;
     if (m < 0 || variant > BS_VARIANT_TC || tc_cfg > 9) return BS_ERR_INVALID_ARG;
+    if (variant == BS_VARIANT_AUTO && tc_cfg < 0) {
+        const int ev = env_variant();
+        if (ev == -1) variant = BS_VARIANT_POPC;
+        else if (ev >= 0 && tc_cfg_fits(ev, k)) tc_cfg = ev;
+    }
     if (nQ == 0) return BS_OK;
     if (!Q || !pcQ || !score || !idx) return BS_ERR_INVALID_ARG;
     if (nDB > 0 && (!DB || !pcDB)) return BS_ERR_INVALID_ARG;
@@ -696,6 +722,7 @@ bs_status bs_topk_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, uint32
     if (!valid_N(N) || k == 0 || k > BS_TOPK_K_MAX || variant > BS_VARIANT_TC)
         return BS_ERR_INVALID_ARG;
     bool tc = false;
+    if (variant == BS_VARIANT_AUTO && env_variant() == -1) variant = BS_VARIANT_POPC;
     if (variant == BS_VARIANT_TC) {
         if (nDB == 0 || !tc_shape_ok(N, k)) return BS_ERR_UNSUPPORTED;
         tc = true;

@@ -90,6 +90,7 @@ class MLPEstimator:
         steps_per_epoch = (n + batch - 1) // batch
         total = epochs * steps_per_epoch
         hist = []
+        done = 0   # steps of this call (the Adam step count self.step runs on across calls)
         for ep in range(epochs):
             perm = torch.randperm(n, generator=g, device=self.device)
             Xp, Tp = X[perm].contiguous(), T[perm].contiguous()
@@ -98,8 +99,9 @@ class MLPEstimator:
                 a = i * batch
                 b = min(n, a + batch)
                 self.step += 1
-                # cosine decay of the step size
-                frac = (self.step - 1) / max(1, total)
+                # cosine decay of the step size over this call's steps
+                frac = done / max(1, total)
+                done += 1
                 rate = lr * 0.5 * (1 + np.cos(np.pi * min(frac, 1.0)))
                 B.bs_mlp_train_step(self.params, self.m, self.v, self.grad, self.step, float(rate),
                                     Xp[a:b], Tp[a:b], b - a, self.loss)

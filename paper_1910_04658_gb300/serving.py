@@ -284,6 +284,26 @@ class SketchDB:
         self.tiled = torch.empty((B.bs_tiled_bytes(n, N),), dtype=torch.uint8, device=dev)
         B.bs_tile_sketches(self.sketch, n, N, self.tiled, stream)
 
+    def save(self, path: str) -> None:
+        """Write the sketches with their (N, seed) (checkpoint.py format)."""
+        from . import checkpoint
+        checkpoint.save_sketches(path, self.sketch, self.pc, self.N, self.seed, self.d)
+
+    @classmethod
+    def load(cls, path: str, device: str = "cuda", expect_N: int = None, expect_seed: int = None,
+             stream=None) -> "SketchDB":
+        """A database from a checkpoint, re-tiled for the tensor-core search;
+        refuses one sketched with another (N, seed) than expected."""
+        import torch
+        from . import binding as B, checkpoint
+        sk, pc, meta = checkpoint.load_sketches(path, device, expect_N, expect_seed)
+        db = cls.__new__(cls)
+        db.n, db.d, db.N, db.seed = meta.n, meta.d, meta.N, meta.seed
+        db.sketch, db.pc = sk, pc
+        db.tiled = torch.empty((B.bs_tiled_bytes(db.n, db.N),), dtype=torch.uint8, device=device)
+        B.bs_tile_sketches(db.sketch, db.n, db.N, db.tiled, stream)
+        return db
+
 
 class GpuExecutor(Executor):
     """Runs a micro-batch on its slot's stream: pinned-host CSR in, sketch,

@@ -35,3 +35,19 @@ def test_host_only_calls():
     # the library's SplitMix64 seeding agrees with the oracle's own implementation
     for seed in (0, 1, 2**40 + 3, 2**64 - 1):
         assert binding.bs_hash_params(seed) == oracle.hash_params(seed)
+
+
+def test_env_variant_override_in_plan():
+    # bs_topk_plan is host-only: the environment override is visible without a GPU
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, '.'); "
+            "from paper_1910_04658_gb300 import binding as B; "
+            "print(int(B.bs_topk_plan(100000, 100000, 4096, 50, 0, True)[0]))")
+    env = dict(__import__("os").environ)
+    env.pop("BS_VARIANT", None)
+    root = __import__("os").path.dirname(__import__("os").path.dirname(__import__("os").path.abspath(__file__)))
+    plain = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=root)
+    env["BS_VARIANT"] = "popc"
+    forced = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=root)
+    assert plain.stdout.strip() == "1" and forced.stdout.strip() == "0", (plain.stderr, forced.stderr)
