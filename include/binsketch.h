@@ -316,7 +316,7 @@ bs_status bs_topk_noalloc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
 /*
  * Learned estimator.  The paper estimates with the closed form of Alg. 1-4;
  * near saturation (|a_s| close to N) that inversion loses accuracy.  These
- * calls train and run a small MLP (4 -> 64 -> 64 -> 4, GELU, weights and
+ * calls train and run a small MLP (4 -> 64 -> 64 -> 4, GELU in its tanh form, weights and
  * activations rounded to BF16, FP32 accumulation) on sketch pairs that
  * BinSketch itself produces, as an alternative estimator for that regime;
  * the closed form stays the reference.
@@ -417,7 +417,13 @@ bs_status bs_mlp_train_step(float *params, float *adam_m, float *adam_v, float *
                             float lr, const float *x, const float *t, uint32_t n, float *loss,
                             bs_stream_t stream);
 
-/* bs_mlp_estimate -- the MLP's IP, Ham, JS, Cos of counts[n][3]; out float[n][4]. */
+/* bs_mlp_estimate -- the MLP's IP, Ham, JS, Cos of counts[n][3]; out float[n][4].
+ * The 64 x 64 hidden layer runs on the tensor cores (tcgen05.mma kind::f16,
+ * BF16 operands, FP32 accumulation); bs_mlp_estimate_ex with variant
+ * BS_VARIANT_POPC runs every layer on the CUDA cores instead (same results up
+ * to the order of FP32 sums), BS_VARIANT_AUTO / BS_VARIANT_TC the former. */
+bs_status bs_mlp_estimate_ex(const float *params, const uint32_t *counts, uint32_t n, uint32_t N,
+                             float *out, uint32_t variant, bs_stream_t stream);
 bs_status bs_mlp_estimate(const float *params, const uint32_t *counts, uint32_t n, uint32_t N, float *out,
                           bs_stream_t stream);
 

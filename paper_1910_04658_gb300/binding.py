@@ -81,6 +81,7 @@ SIGNATURES = [
     ("bs_mlp_prepare", _i32, [_vp, _vp, _u32, _u32, _vp, _vp, _vp]),
     ("bs_mlp_train_step", _i32, [_vp, _vp, _vp, _vp, _u32, ctypes.c_float, _vp, _vp, _u32, _vp, _vp]),
     ("bs_mlp_estimate", _i32, [_vp, _vp, _u32, _u32, _vp, _vp]),
+    ("bs_mlp_estimate_ex", _i32, [_vp, _vp, _u32, _u32, _vp, _u32, _vp]),
     ("bs_get_async_error", _i32, [_vp]),
     ("bs_hash_params", None, [_u64, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     ("bs_status_string", ctypes.c_char_p, [_i32]),
@@ -264,6 +265,11 @@ def bs_mlp_train_step(params, adam_m, adam_v, grad, step, lr, x, t, n, loss=None
 def bs_mlp_estimate(params, counts, n, N, out, stream=None):
     _check(lib().bs_mlp_estimate(_p(params), _p(counts), n, N, _p(out), _s(stream)),
            "bs_mlp_estimate")
+
+
+def bs_mlp_estimate_ex(params, counts, n, N, out, variant=0, stream=None):
+    _check(lib().bs_mlp_estimate_ex(_p(params), _p(counts), n, N, _p(out), variant, _s(stream)),
+           "bs_mlp_estimate_ex")
 
 
 def bs_get_async_error(stream=None) -> int:

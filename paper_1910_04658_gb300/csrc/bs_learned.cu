@@ -15,7 +15,7 @@
 //    sizes -- and so the exact IP, Ham, JS, Cos -- are known by construction.
 //  * bs_mlp_*: a 4 -> 64 -> 64 -> 4 MLP that corrects the closed form (its
 //    inputs are the closed-form n_a, n_b and IP, its outputs are added to the
-//    closed-form estimates), with GELU, weights and activations
+//    closed-form estimates), with GELU (tanh form), weights and activations
 //    rounded to BF16, products accumulated in FP32; a fused training step
 //    (forward and backward of 128 samples per block in shared memory, block
 //    gradient sums added to a global buffer) followed by Adam on FP32 master
@@ -37,11 +37,27 @@ static_assert(NPARAM == BS_MLP_PARAMS, "parameter count");
 constexpr int TB = 128;   // samples (threads) per training block
 
 __device__ __forceinline__ float bf(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118f)); }
+// GELU in the tanh form of Hendrycks and Gimpel (2016):
+//   gelu(z) = z/2 (1 + tanh(u)),  u = sqrt(2/pi) (z + 0.044715 z^3)
+constexpr float kGeluC = 0.7978845608f;   // sqrt(2 / pi)
+constexpr float kGeluA = 0.044715f;
+__device__ __forceinline__ float gelu(float z) {
+    const float u = kGeluC * fmaf(kGeluA * z * z, z, z);
+    return 0.5f * z * (1.0f + tanhf(u));
+}
+// d gelu / dz = (1 + t)/2 + z/2 (1 - t^2) sqrt(2/pi) (1 + 3 a z^2),  t = tanh(u)
 __device__ __forceinline__ float gelu_grad(float z) {
-    const float cdf = 0.5f * (1.0f + erff(z * 0.70710678118f));
-    const float pdf = 0.3989422804f * expf(-0.5f * z * z);
-    return cdf + z * pdf;
+    const float u = kGeluC * fmaf(kGeluA * z * z, z, z);
+    const float t = tanhf(u);
+    return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * kGeluC * fmaf(3.0f * kGeluA, z * z, 1.0f);
+}
+// the same with the hardware tanh approximation (tanh.approx.f32); its
+// error is far below the BF16 rounding every activation gets
+__device__ __forceinline__ float gelu_fast(float z) {
+    const float u = kGeluC * fmaf(kGeluA * z * z, z, z);
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
+    return 0.5f * z * (1.0f + t);
 }
 
 // target scaling: IP / 4N, Ham / 8N, JS, Cos
@@ -250,6 +266,181 @@ __global__ void __launch_bounds__(256)
     for (int o = 0; o < OUT; ++o) out[(size_t)s * OUT + o] = (base[o] + y[o]) * out_scale(o, N);
 }
 
+// ---------------------------------------------------------------------------
+// inference with the 64 x 64 hidden layer on the tensor cores
+// ---------------------------------------------------------------------------
+// A tile of 128 samples per block: each thread computes its sample's first
+// layer on the CUDA cores and stores GELU(h1) rounded to BF16 as row `tid` of
+// the A operand (K-major, 128-byte swizzle: one 128-byte row of 64 BF16 per
+// sample); W2 (BF16, rows = output neurons, K-major) is the B operand, loaded
+// once per block.  One thread issues 4 x tcgen05.mma.kind::f16 (M = 128,
+// N = 64, K = 16, BF16 x BF16 -> FP32) into 64 TMEM columns; every thread
+// then reads its own row (TMEM lane = sample) and finishes b2, GELU and the
+// 64 -> 4 output layer on the CUDA cores.  Same arithmetic as infer_kernel up
+// to the order of the FP32 sums.
+namespace tcm {
+constexpr int ROWS = 128;                    // samples per tile (MMA M, TMEM lanes)
+constexpr int A_BYTES = ROWS * 128;          // 16 KB
+constexpr int B_BYTES = H * 128;             // 8 KB
+// D = F32, A = B = BF16, both K-major, N = 64, M = 128
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(H >> 3) << 17) |
+                           ((uint32_t)(ROWS >> 4) << 24);
+// dynamic shared memory: A, B, small weights, barrier; sized so that at most
+// 7 blocks share an SM (7 x 64 TMEM columns <= 512)
+constexpr int SMEM_BYTES = 30 * 1024;
+
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;                 // LBO (ignored for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;       // SBO: 8-row groups 1024 bytes apart
+    d |= (uint64_t)1 << 46;                 // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+    return d;
+}
+__device__ __forceinline__ uint32_t pack_bf2(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+// 64 values -> one 128-byte swizzled K-major row r (16-byte chunk c at c ^ (r % 8))
+__device__ __forceinline__ void store_row_bf16(uint8_t *tile, int r, const float (&v)[H]) {
+    uint8_t *row = tile + (r >> 3) * 1024 + (r & 7) * 128;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        uint4 q;
+        q.x = pack_bf2(v[8 * c + 0], v[8 * c + 1]);
+        q.y = pack_bf2(v[8 * c + 2], v[8 * c + 3]);
+        q.z = pack_bf2(v[8 * c + 4], v[8 * c + 5]);
+        q.w = pack_bf2(v[8 * c + 6], v[8 * c + 7]);
+        *reinterpret_cast<uint4 *>(row + ((c ^ (r & 7)) << 4)) = q;
+    }
+}
+__device__ __forceinline__ void ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+}  // namespace tcm
+
+__global__ void __launch_bounds__(tcm::ROWS)
+    infer_tc_kernel(const float *__restrict__ params, const uint32_t *__restrict__ counts, uint32_t n,
+                    uint32_t N, float *__restrict__ out, unsigned int *err) {
+    using namespace tcm;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *At = base;
+    uint8_t *Bt = base + A_BYTES;
+    float *Ws = reinterpret_cast<float *>(Bt + B_BYTES);   // W1, b1, b2, W3, b3 (BF16-rounded)
+    float *W1s = Ws, *b1s = W1s + H * IN, *b2s = b1s + H, *W3s = b2s + H, *b3s = W3s + OUT * H;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(b3s + 4);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    // weights: the small layers as FP32 (BF16-rounded), W2 as the BF16 B operand
+    for (int i = tid; i < H * IN; i += ROWS) W1s[i] = bf(params[OW1 + i]);
+    for (int i = tid; i < H; i += ROWS) {
+        b1s[i] = bf(params[OB1 + i]);
+        b2s[i] = bf(params[OB2 + i]);
+    }
+    for (int i = tid; i < OUT * H; i += ROWS) W3s[i] = bf(params[OW3 + i]);
+    if (tid < OUT) b3s[tid] = bf(params[OB3 + tid]);
+    if (tid < H) {   // row tid of B = output neuron tid's 64 input weights
+        float w[H];
+#pragma unroll
+        for (int k = 0; k < H; ++k) w[k] = params[OW2 + tid * H + k];
+        store_row_bf16(Bt, tid, w);
+    }
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(64u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const uint32_t n_tiles = (n + ROWS - 1) / ROWS;
+    bool ok = true;
+    uint32_t phase = 0;
+    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, phase ^= 1u) {
+        const uint32_t s = tile * ROWS + tid;
+        float x[IN] = {0.f, 0.f, 0.f, 0.f}, bsv[OUT] = {0.f, 0.f, 0.f, 0.f};
+        if (s < n) features(counts[3 * s], counts[3 * s + 1], counts[3 * s + 2], N, x, bsv);
+        float h1[H];
+#pragma unroll
+        for (int m = 0; m < H; ++m) {
+            float acc = b1s[m];
+#pragma unroll
+            for (int i = 0; i < IN; ++i) acc = fmaf(W1s[m * IN + i], bf(x[i]), acc);
+            h1[m] = (s < n) ? gelu_fast(acc) : 0.0f;   // rounded to BF16 by the store
+        }
+        store_row_bf16(At, tid, h1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0 && ok) {
+            const uint32_t a = smem_u32(At), b = smem_u32(Bt);
+#pragma unroll
+            for (int kk = 0; kk < H / 16; ++kk) {
+                const uint64_t ad = sw128_desc(a + kk * 32), bd = sw128_desc(b + kk * 32);
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(IDESC), "r"((uint32_t)kk)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(bar))
+                         : "memory");
+        }
+        if (ok && !mbar_wait(bar, phase)) {
+            ok = false;
+            raise_error(err, BS_ERR_TIMEOUT);
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint32_t r0[32], r1[32];
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        ld32(trow, r0);
+        ld32(trow + 32, r1);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float y[OUT];
+#pragma unroll
+        for (int o = 0; o < OUT; ++o) y[o] = b3s[o];
+#pragma unroll
+        for (int m = 0; m < H; ++m) {
+            const float acc = __uint_as_float(m < 32 ? r0[m] : r1[m - 32]) + b2s[m];
+            const float h2 = bf(gelu_fast(acc));
+#pragma unroll
+            for (int o = 0; o < OUT; ++o) y[o] = fmaf(W3s[o * H + m], h2, y[o]);
+        }
+        if (s < n && ok) {
+#pragma unroll
+            for (int o = 0; o < OUT; ++o) out[(size_t)s * OUT + o] = (bsv[o] + y[o]) * out_scale(o, N);
+        }
+        // every thread has read its accumulator row and is done with A before
+        // the next tile overwrites them
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64u) : "memory");
+}
+
 // features x[n][4] and scaled targets t[n][4] from counts and exact sizes
 __global__ void prepare_kernel(const uint32_t *__restrict__ counts, const uint32_t *__restrict__ sizes,
                                uint32_t n, uint32_t N, float *__restrict__ x, float *__restrict__ t) {
@@ -428,13 +619,31 @@ bs_status bs_mlp_train_step(float *params, float *adam_m, float *adam_v, float *
     return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
 }
 
-bs_status bs_mlp_estimate(const float *params, const uint32_t *counts, uint32_t n, uint32_t N, float *out,
-                          bs_stream_t stream) {
+bs_status bs_mlp_estimate_ex(const float *params, const uint32_t *counts, uint32_t n, uint32_t N,
+                             float *out, uint32_t variant, bs_stream_t stream) {
     if (!valid_N_l(N)) return BS_ERR_INVALID_ARG;
+    if (variant > BS_VARIANT_TC) return BS_ERR_INVALID_ARG;
     if (n == 0) return BS_OK;
     if (!params || !counts || !out) return BS_ERR_INVALID_ARG;
-    mlp::infer_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(params, counts, n, N, out);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (variant == BS_VARIANT_POPC) {   // CUDA cores only
+        mlp::infer_kernel<<<(n + 255) / 256, 256, 0, st>>>(params, counts, n, N, out);
+        return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+    }
+    unsigned int *err = error_word();
+    if (!err) return BS_ERR_CUDA;
+    const void *kern = (const void *)mlp::infer_tc_kernel;
+    if (ensure_smem(kern, mlp::tcm::SMEM_BYTES) != cudaSuccess) return BS_ERR_CUDA;
+    const uint32_t tiles = (n + mlp::tcm::ROWS - 1) / mlp::tcm::ROWS;
+    const uint32_t cap = (uint32_t)sm_count() * 6u;
+    const uint32_t grid = tiles < cap ? tiles : cap;
+    mlp::infer_tc_kernel<<<grid, mlp::tcm::ROWS, mlp::tcm::SMEM_BYTES, st>>>(params, counts, n, N, out, err);
     return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+}
+
+bs_status bs_mlp_estimate(const float *params, const uint32_t *counts, uint32_t n, uint32_t N, float *out,
+                          bs_stream_t stream) {
+    return bs_mlp_estimate_ex(params, counts, n, N, out, BS_VARIANT_AUTO, stream);
 }
 
 }  // extern "C"

@@ -61,7 +61,7 @@ def _torch_forward(params, x):
     W1, b1 = p[0:256].view(64, 4), p[256:320]
     W2, b2 = p[320:4416].view(64, 64), p[4416:4480]
     W3, b3 = p[4480:4736].view(4, 64), p[4736:4740]
-    gelu = lambda z: 0.5 * z * (1 + torch.erf(z / 2 ** 0.5))
+    gelu = lambda z: torch.nn.functional.gelu(z, approximate="tanh")
     h1 = bf(gelu(bf(x) @ W1.T + b1))
     h2 = bf(gelu(h1 @ W2.T + b2))
     return h2 @ W3.T + b3
@@ -79,9 +79,28 @@ def test_mlp_inference_matches_torch_reference():
     assert torch.allclose(got, base, rtol=1e-6, atol=1e-5)
     # with a random last layer: closed form + the network's correction
     mlp.params[4480:4740] = torch.randn(260, device="cuda") * 0.1
-    got = mlp.estimate(ps).cpu()
     ref = base + _torch_forward(mlp.params.cpu(), x.cpu()) * scale
-    assert torch.allclose(got, ref, rtol=2e-3, atol=2e-3 * ref.abs().max().item())
+    # both inference kernels: the hidden layer on the tensor cores (default)
+    # and every layer on the CUDA cores
+    outs = []
+    for variant in (B.BS_VARIANT_TC, B.BS_VARIANT_POPC):
+        out = torch.empty((ps.n, 4), dtype=torch.float32, device="cuda")
+        B.bs_mlp_estimate_ex(mlp.params, ps.counts, ps.n, ps.N, out, variant)
+        assert B.bs_get_async_error() == 0
+        got = out.cpu()
+        assert torch.allclose(got, ref, rtol=2e-3, atol=2e-3 * ref.abs().max().item()), variant
+        outs.append(got)
+    # the two differ in the order of FP32 sums and in the tanh evaluation
+    # (hardware approximation vs tanhf), which can move an activation by one
+    # BF16 rounding step (2^-8 relative) -- within the reference tolerance
+    assert torch.allclose(outs[0], outs[1], rtol=2e-3, atol=2e-3 * outs[1].abs().max().item())
+    assert torch.equal(mlp.estimate(ps).cpu(), outs[0])
+    # a ragged last tile and a single sample
+    for n in (1, 130):
+        sub = L.PairSet(ps.N, ps.counts[:n].contiguous(), ps.sizes[:n].contiguous())
+        o = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+        B.bs_mlp_estimate_ex(mlp.params, sub.counts, n, sub.N, o, B.BS_VARIANT_TC)
+        assert torch.allclose(o.cpu(), outs[0][:n], rtol=1e-6, atol=1e-6 * outs[0].abs().max().item())
 
 
 def test_mlp_gradient_matches_torch_autograd():
@@ -103,7 +122,7 @@ def test_mlp_gradient_matches_torch_autograd():
     W1, b1 = p[0:256].view(64, 4), p[256:320]
     W2, b2 = p[320:4416].view(64, 64), p[4416:4480]
     W3, b3 = p[4480:4736].view(4, 64), p[4736:4740]
-    gelu = lambda z: 0.5 * z * (1 + torch.erf(z / 2 ** 0.5))
+    gelu = lambda z: torch.nn.functional.gelu(z, approximate="tanh")
     h1 = ste(gelu(ste(x.cpu()) @ W1.T + b1))
     h2 = ste(gelu(h1 @ W2.T + b2))
     y = h2 @ W3.T + b3
