@@ -363,7 +363,7 @@ struct RowState {
 // (eff_k, eff_i) is the better of this heap's root (when full) and the other
 // group's; a pair not ranking above it cannot reach the final list.
 template <int M>
-__device__ __noinline__ RowState consider(RowState st, float *hkey, uint32_t *hix, int t, uint32_t col,
+__device__ __forceinline__ RowState consider(RowState st, float *hkey, uint32_t *hix, int t, uint32_t col,
                                           uint32_t c, uint32_t b, uint32_t a, float lnA,
                                           float eff_k, uint32_t eff_i, uint32_t N, float invL,
                                           int cap) {
