@@ -70,6 +70,7 @@ struct Geo {
     static_assert(BYTES % (8 * SK) == 0 && A % (8 * SK) == 0, "swizzle atom alignment");
 };
 constexpr uint32_t TMEM_COLS = 512;
+constexpr int CB = 8;                      // admitted pairs a row buffers within a tile
 constexpr uint32_t NO_IDX = 0xFFFFFFFFu;
 // Admit when U' >= bound * (1 - 2^-13).  U' is an exact integer and the bound
 // carries ~1e-6 relative FP32 error (ex2.approx, the row constants, the key it
@@ -87,7 +88,8 @@ struct Smem {
     static constexpr int bars = col + 2 * 2 * BN * 4;
     static constexpr int thr = bars + 256;                      // [NG][BM] key, idx, size
     static constexpr int lock = thr + NG * BM * 12;             // [BM] shared-heap row locks
-    static constexpr int heap = lock + BM * 4;
+    static constexpr int cbuf = lock + BM * 4;                  // [NG][CB][BM] admitted pairs
+    static constexpr int heap = cbuf + NG * CB * BM * 4;
     static_assert((2 * NOP + 4) * 8 + 8 <= 256, "barrier area");
 };
 
@@ -594,10 +596,30 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
         constexpr int COLS = BN / NG;              // tile columns of this group
         RowState st;
         st.thr_k = -INFINITY; st.thr_i = NO_IDX; st.size = 0;
+        // this row's buffer of admitted pairs, (count << 8) | column in tile
+        uint32_t *cb = reinterpret_cast<uint32_t *>(base + Smem::cbuf) + (size_t)grp * CB * BM;
+        int nbuf = 0;
+        uint32_t d_col0 = 0;          // first column of the tile the buffer belongs to
+        const float *d_cv = colv;     // that tile's column values
         float eff_k = -INFINITY;                   // threshold the filter was built from
         uint32_t eff_i = NO_IDX;
         RowFilter filt;
         filt.all = true; filt.c0 = filt.c1 = 0.f;
+        // insert every buffered pair of this row into its heap (warp-wide loop)
+        auto drain = [&]() {
+            while (__any_sync(0xffffffffu, nbuf > 0)) {
+                if (nbuf > 0) {
+                    --nbuf;
+                    const uint32_t ent = cb[nbuf * BM + r];
+                    const uint32_t j = ent & 255u;
+                    st = consider<M>(st, hkey, hix, r, d_col0 + j, ent >> 8, (uint32_t)d_cv[j], a, lnA,
+                                     eff_k, eff_i, p.N, p.invL, (int)p.k);
+                    if (st.thr_i != NO_IDX && better(st.thr_k, st.thr_i, eff_k, eff_i)) {
+                        eff_k = st.thr_k; eff_i = st.thr_i;
+                    }
+                }
+            }
+        };
 
         uint32_t tile = (uint32_t)(u_lo % n_tiles);   // tile of unit u_lo + t
         rb = (uint32_t)(u_lo / n_tiles);
@@ -645,6 +667,8 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
             wait(&acc_full[ab], (t >> 1) & 1);
             tc_fence_after();
             const uint32_t col0 = tile * BN;
+            d_col0 = col0;
+            d_cv = cv;
             // every lane stays in the loops below (they vote); dead rows admit nothing
             const bool live = row_ok && !*abort_flag;
             const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + ab * BN;
@@ -689,28 +713,49 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                     if (qs >= 0 && qs < 32) mask &= ~(1u << (uint32_t)qs);
                 }
                 if (!live) mask = 0;
-                // pass 2: exact keys for the admitted pairs; the warp loops only as
-                // often as its busiest row needs
+                // pass 2: exact keys for the admitted pairs.  Per-group heaps: the
+                // pairs are buffered per row and inserted once per tile (the
+                // warp loops as often as its busiest row needs); a chunk that
+                // does not fit some row's buffer empties the buffers and is
+                // inserted directly.
                 const int size_before = st.size;
                 const uint32_t root_before = st.thr_i;
                 const float rootk_before = st.thr_k;
-                while (__any_sync(0xffffffffu, mask != 0)) {
-                    if (mask) {
-                        const uint32_t jj = __ffs(mask) - 1;
-                        mask &= mask - 1;
-                        const uint32_t c = (uint32_t)(__uint_as_float(select32(v, jj)) * 4096.0f);
-                        const int j = ch * 32 + (int)jj;
-                        if (SHARED) {
-                            const float root = consider_shared<M>(hkey, hix, thr_key, heap_size, row_lock, r,
-                                                                  col_c + jj, c, (uint32_t)cv[j], a, lnA, eff_k,
-                                                                  p.N, p.invL, (int)p.k, p.err);
-                            if (root > eff_k) { eff_k = root; eff_i = 0xFFFFFFFEu; }
-                        } else {
-                            st = consider<M>(st, hkey, hix, r, col_c + jj, c, (uint32_t)cv[j], a, lnA,
-                                             eff_k, eff_i, p.N, p.invL, (int)p.k);
-                            if (st.thr_i != NO_IDX && better(st.thr_k, st.thr_i, eff_k, eff_i)) {
-                                eff_k = st.thr_k; eff_i = st.thr_i;
+                auto insert_direct = [&](uint32_t m) {
+                    while (__any_sync(0xffffffffu, m != 0)) {
+                        if (m) {
+                            const uint32_t jj = __ffs(m) - 1;
+                            m &= m - 1;
+                            const uint32_t c = (uint32_t)(__uint_as_float(select32(v, jj)) * 4096.0f);
+                            const int j = ch * 32 + (int)jj;
+                            if (SHARED) {
+                                const float root = consider_shared<M>(hkey, hix, thr_key, heap_size, row_lock,
+                                                                      r, col_c + jj, c, (uint32_t)cv[j], a, lnA,
+                                                                      eff_k, p.N, p.invL, (int)p.k, p.err);
+                                if (root > eff_k) { eff_k = root; eff_i = 0xFFFFFFFEu; }
+                            } else {
+                                st = consider<M>(st, hkey, hix, r, col_c + jj, c, (uint32_t)cv[j], a, lnA,
+                                                 eff_k, eff_i, p.N, p.invL, (int)p.k);
+                                if (st.thr_i != NO_IDX && better(st.thr_k, st.thr_i, eff_k, eff_i)) {
+                                    eff_k = st.thr_k; eff_i = st.thr_i;
+                                }
                             }
+                        }
+                    }
+                };
+                if (SHARED) {
+                    insert_direct(mask);
+                } else if (__any_sync(0xffffffffu, __popc(mask) > CB - nbuf)) {
+                    drain();
+                    insert_direct(mask);
+                } else {
+                    while (__any_sync(0xffffffffu, mask != 0)) {
+                        if (mask) {
+                            const uint32_t jj = __ffs(mask) - 1;
+                            mask &= mask - 1;
+                            const uint32_t c = (uint32_t)(__uint_as_float(select32(v, jj)) * 4096.0f);
+                            cb[nbuf * BM + r] = (c << 8) | (uint32_t)(ch * 32 + (int)jj);
+                            ++nbuf;
                         }
                     }
                 }
@@ -725,6 +770,17 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[ab]);
+            if (!SHARED) {   // this tile's buffered pairs (TMEM no longer needed)
+                const int sz0 = st.size;
+                const uint32_t ri0 = st.thr_i;
+                const float rk0 = st.thr_k;
+                drain();
+                if (NG == 2 && (st.size != sz0 || st.thr_i != ri0 || st.thr_k != rk0)) {
+                    thr_key[grp * BM + r] = st.thr_k;
+                    thr_idx[grp * BM + r] = st.thr_i;
+                }
+                if (eff_i != NO_IDX) filt = make_filter<M>(eff_k, rc, p.invL, p.log2N);
+            }
             if (t + 1 < n_my_tiles && tile + 1 < n_tiles) continue;
             // ---- end of this row block's segment: its list for part `part`
             const uint64_t x0 = u - tile;   // first unit of this row block
