@@ -381,7 +381,7 @@ def run_serving(args):
     rng = np.random.default_rng(7)
     zc = inputs.ZipfColumns(np.random.default_rng(8), SERVING["d"])
     make = lambda r, q: inputs.query_batch(r, q, zc)
-    slots, max_q, arena = 3, 4096, 6 << 30
+    slots, max_q, arena = args.slots, args.max_batch, 6 << 30
 
     def serve(reqs):
         ex = GpuExecutor(db, k=k, by="js", slots=slots, arena_bytes=arena, max_queries=max_q)
@@ -680,6 +680,8 @@ def main():
     ap.add_argument("--db-rows", type=int, default=SERVING["db_rows"])
     ap.add_argument("--serving-requests", type=int, default=300)
     ap.add_argument("--loads", type=float, nargs="+", default=[0.5, 0.8, 0.95])
+    ap.add_argument("--slots", type=int, default=3, help="serving: concurrent micro-batches")
+    ap.add_argument("--max-batch", type=int, default=4096, help="serving: queries per micro-batch")
     args = ap.parse_args()
     if args.workload == "serving":
         run_serving(args)
