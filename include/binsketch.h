@@ -145,8 +145,10 @@ bs_status bs_estimate_pairs(const uint32_t *A, const uint32_t *pcA, uint32_t nA,
 
 /*
  * bs_topk_workspace_bytes -- device workspace bs_topk / bs_topk_ex need for
- * this shape, whichever kernel runs: per-split candidate lists when the
- * database is split across blocks, and for the tensor-core kernel a
+ * this shape, whichever kernel runs: partial top-k lists when a query row's
+ * database is divided between blocks (the CUDA-core kernel splits the
+ * database; the tensor-core kernel's persistent blocks cut some row blocks
+ * in two), and for the tensor-core kernel a
  * k-chunk-tiled copy of Q and DB (N/8 bytes per row, rows rounded up to 128).
  */
 size_t bs_topk_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k);
@@ -258,8 +260,8 @@ bs_status bs_topk_merge(const float *score_parts, const uint32_t *idx_parts, uin
 
 /*
  * bs_topk_plan -- how bs_topk_ex would run this shape, without running it:
- * *uses_tc = 1 when the tensor-core kernel is chosen, *splits = database
- * splits (a merge kernel runs when > 1), *launches = kernels launched per
+ * *uses_tc = 1 when the tensor-core kernel is chosen, *splits = partial
+ * lists per query row (a merge kernel runs when > 1), *launches = kernels launched per
  * call.  same_matrix != 0 when Q and DB will be the same array (the
  * tensor-core path then re-lays out one matrix instead of two).  Any output
  * pointer may be NULL.  Host only; Q/DB alignment is assumed to be 16 bytes.

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(PKG, "_build", "libbinsketch.so")
 
 BS_IP, BS_HAM, BS_JS, BS_COS = 1, 2, 4, 8
 BS_VARIANT_AUTO, BS_VARIANT_POPC, BS_VARIANT_TC = 0, 1, 2
-VARIANTS = {"auto": 0, "popc": 1, "tc": 2}
+VARIANTS = {"auto": 0, "popc": 1, "tc": 2}   # plus "tc0" .. "tc9" below
 
 
 BS_TC_CONFIGS = 10
@@ -25,6 +25,9 @@ BS_TC_CONFIGS = 10
 def BS_VARIANT_TC_CFG(c: int) -> int:
     """Bits selecting tensor-core block configuration c (0..9) in bs_topk_ex's variant."""
     return (c + 1) << 4
+
+
+VARIANTS.update({f"tc{c}": BS_VARIANT_TC | BS_VARIANT_TC_CFG(c) for c in range(BS_TC_CONFIGS)})
 
 
 class bs_sketch_job(ctypes.Structure):

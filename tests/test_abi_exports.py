@@ -51,3 +51,22 @@ def test_env_variant_override_in_plan():
     env["BS_VARIANT"] = "popc"
     forced = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=root)
     assert plain.stdout.strip() == "1" and forced.stdout.strip() == "0", (plain.stderr, forced.stderr)
+
+
+def test_tensor_core_plan_parts_match_the_persistent_schedule():
+    # bs_topk_plan is host-only; without a GPU the library assumes 148 SMs.
+    # Parts = the most blocks any 128-row query block is spread over when
+    # 256-row database tiles are dealt out as equal contiguous ranges.
+    from paper_1910_04658_gb300 import binding as B
+
+    def parts(nq, ndb, G=148):
+        rbs, T = (nq + 127) // 128, (ndb + 255) // 256
+        U = rbs * T
+        G = min(G, U)
+        first = lambda x: ((x + 1) * G - 1) // U
+        return max(first(rb * T + T - 1) - first(rb * T) + 1 for rb in range(rbs))
+
+    for nq, ndb in ((100_000, 100_000), (4096, 1_000_000), (1000, 1000), (37, 20_000), (129, 257)):
+        uses_tc, splits, launches = B.bs_topk_plan(nq, ndb, 4096, 50, B.BS_VARIANT_TC, nq == ndb)
+        assert uses_tc and splits == parts(nq, ndb), (nq, ndb, splits, parts(nq, ndb))
+        assert launches == 1 + (splits > 1) + (1 if nq == ndb else 2)
