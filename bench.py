@@ -191,7 +191,7 @@ def run_reference(args, rank, world):
 def run_ours(args, rank, world, dist):
     import torch
 
-    from paper_1910_04658_gb300 import api, binding as B, build, inputs, sharded
+    from paper_1910_04658_gb300 import binding as B, build, inputs, sharded
 
     build.build()
     B.lib()
@@ -366,7 +366,7 @@ def run_serving(args):
     import torch
 
     from paper_1910_04658_gb300 import binding as B, build, inputs
-    from paper_1910_04658_gb300.serving import (GpuExecutor, Request, Scheduler, SketchDB,
+    from paper_1910_04658_gb300.serving import (GpuExecutor, Scheduler, SketchDB,
                                                 latency_stats, poisson_requests)
 
     build.build()

@@ -106,12 +106,6 @@ __device__ __forceinline__ void raise_error(unsigned int *err, unsigned int code
     if (err) atomicCAS(err, 0u, code);
 }
 
-__device__ __forceinline__ uint64_t globaltimer_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }

@@ -4,7 +4,6 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_1910_04658_gb300 import inputs
 from tests.helpers import check_topk_row, u32
 
 torch = pytest.importorskip("torch")

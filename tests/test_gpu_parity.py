@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 from paper_1910_04658_gb300 import inputs
-from tests.helpers import assert_close, check_topk_row, dev_u32, to_dev, u32
+from tests.helpers import assert_close, check_topk_row, to_dev, u32
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu

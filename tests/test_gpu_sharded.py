@@ -4,12 +4,11 @@ indices and bit-identical scores -- for both pair-counting kernels, in
 all-pairs mode (self pair excluded through the shard offset) and in
 query-vs-database mode, with ragged shards and a shard smaller than k.  The
 merged lists are also checked against the FP64 oracle."""
-import numpy as np
 import pytest
 
 import oracle
 from paper_1910_04658_gb300 import inputs, sharded
-from tests.helpers import check_topk_row, dev_u32, to_dev, u32
+from tests.helpers import check_topk_row, to_dev, u32
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
