@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(256)
 struct Heap {
     float *key;      // key[i * BM + t]
     uint32_t *ix;
-    int t, size, cap;
+    int t, size, cap, levels;
     __device__ float k_at(int i) const { return key[i * BM + t]; }
     __device__ uint32_t i_at(int i) const { return ix[i * BM + t]; }
     __device__ void put(int i, float kk, uint32_t ii) { key[i * BM + t] = kk; ix[i * BM + t] = ii; }
@@ -282,6 +282,12 @@ struct Heap {
         }
     }
 };
+
+__host__ __device__ constexpr int heap_levels(int cap) {
+    int lv = 0;
+    while ((1 << lv) <= cap) ++lv;   // a heap of cap entries has lv levels
+    return lv;
+}
 
 // Per-row constants of the admission bound (see filter_bound).
 struct RowFilter {
