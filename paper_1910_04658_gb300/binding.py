@@ -2,8 +2,12 @@
 
 Each function has the name of the C entry point it calls and only marshals
 arguments: tensors become device pointers, ``stream=None`` becomes the current
-torch stream.  All work runs in the library's CUDA kernels; if the library is
-missing, ``lib()`` raises -- there is no CPU fallback.
+torch stream.  A tensor argument must be a contiguous CUDA tensor; for the
+sketch, estimate and top-k entry points it must also hold at least the bytes
+the call's sizes imply.  Anything else raises ValueError before a kernel sees
+the address (an int is taken as a device address as is).  All work runs in
+the library's CUDA kernels; if the library is missing, ``lib()`` raises --
+there is no CPU fallback.
 """
 from __future__ import annotations
 
@@ -113,12 +117,27 @@ def lib():
     return _lib
 
 
-def _p(x):
+def _p(x, nbytes: int = 0, name: str = "argument"):
+    """Device address of `x`: None, an int (taken as a device address as is),
+    or a contiguous CUDA tensor of at least `nbytes` bytes.  A host tensor, a
+    strided view or a tensor too small for the call raises ValueError here
+    instead of reaching a kernel."""
     if x is None:
         return None
     if isinstance(x, int):
         return x
+    if not x.is_cuda:
+        raise ValueError(f"{name}: a CUDA tensor is required, got one on {x.device}")
+    if not x.is_contiguous():
+        raise ValueError(f"{name}: the tensor must be contiguous")
+    have = x.numel() * x.element_size()
+    if have < nbytes:
+        raise ValueError(f"{name}: {have} bytes, the call needs {nbytes}")
     return x.data_ptr()
+
+
+def _nmeasures(measures: int) -> int:
+    return bin(int(measures) & 15).count("1")
 
 
 def _s(stream):
@@ -135,9 +154,14 @@ def _check(rc, where):
         raise BinSketchError(rc, where)
 
 
+def _sketch_args(row_ptr, col, n_rows, nnz, N, sketch, popcnt):
+    return (_p(row_ptr, 8 * (n_rows + 1) if n_rows else 0, "row_ptr"), _p(col, 4 * nnz, "col"), n_rows,
+            nnz), (_p(sketch, n_rows * (N // 8), "sketch"), _p(popcnt, 4 * n_rows, "popcnt"))
+
+
 def bs_sketch(row_ptr, col, n_rows, nnz, d, N, seed, sketch, popcnt=None, stream=None):
-    _check(lib().bs_sketch(_p(row_ptr), _p(col), n_rows, nnz, d, N, seed, _p(sketch), _p(popcnt),
-                           _s(stream)), "bs_sketch")
+    (rp, c, n, z), (sk, pc) = _sketch_args(row_ptr, col, n_rows, nnz, N, sketch, popcnt)
+    _check(lib().bs_sketch(rp, c, n, z, d, N, seed, sk, pc, _s(stream)), "bs_sketch")
 
 
 def bs_sketch_batched(jobs_dev, n_jobs, max_N, stream=None):
@@ -146,41 +170,56 @@ def bs_sketch_batched(jobs_dev, n_jobs, max_N, stream=None):
 
 
 def bs_sketch_parity(row_ptr, col, n_rows, nnz, d, N, seed, sketch, popcnt=None, stream=None):
-    _check(lib().bs_sketch_parity(_p(row_ptr), _p(col), n_rows, nnz, d, N, seed, _p(sketch),
-                                  _p(popcnt), _s(stream)), "bs_sketch_parity")
+    (rp, c, n, z), (sk, pc) = _sketch_args(row_ptr, col, n_rows, nnz, N, sketch, popcnt)
+    _check(lib().bs_sketch_parity(rp, c, n, z, d, N, seed, sk, pc, _s(stream)), "bs_sketch_parity")
 
 
 def bs_popcount_rows(sketch, n_rows, N, popcnt, stream=None):
-    _check(lib().bs_popcount_rows(_p(sketch), n_rows, N, _p(popcnt), _s(stream)), "bs_popcount_rows")
+    sk, pc = _p(sketch, n_rows * (N // 8), "sketch"), _p(popcnt, 4 * n_rows, "popcnt")
+    _check(lib().bs_popcount_rows(sk, n_rows, N, pc, _s(stream)), "bs_popcount_rows")
 
 
 def bs_estimate_pairs(A, pcA, nA, B, pcB, nB, N, measures, out=None, counts=None, stream=None):
-    _check(lib().bs_estimate_pairs(_p(A), _p(pcA), nA, _p(B), _p(pcB), nB, N, measures, _p(out),
-                                   _p(counts), _s(stream)), "bs_estimate_pairs")
+    pairs = nA * nB
+    a, pa = _p(A, nA * (N // 8), "A"), _p(pcA, 4 * nA, "pcA")
+    b, pb = _p(B, nB * (N // 8), "B"), _p(pcB, 4 * nB, "pcB")
+    o, c = _p(out, 4 * _nmeasures(measures) * pairs, "out"), _p(counts, 4 * pairs, "counts")
+    _check(lib().bs_estimate_pairs(a, pa, nA, b, pb, nB, N, measures, o, c, _s(stream)),
+           "bs_estimate_pairs")
 
 
 def bs_topk_workspace_bytes(nQ, nDB, N, k) -> int:
     return int(lib().bs_topk_workspace_bytes(nQ, nDB, N, k))
 
 
+def _topk_args(Q, pcQ, nQ, DB, pcDB, nDB, N, k, score, idx, workspace, workspace_bytes):
+    return (_p(Q, nQ * (N // 8), "Q"), _p(pcQ, 4 * nQ, "pcQ"), _p(DB, nDB * (N // 8), "DB"),
+            _p(pcDB, 4 * nDB, "pcDB"), _p(score, 4 * nQ * k, "score"), _p(idx, 4 * nQ * k, "idx"),
+            _p(workspace, workspace_bytes, "workspace"))
+
+
 def bs_topk(Q, pcQ, nQ, DB, pcDB, nDB, N, by, k, exclude_self, score, idx, workspace=None,
             workspace_bytes=0, stream=None):
-    _check(lib().bs_topk(_p(Q), _p(pcQ), nQ, _p(DB), _p(pcDB), nDB, N, by, k, int(exclude_self),
-                         _p(score), _p(idx), _p(workspace), workspace_bytes, _s(stream)), "bs_topk")
+    q, pq, db, pdb, sc, ix, ws = _topk_args(Q, pcQ, nQ, DB, pcDB, nDB, N, k, score, idx, workspace,
+                                            workspace_bytes)
+    _check(lib().bs_topk(q, pq, nQ, db, pdb, nDB, N, by, k, int(exclude_self), sc, ix, ws,
+                         workspace_bytes, _s(stream)), "bs_topk")
 
 
 def bs_topk_ex(Q, pcQ, nQ, DB, pcDB, nDB, N, by, k, exclude_self, score, idx, workspace=None,
                workspace_bytes=0, variant=0, stream=None):
-    _check(lib().bs_topk_ex(_p(Q), _p(pcQ), nQ, _p(DB), _p(pcDB), nDB, N, by, k, int(exclude_self),
-                            _p(score), _p(idx), _p(workspace), workspace_bytes, variant,
-                            _s(stream)), "bs_topk_ex")
+    q, pq, db, pdb, sc, ix, ws = _topk_args(Q, pcQ, nQ, DB, pcDB, nDB, N, k, score, idx, workspace,
+                                            workspace_bytes)
+    _check(lib().bs_topk_ex(q, pq, nQ, db, pdb, nDB, N, by, k, int(exclude_self), sc, ix, ws,
+                            workspace_bytes, variant, _s(stream)), "bs_topk_ex")
 
 
 def bs_topk_shard(Q, pcQ, nQ, DB, pcDB, nDB, db_offset, N, by, k, exclude_self, score, idx,
                   workspace=None, workspace_bytes=0, variant=0, stream=None):
-    _check(lib().bs_topk_shard(_p(Q), _p(pcQ), nQ, _p(DB), _p(pcDB), nDB, db_offset, N, by, k,
-                               int(exclude_self), _p(score), _p(idx), _p(workspace),
-                               workspace_bytes, variant, _s(stream)), "bs_topk_shard")
+    q, pq, db, pdb, sc, ix, ws = _topk_args(Q, pcQ, nQ, DB, pcDB, nDB, N, k, score, idx, workspace,
+                                            workspace_bytes)
+    _check(lib().bs_topk_shard(q, pq, nQ, db, pdb, nDB, db_offset, N, by, k, int(exclude_self), sc,
+                               ix, ws, workspace_bytes, variant, _s(stream)), "bs_topk_shard")
 
 
 def bs_topk_merge(score_parts, idx_parts, parts, nQ, k, part_offset, by, score, idx, stream=None):
@@ -237,9 +276,9 @@ def bs_topk_pretiled(Q, pcQ, nQ, DB_tiled, pcDB, nDB, N, by, k, score, idx, work
 
 
 def bs_topk_noalloc(Q, pcQ, nQ, DB, pcDB, nDB, N, by, k, exclude_self, score, idx, stream=None):
-    _check(lib().bs_topk_noalloc(_p(Q), _p(pcQ), nQ, _p(DB), _p(pcDB), nDB, N, by, k,
-                                 int(exclude_self), _p(score), _p(idx), _s(stream)),
-           "bs_topk_noalloc")
+    q, pq, db, pdb, sc, ix, _ = _topk_args(Q, pcQ, nQ, DB, pcDB, nDB, N, k, score, idx, None, 0)
+    _check(lib().bs_topk_noalloc(q, pq, nQ, db, pdb, nDB, N, by, k, int(exclude_self), sc, ix,
+                                 _s(stream)), "bs_topk_noalloc")
 
 
 BS_MLP_PARAMS = 4740
