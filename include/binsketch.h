@@ -18,6 +18,14 @@
  *    (column index >= d, malformed row offsets) do not fault: the offending
  *    row is skipped (its sketch and count are written as zero) and a sticky
  *    per-device flag is raised; bs_get_async_error() reads and clears it.
+ *  - Errors every call shares: BS_ERR_INVALID_ARG for a size parameter
+ *    outside its documented range (N, k, d, thresholds), an unknown measure
+ *    or variant, a NULL array that a non-zero count needs, or a pointer
+ *    without the alignment the call states; BS_ERR_CUDA when a launch or a
+ *    CUDA attribute call fails.  Kernels with bounded waits (tensor-core
+ *    top-k, learned inference) raise BS_ERR_TIMEOUT through
+ *    bs_get_async_error instead of hanging.  A call with a zero count (no
+ *    rows, no queries) returns BS_OK after checking its size parameters.
  *  - Sketch layout: row r of a sketch matrix is N/32 consecutive uint32
  *    words; bucket j is bit (j & 31) of word (j >> 5) (LSB first).  Rows are
  *    contiguous (row stride N/32 words).
@@ -138,6 +146,9 @@ bs_status bs_popcount_rows(const uint32_t *sketch, uint32_t n_rows, uint32_t N, 
  * Saturated counts are clamped so that N - |a_s|, N - |b_s| and
  * N - |a_s OR b_s| are at least 1; Cos = 0 when an estimated size is 0 and
  * JS = 0 when the estimated union is 0.  Estimates are not clamped.
+ * Errors: BS_ERR_INVALID_ARG for measure bits outside the four or out NULL
+ * with measures != 0; BS_ERR_UNSUPPORTED for nB > 65535 * 128 rows (call
+ * once per slice of B).
  */
 bs_status bs_estimate_pairs(const uint32_t *A, const uint32_t *pcA, uint32_t nA,
                             const uint32_t *B, const uint32_t *pcB, uint32_t nB, uint32_t N,
@@ -172,7 +183,9 @@ size_t bs_topk_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k
  *  workspace    device memory of at least bs_topk_workspace_bytes(...)
  *               bytes, 256-byte aligned (may be NULL when that is 0);
  *               contents are scratch
- * Errors: BS_ERR_NO_MEMORY when workspace_bytes is too small.
+ * Errors: BS_ERR_INVALID_ARG for k outside 1..BS_TOPK_K_MAX, `by` not one
+ * measure, exclude_self with nQ > nDB, or a workspace not 256-byte aligned;
+ * BS_ERR_NO_MEMORY when workspace_bytes is below what the shape needs.
  */
 bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
                   const uint32_t *DB, const uint32_t *pcDB, uint32_t nDB, uint32_t N,
