@@ -25,7 +25,8 @@
  *    CUDA attribute call fails.  Kernels with bounded waits (tensor-core
  *    top-k, learned inference) raise BS_ERR_TIMEOUT through
  *    bs_get_async_error instead of hanging.  A call with a zero count (no
- *    rows, no queries) returns BS_OK after checking its size parameters.
+ *    rows, no queries) returns BS_OK after checking its size parameters,
+ *    except bs_mlp_train_step (a step needs a batch).
  *  - Sketch layout: row r of a sketch matrix is N/32 consecutive uint32
  *    words; bucket j is bit (j & 31) of word (j >> 5) (LSB first).  Rows are
  *    contiguous (row stride N/32 words).
@@ -427,7 +428,8 @@ bs_status bs_mlp_prepare(const uint32_t *counts, const uint32_t *sizes, uint32_t
 /* bs_mlp_train_step -- one Adam step (beta 0.9 / 0.999, eps 1e-8) on the mean
  * squared error of a batch: params, adam_m, adam_v, grad are float
  * [BS_MLP_PARAMS] (grad must start at zero and is left at zero); step counts
- * from 1; loss (may be NULL) receives the batch loss added to its value. */
+ * from 1; loss (may be NULL) receives the batch loss added to its value.
+ * Errors: BS_ERR_INVALID_ARG for n = 0 or step = 0. */
 bs_status bs_mlp_train_step(float *params, float *adam_m, float *adam_v, float *grad, uint32_t step,
                             float lr, const float *x, const float *t, uint32_t n, float *loss,
                             bs_stream_t stream);
