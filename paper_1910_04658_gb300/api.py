@@ -47,7 +47,7 @@ def topk(Q, pcQ, DB, pcDB, N: int, k: int, by: str = "js", exclude_self: bool = 
     score = torch.empty((nQ, k), dtype=torch.float32, device=Q.device)
     idx = torch.empty((nQ, k), dtype=torch.int32, device=Q.device)
     wsb = B.bs_topk_workspace_bytes(nQ, nDB, N, k)
-    if wsb and (workspace is None or workspace.numel() < wsb):
+    if wsb and (workspace is None or workspace.numel() * workspace.element_size() < wsb):
         workspace = torch.empty((wsb,), dtype=torch.uint8, device=Q.device)
     B.bs_topk_ex(Q, pcQ, nQ, DB, pcDB, nDB, N, B.MEASURE_BITS[by], k, exclude_self, score, idx,
                  workspace if wsb else None, wsb, B.VARIANTS[variant], stream)
