@@ -57,8 +57,8 @@ def test_sketch_unaligned_column_pointer_and_empty_rows():
     N = 512
     osk, opc = oracle.sketch(c.row_ptr, c.col, c.d, N, 3)
     for shift in (1, 2, 3, 4, 5):
-        # the same rows stored `shift` words into the column buffer (16-byte
-        # aligned at shift 4: the streamed kernel; otherwise the per-row one)
+        # the same rows stored `shift` words into the column buffer: every
+        # offset of the first 16-byte boundary the kernel peels up to
         col = torch.zeros(c.col.size + 8, dtype=torch.int32, device="cuda")
         col[shift:shift + c.col.size] = torch.from_numpy(c.col.view(np.int32)).cuda()
         rp = torch.from_numpy(c.row_ptr.view(np.int64)).cuda()
@@ -84,7 +84,8 @@ def test_sketch_long_rows_and_duplicates():
 
 @pytest.mark.parametrize("N", [64, 4096])
 def test_sketch_many_short_rows(N):
-    # thousands of rows per staged batch, several row blocks per thread block
+    # 40,000 rows of 0-3 indices: most of a row's lanes idle, empty rows,
+    # several rows per warp (the grid strides over them)
     rng = np.random.default_rng(N)
     n = 40_000
     nnz = rng.integers(0, 4, n)
