@@ -31,18 +31,31 @@ IP, HAM, JS, COS = 0, 1, 2, 3
 MEASURES = {"ip": IP, "ham": HAM, "js": JS, "cos": COS}
 
 
+def compile_library(src: str, out: str) -> str:
+    """gcc with the oracle's flags (portable, no FMA contraction): src -> out."""
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-ffp-contract=off", "-fPIC",
+           "-shared", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (portable flags, no FMA contraction)."""
+    """Compile bs_oracle.c into _build/ unless the library is up to date."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-ffp-contract=off", "-fPIC",
-           "-shared", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    return compile_library(_SRC, _LIB_PATH)
+
+
+def _library_path() -> str:
+    # BS_ORACLE_LIB names another build of bs_oracle.c to load instead; the
+    # mutation tests use it to run the pins against copies with a planted
+    # mistake and check that a pin fails.
+    alt = os.environ.get("BS_ORACLE_LIB")
+    return alt if alt else build()
 
 
 def _P(t):
@@ -53,7 +66,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
+            L = ctypes.CDLL(_library_path())
             u32, u64, i32, f64 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_double
             L.bso_hash_params.argtypes = [u64, _P(u64), _P(u64)]
             L.bso_bucket.argtypes = [u64, u64, u32, u32]

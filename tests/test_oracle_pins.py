@@ -160,9 +160,15 @@ def test_bcs_parity_sketch_is_linear():
 
 
 def test_out_of_range_column_is_rejected():
-    rp, col = _csr([[1, 2], [3, 99]], 50)
-    with pytest.raises(ValueError):
-        oracle.sketch(rp, col, 50, 64, seed=0)
+    # columns are 0 .. d-1: d itself is the first index out of range
+    for bad in (50, 99):
+        rp, col = _csr([[1, 2], [3, bad]], 50)
+        for parity in (False, True):
+            with pytest.raises(ValueError):
+                oracle.sketch(rp, col, 50, 64, seed=0, parity=parity)
+    rp, col = _csr([[1, 2], [3, 49]], 50)
+    sk, pc = oracle.sketch(rp, col, 50, 64, seed=0)
+    assert pc[1] >= 1
 
 
 def test_counts_brute_force():
