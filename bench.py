@@ -136,7 +136,7 @@ def oracle_sample(csr, N, k, budget_s):
     t0 = time.perf_counter()
     sk, pc = oracle.sketch(csr.row_ptr, csr.col, csr.d, N, 0)
     t_sketch = time.perf_counter() - t0
-    rows, t_topk, batch = 0, 0.0, 16
+    rows, t_topk, batch = 0, 0.0, min(16, csr.n)
     rng = np.random.default_rng(1)
     while t_topk < budget_s:
         q = rng.choice(csr.n, batch, replace=False)
@@ -144,7 +144,7 @@ def oracle_sample(csr, N, k, budget_s):
         oracle.topk(sk[q], sk, N, oracle.JS, k, exclude_self=False)
         t_topk += time.perf_counter() - t0
         rows += batch
-        batch = min(batch * 2, 1024)
+        batch = min(batch * 2, 1024, csr.n)
     pairs_per_s = rows * (csr.n - 1) / t_topk
     n = csr.n
     step_s = t_sketch + n * (t_topk / rows)
@@ -157,7 +157,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     from paper_1910_04658_gb300 import inputs
-    csr = inputs.bow_corpus(0)
+    csr = inputs.bow_corpus(0, n=args.n)    # the corpus our arm's rank 0 sketches
     N, k = WORKLOAD["N"], WORKLOAD["k"]
     vals = []
     info = None
@@ -171,12 +171,13 @@ def run_reference(args, rank, world):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "pair-estimates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": (WORKLOAD["n"] * (WORKLOAD["n"] - 1)) / value * 1e3,
+        "ms_per_step": (csr.n * (csr.n - 1)) / value * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": dict(WORKLOAD, step="oracle: full sketch + sampled top-k rows"),
+        "data": "synthetic",
+        "config": dict(WORKLOAD, n=csr.n, step="oracle: full sketch + sampled top-k rows"),
         "cpu_baseline": {"kind": "oracle", "value": value, "unit": "pair-estimates/s",
                          "cores": info[5],
-                         "sample": f"full sketch of 100,000 rows + top-{k} of {info[3]} sampled "
+                         "sample": f"full sketch of {csr.n:,} rows + top-{k} of {info[3]} sampled "
                                    f"query rows per step, extrapolated to all rows"},
         "e2e": {"value": value, "unit": "pair-estimates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
