@@ -1,6 +1,7 @@
 """Ranking-quality evaluation (Experiment 2, Sec. 4) on the GPU vs the oracle:
 exact common counts bit for bit, retrieval-set counts exactly (both sides
-decide in FP64 on the same estimates), and the end-to-end evaluation."""
+threshold the oracle's estimates, rounded to FP32 as the GPU path holds them,
+in FP64), and the end-to-end evaluation."""
 import numpy as np
 import pytest
 
@@ -70,13 +71,14 @@ def test_threshold_eval_matches_oracle(N):
     q, t = ranking.take_rows(c, qr), ranking.take_rows(c, tr)
     cnt, qs, ts = _counts(q, t, c.d)
     ex = _oracle_exact(q, t)
-    q_rp, q_col = to_dev(q)
-    t_rp, t_col = to_dev(t)
-    qsk, qpc = api.sketch(q_rp, q_col, c.d, N, 4)
-    tsk, tpc = api.sketch(t_rp, t_col, c.d, N, 4)
-    est = torch.empty((4, q.n, t.n), dtype=torch.float32, device="cuda")
-    B.bs_estimate_pairs(qsk, qpc, q.n, tsk, tpc, t.n, N, 15, est, None)
-    e = est.cpu().numpy().astype(np.float64)
+    assert np.array_equal(u32(cnt).astype(np.float64), ex[:, :, 0])
+    # the estimates both sides threshold: the oracle's, from its own sketches,
+    # rounded to the FP32 the GPU path keeps them in
+    oqs, _ = oracle.sketch(q.row_ptr, q.col, c.d, N, 4)
+    ots, _ = oracle.sketch(t.row_ptr, t.col, c.d, N, 4)
+    e32 = oracle.estimate_pairs(oqs, ots, N)[0].astype(np.float32)
+    est = torch.from_numpy(e32).cuda()
+    e = e32.astype(np.float64)
     max_ip = float(ex[:, :, 0].max())
     cases = [("js", 2, ranking.THRESHOLDS), ("cos", 3, ranking.THRESHOLDS),
              ("ip", 0, tuple(f * max_ip for f in ranking.THRESHOLDS)), ("ham", 1, (5.0, 40.0, 200.0, 400.0))]

@@ -63,7 +63,8 @@ def test_mixed_equals_alone(served):
 def test_served_results_match_oracle(served):
     db_csr, db, reqs = served
     res, _ = _serve(db, reqs, slots=2, max_q=256)
-    dsk = u32(db.sketch)
+    dsk, _ = oracle.sketch(db_csr.row_ptr, db_csr.col, db_csr.d, N, seed=5)
+    assert np.array_equal(u32(db.sketch), dsk)
     for r in [reqs[1], reqs[4], reqs[9]]:
         qsk, _ = oracle.sketch(r.row_ptr, r.col, db_csr.d, N, seed=5)
         oest, _ = oracle.estimate_pairs(qsk, dsk, N)

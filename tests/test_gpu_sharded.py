@@ -4,6 +4,7 @@ indices and bit-identical scores -- for both pair-counting kernels, in
 all-pairs mode (self pair excluded through the shard offset) and in
 query-vs-database mode, with ragged shards and a shard smaller than k.  The
 merged lists are also checked against the FP64 oracle."""
+import numpy as np
 import pytest
 
 import oracle
@@ -24,6 +25,12 @@ def _sketch(seed, n, N):
     rp, col = to_dev(c)
     sk, pc = api.sketch(rp, col, c.d, N, 7)
     return sk, pc
+
+
+def _oracle_sketch(seed, n, N):
+    """The oracle's own sketches of the batch _sketch(seed, n, N) sketches."""
+    c = inputs.random_csr(seed, n, 50_000, 1, 400)
+    return oracle.sketch(c.row_ptr, c.col, c.d, N, 7)[0]
 
 
 def _unsharded(Q, pcQ, DB, pcDB, N, by, k, excl, variant):
@@ -79,7 +86,9 @@ def test_query_vs_sharded_db_matches_oracle(variant):
     ref_s, ref_i = _unsharded(q, pq, db, pdb, N, B.BS_JS, k, False, v)
     got_s, got_i = _sharded(q, pq, db, pdb, N, B.BS_JS, k, False, v, bounds)
     assert torch.equal(got_i, ref_i) and torch.equal(got_s, ref_s)
-    est, _ = oracle.estimate_pairs(u32(q), u32(db), N)
+    oq, odb = _oracle_sketch(22, 333, N), _oracle_sketch(21, 3000, N)
+    assert np.array_equal(u32(q), oq) and np.array_equal(u32(db), odb)
+    est, _ = oracle.estimate_pairs(oq, odb, N)
     gs, gi = got_s.cpu().numpy(), u32(got_i)
     for r in range(0, 333, 7):
         check_topk_row(gs[r], gi[r], est[oracle.JS][r], k, oracle.JS)
