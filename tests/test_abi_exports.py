@@ -70,3 +70,35 @@ def test_tensor_core_plan_parts_match_the_persistent_schedule():
         uses_tc, splits, launches = B.bs_topk_plan(nq, ndb, 4096, 50, B.BS_VARIANT_TC, nq == ndb)
         assert uses_tc and splits == parts(nq, ndb), (nq, ndb, splits, parts(nq, ndb))
         assert launches == 1 + (splits > 1) + (1 if nq == ndb else 2)
+
+
+def test_header_is_plain_c_and_a_c_program_links(tmp_path):
+    # the boundary is usable from C: the header compiles as pedantic C99, a
+    # program taking the address of every declared function links against the
+    # library, and its host-only calls run without a GPU
+    import subprocess
+    build.build()
+    decl = declared_functions()
+    src = tmp_path / "caller.c"
+    src.write_text(
+        '#include <inttypes.h>\n#include <stdio.h>\n#include "binsketch.h"\n'
+        "typedef void (*any_fn)(void);\n"
+        "static any_fn table[] = {" + ", ".join(f"(any_fn){n}" for n in decl) + "};\n"
+        "int main(void) {\n"
+        "    uint64_t m = 0, a = 0;\n"
+        "    bs_hash_params(12345, &m, &a);\n"
+        '    printf("%d %zu %" PRIu64 " %" PRIu64 " %s\\n", bs_version(), sizeof(table) / sizeof(table[0]),\n'
+        "           m, a, bs_status_string(BS_ERR_ROWPTR));\n"
+        "    return 0;\n}\n")
+    lib_dir = os.path.dirname(binding.LIB_PATH)
+    exe = tmp_path / "caller"
+    r = subprocess.run(["gcc", "-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror", "-I",
+                        os.path.join(ROOT, "include"), str(src), "-L", lib_dir, "-lbinsketch",
+                        f"-Wl,-rpath,{lib_dir}", "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    ver, n, m, a, *status = out.stdout.split()
+    assert int(ver) >= 100 and int(n) == len(decl)
+    assert (int(m), int(a)) == oracle.hash_params(12345)
+    assert " ".join(status) == "malformed row offsets"
