@@ -93,3 +93,32 @@ def test_latency_stats():
     st = latency_stats(res)
     assert st["requests"] == 3 and st["queries"] == 12
     assert st["p50_ms"] >= 0 and st["p99_ms"] >= st["p50_ms"]
+
+
+def test_arena_random_alloc_release_keeps_its_invariants():
+    # live ranges never overlap and stay aligned, free + live = size, and
+    # releasing everything leaves one free range covering the arena
+    rng = np.random.default_rng(7)
+    size = 1 << 20
+    for _ in range(20):
+        a = Arena(size)
+        live = {}
+        for step in range(400):
+            if live and (rng.random() < 0.45 or len(live) > 60):
+                off = list(live)[int(rng.integers(len(live)))]
+                a.release(off, live.pop(off))
+            else:
+                n = int(rng.integers(1, 60_000))
+                off = a.alloc(n)
+                if off is None:
+                    assert all(ln < a._round(n) for _, ln in a.free)   # first fit found no hole
+                    continue
+                assert off % Arena.ALIGN == 0 and off + a._round(n) <= size
+                live[off] = n
+            spans = sorted((o, o + a._round(n)) for o, n in live.items())
+            assert all(e <= s for (_, e), (s, _) in zip(spans, spans[1:]))
+            assert a.free_bytes + sum(a._round(n) for n in live.values()) == size
+            assert all(o1 + l1 < o2 for (o1, l1), (o2, _) in zip(a.free, a.free[1:]))   # coalesced
+        for off, n in list(live.items()):
+            a.release(off, n)
+        assert a.free == [(0, size)]
