@@ -156,6 +156,25 @@ bs_status bs_estimate_pairs(const uint32_t *A, const uint32_t *pcA, uint32_t nA,
                             uint32_t measures, float *out, uint32_t *counts, bs_stream_t stream);
 
 /*
+ * bs_estimate_pairs_ex -- bs_estimate_pairs with an explicit choice of the
+ * pair-counting kernel (same results, bit for bit in the counts):
+ *   BS_VARIANT_TC    the common-bit counts on the tensor cores (0/1 bits
+ *                    widened to E2M1 elements of a block-scaled FP4 MMA with
+ *                    unit scales, exact FP32 accumulation), reading the
+ *                    row-major sketches directly: N % 128 == 0,
+ *                    256 <= N <= 8192, 16-byte aligned A and B
+ *                    (BS_ERR_UNSUPPORTED otherwise);
+ *   BS_VARIANT_POPC  AND + population count on the CUDA cores, any N;
+ *   BS_VARIANT_AUTO  the tensor cores where they apply, else POPC (what
+ *                    bs_estimate_pairs does; BS_VARIANT=popc in the
+ *                    environment forces POPC).
+ */
+bs_status bs_estimate_pairs_ex(const uint32_t *A, const uint32_t *pcA, uint32_t nA,
+                               const uint32_t *B, const uint32_t *pcB, uint32_t nB, uint32_t N,
+                               uint32_t measures, float *out, uint32_t *counts, uint32_t variant,
+                               bs_stream_t stream);
+
+/*
  * bs_topk_workspace_bytes -- device workspace bs_topk / bs_topk_ex need for
  * this shape, whichever kernel runs: partial top-k lists when a query row's
  * database is divided between blocks (the CUDA-core kernel splits the
@@ -199,16 +218,18 @@ bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
  * computed differs:
  *   BS_VARIANT_POPC  AND + population count on 32-bit words (CUDA cores),
  *                    any N and k;
- *   BS_VARIANT_TC    0/1 bits widened to FP8 and multiplied on the tensor
- *                    cores (tcgen05.mma, exact FP32 accumulation), for
- *                    N % 128 == 0, 256 <= N <= 8192, k <= 100 and 16-byte
- *                    aligned Q and DB; BS_ERR_UNSUPPORTED otherwise;
+ *   BS_VARIANT_TC    0/1 bits widened to 4-bit E2M1 elements (1.0 / 0) and
+ *                    multiplied on the tensor cores (tcgen05.mma block-scaled
+ *                    FP4 with unit scales, exact FP32 accumulation), for
+ *                    N % 128 == 0, 256 <= N <= 8192, k up to the largest
+ *                    configuration's heap (k <= 121) and 16-byte aligned Q and
+ *                    DB; BS_ERR_UNSUPPORTED otherwise;
  *   BS_VARIANT_AUTO  the tensor-core kernel where it applies, else POPC
  *                    (this is what bs_topk does).
  * For the tensor-core kernel, BS_VARIANT_TC_CFG(c) OR-ed into `variant` picks
  * its block configuration c (an autotuner's knob): epilogue groups, operand
- * slots, and K bytes per row in a slot (128: one 128-bit k-chunk per slot;
- * 64 / 32: half / quarter k-chunks, so more slots fit the same memory):
+ * slots, and K bytes per row in a slot (128: 256 sketch bits per slot;
+ * 64 / 32: 128 / 64 bits, so more slots fit the same memory):
  *   c = 0: 2 groups, 3 slots x 128    c = 1: 2 groups, 2 slots x 128
  *   c = 2: 1 group,  3 slots x 128    c = 3: 1 group,  2 slots x 128
  *   c = 4: 2 groups, 4 slots x 64     c = 5: 2 groups, 8 slots x 32
@@ -223,14 +244,75 @@ bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
  * kernel applies and c fits k.
  * A configuration whose shared memory does not fit k returns
  * BS_ERR_UNSUPPORTED.  bs_topk_workspace_bytes() covers every variant.
+ *
+ * BS_VARIANT_INJECT_STALL OR-ed into a tensor-core request is a fault
+ * injector for testing failure detection, not for production: the kernel's
+ * MMA-issuing thread skips announcing its first finished accumulator (as if
+ * it had died), and every bounded wait of that launch gives up after about
+ * 2e6 cycles instead of 4e9.  The waiting warps then raise BS_ERR_TIMEOUT
+ * (read by bs_get_async_error), every role drains and exits, the kernel
+ * frees its tensor memory, and the call's outputs are unspecified.  The GPU
+ * context stays usable; the next call on the stream runs normally.
  */
 enum { BS_VARIANT_AUTO = 0, BS_VARIANT_POPC = 1, BS_VARIANT_TC = 2 };
 #define BS_VARIANT_TC_CFG(c) (((uint32_t)(c) + 1u) << 4)
+#define BS_VARIANT_INJECT_STALL 0x100u
 bs_status bs_topk_ex(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
                      const uint32_t *DB, const uint32_t *pcDB, uint32_t nDB, uint32_t N,
                      uint32_t by, uint32_t k, int exclude_self, float *score, uint32_t *idx,
                      void *workspace, size_t workspace_bytes, uint32_t variant,
                      bs_stream_t stream);
+
+/*
+ * bs_topk_batched -- bs_topk for many independent problems (datasets, each
+ * with its own sketches, N, rows and self-exclusion; one measure `by` and one
+ * k for all) in ONE persistent tensor-core launch: the work units (problem,
+ * 128-row query block, 240-row database tile) of all problems form one
+ * queue, cut into equal-cost contiguous ranges per SM, so small problems
+ * fill the gaps of large ones.  The ranking of every problem is that of
+ * bs_topk (Experiment 2, Sec. 4), index for index and bit for bit.
+ *  jobs        HOST array of n_jobs bs_topk_job (their pointers are device
+ *              memory); 1 <= n_jobs <= BS_TOPK_BATCH_MAX.  Every job needs
+ *              the tensor-core shape (N % 128 == 0, 256 <= N <= 8192, 16-byte
+ *              aligned Q and DB); exclude_self requires Q == DB, nQ == nDB.
+ *              A job with nQ == 0 is skipped; one with nDB == 0 and nQ > 0
+ *              is refused, as bs_topk_ex refuses it for the tensor-core
+ *              variant.
+ *  variant     BS_VARIANT_AUTO or BS_VARIANT_TC, optionally with
+ *              BS_VARIANT_TC_CFG(c): one block configuration for the launch
+ *  workspace   device memory of at least bs_topk_batched_workspace_bytes()
+ *              bytes, 256-byte aligned: tiled copies of every job's sketches
+ *              and the partial lists
+ * Launches: one re-layout kernel for all jobs, the persistent ranking kernel,
+ * and one merge kernel when some row block is split between SMs.
+ * Errors: BS_ERR_INVALID_ARG for n_jobs outside 1..BS_TOPK_BATCH_MAX, a bad
+ * measure or k, NULL arrays; BS_ERR_UNSUPPORTED for a job outside the
+ * tensor-core shape or a configuration that does not fit k;
+ * BS_ERR_NO_MEMORY for a short workspace.
+ */
+#define BS_TOPK_BATCH_MAX 64
+typedef struct {
+    const uint32_t *Q;      /* [nQ][N/32] query sketches */
+    const uint32_t *pcQ;    /* [nQ] */
+    const uint32_t *DB;     /* [nDB][N/32] database sketches */
+    const uint32_t *pcDB;   /* [nDB] */
+    float *score;           /* [nQ][k] out */
+    uint32_t *idx;          /* [nQ][k] out */
+    uint32_t nQ;
+    uint32_t nDB;
+    uint32_t N;
+    int exclude_self;
+} bs_topk_job;
+size_t bs_topk_batched_workspace_bytes(const bs_topk_job *jobs, uint32_t n_jobs, uint32_t k);
+bs_status bs_topk_batched(const bs_topk_job *jobs, uint32_t n_jobs, uint32_t by, uint32_t k,
+                          void *workspace, size_t workspace_bytes, uint32_t variant,
+                          bs_stream_t stream);
+/* bs_topk_batched_plan -- host only: *splits = partial lists per query row
+ * (the merge kernel runs when > 1), *launches = kernels one bs_topk_batched
+ * call launches (0 when every job is empty).  Errors as bs_topk_batched
+ * returns them for this table and k; either output may be NULL. */
+bs_status bs_topk_batched_plan(const bs_topk_job *jobs, uint32_t n_jobs, uint32_t k, uint32_t *splits,
+                               uint32_t *launches);
 
 /*
  * bs_topk_shard -- bs_topk_ex against one contiguous shard of a database that
@@ -299,7 +381,7 @@ bs_status bs_tile_sketches(const uint32_t *sketch, uint32_t n_rows, uint32_t N, 
  * bs_topk_pretiled -- bs_topk (tensor-core kernel) of nQ row-major query
  * sketches against a database kept tiled by bs_tile_sketches: the ranking of
  * Experiment 2 (Sec. 4) for a query stream against a resident corpus.
- * Requires N % 128 == 0, 256 <= N <= 8192, k <= 100 (BS_ERR_UNSUPPORTED
+ * Requires N % 128 == 0, 256 <= N <= 8192, k <= 121 (BS_ERR_UNSUPPORTED
  * otherwise); no self-exclusion.  Workspace: bs_topk_pretiled_workspace_bytes.
  */
 size_t bs_topk_pretiled_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k);
@@ -318,8 +400,13 @@ bs_status bs_topk_pretiled(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, 
  * BS_TOPK_NOALLOC_SCRATCH_BYTES inside the library, present on every GPU that
  * loads it until the process exits.  Shapes whose bs_topk_workspace_bytes()
  * exceeds that size are refused with BS_ERR_NO_MEMORY (nothing launched).
- * The array's address is looked up on the first call on each device (make
- * that call before any stream capture).  Calls share the array: calls whose
+ * The array is reserved on a device when the library's module holding it is
+ * first loaded there (CUDA loads device code lazily): at the first call made
+ * while that device is current, which also looks up its address and may
+ * synchronise.  Make that first call before the caller's own memory arena
+ * takes the whole device and before any stream capture; if the reservation
+ * fails the call returns BS_ERR_CUDA and leaves no CUDA error set for later
+ * calls.  Calls share the array: calls whose
  * kernels overlap on the GPU race on it and must be serialised by the caller.
  * Allocates nothing.
  */

@@ -27,7 +27,9 @@ def sketch(row_ptr: torch.Tensor, col: torch.Tensor, d: int, N: int, seed: int =
 
 
 def estimate_pairs(A, pcA, Bm, pcB, N: int, measures=("ip", "ham", "js", "cos"), counts=True,
-                   stream=None):
+                   stream=None, variant: str = "auto"):
+    """Counts and estimates of every (A row, B row) pair (bs_estimate_pairs_ex);
+    variant: "auto", "popc" or "tc"."""
     mask = 0
     for m in measures:
         mask |= B.MEASURE_BITS[m]
@@ -35,7 +37,7 @@ def estimate_pairs(A, pcA, Bm, pcB, N: int, measures=("ip", "ham", "js", "cos"),
     nm = bin(mask).count("1")
     out = torch.empty((nm, nA, nB), dtype=torch.float32, device=A.device) if nm else None
     cnt = torch.empty((nA, nB), dtype=torch.int32, device=A.device) if counts else None
-    B.bs_estimate_pairs(A, pcA, nA, Bm, pcB, nB, N, mask, out, cnt, stream)
+    B.bs_estimate_pairs_ex(A, pcA, nA, Bm, pcB, nB, N, mask, out, cnt, B.VARIANTS[variant], stream)
     return out, cnt
 
 

@@ -40,6 +40,18 @@ class bs_sketch_job(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("n_rows", ctypes.c_uint32), ("d", ctypes.c_uint32),
                 ("N", ctypes.c_uint32), ("pad_", ctypes.c_uint32), ("sketch", ctypes.c_void_p),
                 ("popcnt", ctypes.c_void_p)]
+
+
+class bs_topk_job(ctypes.Structure):
+    """Mirror of the C struct bs_topk_job (include/binsketch.h)."""
+    _fields_ = [("Q", ctypes.c_void_p), ("pcQ", ctypes.c_void_p), ("DB", ctypes.c_void_p),
+                ("pcDB", ctypes.c_void_p), ("score", ctypes.c_void_p), ("idx", ctypes.c_void_p),
+                ("nQ", ctypes.c_uint32), ("nDB", ctypes.c_uint32), ("N", ctypes.c_uint32),
+                ("exclude_self", ctypes.c_int)]
+
+
+BS_VARIANT_INJECT_STALL = 0x100
+BS_TOPK_BATCH_MAX = 64
 MEASURE_BITS = {"ip": BS_IP, "ham": BS_HAM, "js": BS_JS, "cos": BS_COS}
 BS_TOPK_K_MAX = 128
 BS_TOPK_MERGE_PARTS_MAX = 256
@@ -61,7 +73,11 @@ SIGNATURES = [
     ("bs_sketch_batched", _i32, [_vp, _u32, _u32, _vp]),
     ("bs_popcount_rows", _i32, [_vp, _u32, _u32, _vp, _vp]),
     ("bs_estimate_pairs", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp]),
+    ("bs_estimate_pairs_ex", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _vp, _vp, _u32, _vp]),
     ("bs_topk_workspace_bytes", _sz, [_u32, _u32, _u32, _u32]),
+    ("bs_topk_batched_workspace_bytes", _sz, [_vp, _u32, _u32]),
+    ("bs_topk_batched", _i32, [_vp, _u32, _u32, _u32, _vp, _sz, _u32, _vp]),
+    ("bs_topk_batched_plan", _i32, [_vp, _u32, _u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
     ("bs_topk", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, _i32, _vp, _vp, _vp,
                        _sz, _vp]),
     ("bs_topk_ex", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, _i32, _vp, _vp, _vp,
@@ -186,6 +202,57 @@ def bs_estimate_pairs(A, pcA, nA, B, pcB, nB, N, measures, out=None, counts=None
     o, c = _p(out, 4 * _nmeasures(measures) * pairs, "out"), _p(counts, 4 * pairs, "counts")
     _check(lib().bs_estimate_pairs(a, pa, nA, b, pb, nB, N, measures, o, c, _s(stream)),
            "bs_estimate_pairs")
+
+
+def bs_estimate_pairs_ex(A, pcA, nA, B, pcB, nB, N, measures, out=None, counts=None, variant=0,
+                         stream=None):
+    pairs = nA * nB
+    a, pa = _p(A, nA * (N // 8), "A"), _p(pcA, 4 * nA, "pcA")
+    b, pb = _p(B, nB * (N // 8), "B"), _p(pcB, 4 * nB, "pcB")
+    o, c = _p(out, 4 * _nmeasures(measures) * pairs, "out"), _p(counts, 4 * pairs, "counts")
+    _check(lib().bs_estimate_pairs_ex(a, pa, nA, b, pb, nB, N, measures, o, c, variant, _s(stream)),
+           "bs_estimate_pairs_ex")
+
+
+def _job_table(jobs):
+    """jobs: sequence of dicts with Q, pcQ, DB, pcDB, score, idx, nQ, nDB, N, exclude_self
+    (tensors or device addresses) -> a HOST ctypes array of bs_topk_job."""
+    arr = (bs_topk_job * len(jobs))()
+    for i, j in enumerate(jobs):
+        nQ, nDB, N = int(j["nQ"]), int(j["nDB"]), int(j["N"])
+        k = int(j.get("k", 0))
+        arr[i].Q = _p(j["Q"], nQ * (N // 8), "Q")
+        arr[i].pcQ = _p(j["pcQ"], 4 * nQ, "pcQ")
+        arr[i].DB = _p(j["DB"], nDB * (N // 8), "DB")
+        arr[i].pcDB = _p(j["pcDB"], 4 * nDB, "pcDB")
+        arr[i].score = _p(j["score"], 4 * nQ * k, "score")
+        arr[i].idx = _p(j["idx"], 4 * nQ * k, "idx")
+        arr[i].nQ, arr[i].nDB, arr[i].N = nQ, nDB, N
+        arr[i].exclude_self = int(bool(j.get("exclude_self", False)))
+    return arr
+
+
+def bs_topk_batched_workspace_bytes(jobs, k) -> int:
+    """jobs: a ctypes array from _job_table, or a sequence of job dicts."""
+    arr = jobs if isinstance(jobs, ctypes.Array) else _job_table(jobs)
+    return int(lib().bs_topk_batched_workspace_bytes(arr, len(arr), k))
+
+
+def bs_topk_batched(jobs, by, k, workspace=None, workspace_bytes=0, variant=0, stream=None):
+    """jobs: a sequence of job dicts (see _job_table; each with its k for the size checks)
+    or a prepared ctypes array of bs_topk_job."""
+    arr = jobs if isinstance(jobs, ctypes.Array) else _job_table([dict(j, k=k) for j in jobs])
+    _check(lib().bs_topk_batched(arr, len(arr), by, k, _p(workspace, workspace_bytes, "workspace"),
+                                 workspace_bytes, variant, _s(stream)), "bs_topk_batched")
+
+
+def bs_topk_batched_plan(jobs, k):
+    """(splits, launches) of a bs_topk_batched call on this job table."""
+    arr = jobs if isinstance(jobs, ctypes.Array) else _job_table(jobs)
+    s, l = _u32(), _u32()
+    _check(lib().bs_topk_batched_plan(arr, len(arr), k, ctypes.byref(s), ctypes.byref(l)),
+           "bs_topk_batched_plan")
+    return int(s.value), int(l.value)
 
 
 def bs_topk_workspace_bytes(nQ, nDB, N, k) -> int:

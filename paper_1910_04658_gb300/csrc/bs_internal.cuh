@@ -137,12 +137,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: returns false after ~4e9 SM cycles (about 2 s at full clock;
-// longer at lower clocks) without the phase completing.  The cycle counter is
-// read only after a burst of polls, so the common short wait costs nothing
-// beyond the polls themselves.
+// Bounded wait: returns false after `limit` SM cycles (default ~4e9, about
+// 2 s at full clock; longer at lower clocks) without the phase completing.
+// The cycle counter is read only after a burst of polls, so the common short
+// wait costs nothing beyond the polls themselves.
 constexpr long long kWaitLimitCycles = 4000000000ll;
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          long long limit = kWaitLimitCycles) {
 #pragma unroll 1
     for (int i = 0; i < 32; ++i)
         if (mbar_try_wait(bar, parity)) return true;
@@ -151,7 +152,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 #pragma unroll 1
         for (int i = 0; i < 32; ++i)
             if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - t0 > kWaitLimitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 
@@ -278,13 +279,33 @@ bool tc_supported(const uint32_t *Q, const uint32_t *DB, uint32_t N, uint32_t k)
 uint32_t tc_splits(uint32_t nQ, uint32_t nDB);
 // bytes of the k-chunk-tiled copy of an n-row sketch matrix
 size_t tc_tiled_bytes(uint32_t n, uint32_t N);
+// wait budget of the tensor-core kernel's bounded waits (cycles), and the
+// shortened budget of a fault-injected call
+constexpr long long kTcWaitLimit = kWaitLimitCycles;
+constexpr long long kTcInjectWaitLimit = 2000000ll;
 // tiled: scratch for the tiled copies, tc_tiled_bytes(nQ) + tc_tiled_bytes(nDB)
 // bytes (only the first part is used when Q and DB are the same matrix)
+// inject: test-only fault injection (0 = none, 1 = the MMA issuer never
+// announces its first accumulator; waits give up after kTcInjectWaitLimit)
 bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
                   const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
                   int exclude_self, uint32_t self_off, float *score, uint32_t *idx, float *ws_key,
                   uint32_t *ws_idx, uint32_t splits, void *tiled, const void *db_tiled, int cfg,
-                  unsigned int *err, cudaStream_t stream);
+                  uint32_t inject, unsigned int *err, cudaStream_t stream);
+// full count / estimate matrices on the tensor cores (N % 128 == 0, 256 <= N
+// <= 8192, 16-byte aligned A and B), reading the row-major sketches directly
+bool tc_store_supported(const uint32_t *A, const uint32_t *B, uint32_t N);
+bs_status estimate_tc(const uint32_t *A, const uint32_t *pcA, uint32_t nA, const uint32_t *B,
+                      const uint32_t *pcB, uint32_t nB, uint32_t N, uint32_t measures, float *out,
+                      uint32_t *counts, unsigned int *err, cudaStream_t stream);
+// batched tensor-core top-k: workspace bytes (0 when some job is not
+// supported) and the call
+size_t tc_batched_workspace(const bs_topk_job *jobs, uint32_t n, uint32_t k);
+// partial lists per row and non-empty jobs of a batch (host only)
+bs_status tc_batched_plan(const bs_topk_job *jobs, uint32_t n, uint32_t k, uint32_t *splits,
+                          uint32_t *jobs_run);
+bs_status topk_tc_batched(const bs_topk_job *jobs, uint32_t n, int measure, uint32_t k, void *workspace,
+                          size_t workspace_bytes, int cfg, unsigned int *err, cudaStream_t stream);
 // tensor-core block configuration chosen for k when none is requested; -1 if
 // no configuration fits
 int tc_default_cfg(uint32_t k);
@@ -292,5 +313,19 @@ bool tc_cfg_fits(int cfg, uint32_t k);
 bool tc_shape_ok(uint32_t N, uint32_t k);
 // row-major sketches [n][N/32] -> k-chunk tiles (N % 128 == 0)
 bs_status tile_sketches(const uint32_t *sk, uint32_t n, uint32_t N, void *tiled, cudaStream_t stream);
+
+// Batched merge of split lists: for job j, lists key[j]/ix[j] [splits][nQ[j]][k]
+// into score[j]/idx[j] [nQ[j]][k]; rows numbered job by job from row_base.
+struct MergeJobs {
+    const float *key[BS_TOPK_BATCH_MAX];
+    const uint32_t *ix[BS_TOPK_BATCH_MAX];
+    float *score[BS_TOPK_BATCH_MAX];
+    uint32_t *idx[BS_TOPK_BATCH_MAX];
+    uint32_t nQ[BS_TOPK_BATCH_MAX];
+    uint64_t row_base[BS_TOPK_BATCH_MAX + 1];
+    uint32_t njobs;
+};
+bs_status launch_merge_batched(int measure, const MergeJobs &jobs, uint32_t k, uint32_t splits,
+                               cudaStream_t stream);
 
 }  // namespace bs

@@ -18,6 +18,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "bs_internal.cuh"
@@ -437,6 +438,72 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Merge of the split lists of many problems in one launch (the batched
+// tensor-core top-k): one warp per query row, rows numbered problem by
+// problem (MergeJobs::row_base), the same merge as merge_topk_kernel.
+template <int M>
+__global__ void __launch_bounds__(256)
+    merge_batched_kernel(const __grid_constant__ MergeJobs mj, uint32_t k, uint32_t splits) {
+    __shared__ float skey[8][CAP];
+    __shared__ uint32_t sidx[8][CAP];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *key = skey[warp];
+    uint32_t *ix = sidx[warp];
+    const uint64_t rows = mj.row_base[mj.njobs];
+    for (uint64_t g = (uint64_t)blockIdx.x * 8 + warp; g < rows; g += (uint64_t)gridDim.x * 8) {
+        uint32_t lo = 0, hi = mj.njobs - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (mj.row_base[mid] <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const uint32_t nQ = mj.nQ[lo];
+        const uint32_t q = (uint32_t)(g - mj.row_base[lo]);
+        const float *ws_key = mj.key[lo];
+        const uint32_t *ws_idx = mj.ix[lo];
+        int cnt = 0;
+        float tk = -INFINITY;
+        uint32_t ti = NO_IDX;
+        for (uint32_t s = 0; s < splits; ++s) {
+            const size_t o = ((size_t)s * nQ + q) * k;
+            for (uint32_t t0 = 0; t0 < k; t0 += 32) {
+                const uint32_t t = t0 + lane;
+                float kk = -INFINITY;
+                uint32_t ii = NO_IDX;
+                if (t < k) {
+                    kk = ws_key[o + t];
+                    ii = ws_idx[o + t];
+                }
+                const bool take = t < k && ii != NO_IDX && better(kk, ii, tk, ti);
+                const uint32_t m = __ballot_sync(0xffffffffu, take);
+                const int slot = cnt + __popc(m & ((1u << lane) - 1u));
+                if (take && slot < CAP) {
+                    key[slot] = kk;
+                    ix[slot] = ii;
+                }
+                cnt += __popc(m);
+            }
+            __syncwarp();
+            if (cnt > CAP - (int)k) {
+                cnt = shrink_row(key, ix, cnt, (int)k, lane);
+                if (cnt == (int)k) {
+                    tk = key[k - 1];
+                    ti = ix[k - 1];
+                }
+            }
+        }
+        const int kept = shrink_row(key, ix, cnt, (int)k, lane);
+        float *score = mj.score[lo];
+        uint32_t *idx = mj.idx[lo];
+        for (uint32_t t = lane; t < k; t += 32) {
+            const float kk = (int)t < kept ? key[t] : -INFINITY;
+            score[(size_t)q * k + t] = (M == M_HAM) ? -kk : kk;
+            idx[(size_t)q * k + t] = (int)t < kept ? ix[t] : NO_IDX;
+        }
+        __syncwarp();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -527,6 +594,20 @@ bs_status launch_merge(int measure, const float *ws_key, const uint32_t *ws_idx,
     return merge_lists<false>(measure, ws_key, ws_idx, nQ, k, splits, score, idx, zero, st);
 }
 
+bs_status launch_merge_batched(int measure, const MergeJobs &mj, uint32_t k, uint32_t splits,
+                               cudaStream_t st) {
+    const uint64_t rows = mj.row_base[mj.njobs];
+    if (rows == 0) return BS_OK;
+    const uint32_t blocks = (uint32_t)std::min<uint64_t>((rows + 7) / 8, 65535u * 16u);
+    switch (measure) {
+        case M_IP: merge_batched_kernel<M_IP><<<blocks, 256, 0, st>>>(mj, k, splits); break;
+        case M_HAM: merge_batched_kernel<M_HAM><<<blocks, 256, 0, st>>>(mj, k, splits); break;
+        case M_JS: merge_batched_kernel<M_JS><<<blocks, 256, 0, st>>>(mj, k, splits); break;
+        default: merge_batched_kernel<M_COS><<<blocks, 256, 0, st>>>(mj, k, splits); break;
+    }
+    return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+}
+
 bs_status topk_popc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
                     const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
                     int exclude_self, uint32_t self_off, float *score, uint32_t *idx, float *ws_key,
@@ -570,18 +651,40 @@ static size_t ws_bytes(uint32_t splits, uint32_t nQ, uint32_t k) {
 
 using namespace bs;
 
+// Kernel choice forced by the environment for calls that leave it to the
+// library (BS_VARIANT_AUTO): BS_VARIANT=popc forces the CUDA-core kernel,
+// BS_VARIANT=tc<c> (c = 0..9) picks tensor-core configuration c where the
+// tensor-core kernel applies.  Read once.  Returns -2: not set, -1: POPC,
+// c >= 0: configuration c.
+static int env_variant() {
+    static std::once_flag once;
+    static int v = -2;
+    std::call_once(once, [] {
+        const char *e = getenv("BS_VARIANT");
+        if (!e) return;
+        if (!strcmp(e, "popc")) v = -1;
+        else if (e[0] == 't' && e[1] == 'c' && e[2] >= '0' && e[2] <= '9' && e[3] == 0) v = e[2] - '0';
+    });
+    return v;
+}
+
 extern "C" {
 
-bs_status bs_estimate_pairs(const uint32_t *A, const uint32_t *pcA, uint32_t nA, const uint32_t *B,
-                            const uint32_t *pcB, uint32_t nB, uint32_t N, uint32_t measures,
-                            float *out, uint32_t *counts, bs_stream_t stream) {
-    if (!valid_N(N) || (measures & ~15u)) return BS_ERR_INVALID_ARG;
+bs_status bs_estimate_pairs_ex(const uint32_t *A, const uint32_t *pcA, uint32_t nA, const uint32_t *B,
+                               const uint32_t *pcB, uint32_t nB, uint32_t N, uint32_t measures,
+                               float *out, uint32_t *counts, uint32_t variant, bs_stream_t stream) {
+    if (!valid_N(N) || (measures & ~15u) || variant > BS_VARIANT_TC) return BS_ERR_INVALID_ARG;
     if (nA == 0 || nB == 0) return BS_OK;
     if (!A || !B || !pcA || !pcB) return BS_ERR_INVALID_ARG;
     if (measures && !out) return BS_ERR_INVALID_ARG;
     if (!measures && !counts) return BS_OK;
     unsigned int *err = error_word();
     if (!err) return BS_ERR_CUDA;
+    if (variant == BS_VARIANT_AUTO && env_variant() == -1) variant = BS_VARIANT_POPC;
+    const bool tc_ok = tc_store_supported(A, B, N);
+    if (variant == BS_VARIANT_TC && !tc_ok) return BS_ERR_UNSUPPORTED;
+    if (variant != BS_VARIANT_POPC && tc_ok)
+        return estimate_tc(A, pcA, nA, B, pcB, nB, N, measures, out, counts, err, (cudaStream_t)stream);
     PairArgs p = {};
     p.Q = A; p.DB = B; p.pcQ = pcA; p.pcDB = pcB;
     p.nQ = nA; p.nDB = nB; p.N = N; p.W = N / 32; p.nK = (p.W + KC - 1) / KC;
@@ -591,6 +694,12 @@ bs_status bs_estimate_pairs(const uint32_t *A, const uint32_t *pcA, uint32_t nA,
     dim3 grid((nA + BM - 1) / BM, (nB + BN - 1) / BN);
     if (grid.y > 65535) return BS_ERR_UNSUPPORTED;
     return launch_pairs<MODE_ESTIMATE, 0>(p, grid, (cudaStream_t)stream);
+}
+
+bs_status bs_estimate_pairs(const uint32_t *A, const uint32_t *pcA, uint32_t nA, const uint32_t *B,
+                            const uint32_t *pcB, uint32_t nB, uint32_t N, uint32_t measures,
+                            float *out, uint32_t *counts, bs_stream_t stream) {
+    return bs_estimate_pairs_ex(A, pcA, nA, B, pcB, nB, N, measures, out, counts, BS_VARIANT_AUTO, stream);
 }
 
 // Workspace of one top-k call: the per-split lists (when the database is split
@@ -613,23 +722,6 @@ size_t bs_topk_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k
     return need;
 }
 
-// Kernel choice forced by the environment for calls that leave it to the
-// library (BS_VARIANT_AUTO): BS_VARIANT=popc forces the CUDA-core kernel,
-// BS_VARIANT=tc<c> (c = 0..9) picks tensor-core configuration c where the
-// tensor-core kernel applies.  Read once.  Returns -2: not set, -1: POPC,
-// c >= 0: configuration c.
-static int env_variant() {
-    static std::once_flag once;
-    static int v = -2;
-    std::call_once(once, [] {
-        const char *e = getenv("BS_VARIANT");
-        if (!e) return;
-        if (!strcmp(e, "popc")) v = -1;
-        else if (e[0] == 't' && e[1] == 'c' && e[2] >= '0' && e[2] <= '9' && e[3] == 0) v = e[2] - '0';
-    });
-    return v;
-}
-
 static bs_status topk_impl(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
                            const uint32_t *pcDB, uint32_t nDB, uint32_t N, uint32_t by, uint32_t k,
                            int exclude_self, uint32_t self_off, float *score, uint32_t *idx,
@@ -638,7 +730,10 @@ static bs_status topk_impl(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, 
     if (!valid_N(N)) return BS_ERR_INVALID_ARG;
     if (k == 0 || k > BS_TOPK_K_MAX) return BS_ERR_INVALID_ARG;
     const int m = measure_code(by);
+    const uint32_t inject = (variant & BS_VARIANT_INJECT_STALL) ? 1u : 0u;
+    variant &= ~BS_VARIANT_INJECT_STALL;
     int tc_cfg = (int)((variant >> 4) & 15u) - 1;   // -1: default configuration
+    if (variant >> 8) return BS_ERR_INVALID_ARG;
     variant &= 15u;
     if (m < 0 || variant > BS_VARIANT_TC || tc_cfg > 9) return BS_ERR_INVALID_ARG;
     if (variant == BS_VARIANT_AUTO && tc_cfg < 0) {
@@ -659,6 +754,7 @@ static bs_status topk_impl(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, 
     } else if (variant == BS_VARIANT_AUTO) {
         use_tc = nDB > 0 && tc_supported(Q, DB, N, k);
     }
+    if (inject && !use_tc) return BS_ERR_UNSUPPORTED;   // the injector lives in the tensor-core kernel
     const uint32_t splits = use_tc ? tc_splits(nQ, nDB) : popc_splits(nQ, nDB);
     const size_t need = use_tc ? tc_workspace(nQ, nDB, N, k, splits) : ws_bytes(splits, nQ, k);
     float *ws_key = nullptr;
@@ -675,7 +771,7 @@ static bs_status topk_impl(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, 
         tiled = w + align256(ws_bytes(splits, nQ, k));
     }
     bs_status s1 = use_tc ? topk_tc(Q, pcQ, nQ, DB, pcDB, nDB, N, m, k, exclude_self, self_off, score,
-                                    idx, ws_key, ws_idx, splits, tiled, nullptr, tc_cfg, err, st)
+                                    idx, ws_key, ws_idx, splits, tiled, nullptr, tc_cfg, inject, err, st)
                           : topk_popc(Q, pcQ, nQ, DB, pcDB, nDB, N, m, k, exclude_self, self_off,
                                       score, idx, ws_key, ws_idx, splits, err, st);
     if (s1 != BS_OK || splits <= 1) return s1;
@@ -787,9 +883,44 @@ bs_status bs_topk_pretiled(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, 
     }
     void *tiled = w + align256(ws_bytes(splits, nQ, k));
     bs_status s1 = topk_tc(Q, pcQ, nQ, nullptr, pcDB, nDB, N, m, k, 0, 0, score, idx, ws_key,
-                           ws_idx, splits, tiled, DB_tiled, -1, err, st);
+                           ws_idx, splits, tiled, DB_tiled, -1, 0, err, st);
     if (s1 != BS_OK || splits <= 1) return s1;
     return launch_merge(m, ws_key, ws_idx, nQ, k, splits, score, idx, st);
+}
+
+size_t bs_topk_batched_workspace_bytes(const bs_topk_job *jobs, uint32_t n_jobs, uint32_t k) {
+    if (!jobs || n_jobs == 0 || n_jobs > BS_TOPK_BATCH_MAX || k == 0 || k > BS_TOPK_K_MAX) return 0;
+    return tc_batched_workspace(jobs, n_jobs, k);
+}
+
+bs_status bs_topk_batched_plan(const bs_topk_job *jobs, uint32_t n_jobs, uint32_t k, uint32_t *splits,
+                               uint32_t *launches) {
+    if (!jobs || n_jobs == 0 || n_jobs > BS_TOPK_BATCH_MAX) return BS_ERR_INVALID_ARG;
+    if (k == 0 || k > BS_TOPK_K_MAX) return BS_ERR_INVALID_ARG;
+    for (uint32_t i = 0; i < n_jobs; ++i)
+        if (!valid_N(jobs[i].N)) return BS_ERR_INVALID_ARG;
+    uint32_t s = 1, nj = 0;
+    const bs_status st = tc_batched_plan(jobs, n_jobs, k, &s, &nj);
+    if (st != BS_OK) return st;
+    if (splits) *splits = s;
+    if (launches) *launches = nj == 0 ? 0 : 2 + (s > 1 ? 1 : 0);
+    return BS_OK;
+}
+
+bs_status bs_topk_batched(const bs_topk_job *jobs, uint32_t n_jobs, uint32_t by, uint32_t k,
+                          void *workspace, size_t workspace_bytes, uint32_t variant,
+                          bs_stream_t stream) {
+    if (!jobs || n_jobs == 0 || n_jobs > BS_TOPK_BATCH_MAX) return BS_ERR_INVALID_ARG;
+    if (k == 0 || k > BS_TOPK_K_MAX) return BS_ERR_INVALID_ARG;
+    const int m = measure_code(by);
+    const int cfg = (int)((variant >> 4) & 15u) - 1;
+    if (m < 0 || (variant >> 8) || cfg > 9) return BS_ERR_INVALID_ARG;
+    if ((variant & 15u) != BS_VARIANT_AUTO && (variant & 15u) != BS_VARIANT_TC) return BS_ERR_INVALID_ARG;
+    for (uint32_t i = 0; i < n_jobs; ++i)
+        if (!valid_N(jobs[i].N)) return BS_ERR_INVALID_ARG;
+    unsigned int *err = error_word();
+    if (!err) return BS_ERR_CUDA;
+    return topk_tc_batched(jobs, n_jobs, m, k, workspace, workspace_bytes, cfg, err, (cudaStream_t)stream);
 }
 
 bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,

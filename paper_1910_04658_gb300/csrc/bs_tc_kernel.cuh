@@ -1,0 +1,1046 @@
+// Pair counting on the 5th-generation tensor cores, fused with the estimates
+// and either the per-query top-k (Experiment 2 as top-k) or a store of the
+// full count / estimate matrices (Alg. 1 step 2, Alg. 1-4).
+//
+// The common-bit count <a_s, b_s> is a dot product of two 0/1 vectors, i.e.
+// one entry of the product Q * DB^T of the 0/1 sketch matrices.  Packed bits
+// cannot feed tcgen05.mma directly (there is no 1-bit kind, and kind::i8 is
+// not available on sm_103a), so every bit is widened in shared memory to one
+// 4-bit E2M1 element of a block-scaled FP4 MMA (kind::mxf4): a set bit becomes
+// 0x2 = 1.0, a clear bit 0, and every 32-element block carries the unit scale
+// UE8M0 127 = 2^0, held once in TMEM.  Products are 0 or 1 and every partial
+// sum is an integer <= N <= 8192 < 2^24, so the FP32 accumulator IS the exact
+// count.  A 32-bit word w of a row becomes the 16 bytes
+// ((w << 1) & M, w & M, (w >> 1) & M, (w >> 2) & M) with M = 0x22222222 --
+// bit 4i + t of w lands in nibble i of output word t -- which permutes the K
+// order identically for both operands; a dot product does not see it.
+//
+// Block (one per SM, persistent): a job table (one job for a single call,
+// up to BS_TOPK_BATCH_MAX for the batched form) is cut into work units
+// (job, 128-row query block, 240-row database tile), numbered job by job and
+// row block by row block; block c takes the contiguous range
+// [block_start[c], block_start[c+1]) that the host balanced by cost.  A row
+// block cut between blocks yields one partial list per block ("part"), merged
+// afterwards.
+//   warp 0     TMEM owner (512 columns: two 240-column accumulators and the
+//              unit scale factors) and single-thread MMA issuer:
+//              tcgen05.mma.kind::mxf4.block_scale (M=128, N=240, K=64), four
+//              per 128-byte operand slot
+//   warps 1-4  fetch the packed bits of up to three rows each (query row e,
+//              database rows e and e + 128 of the tile) and widen them into
+//              the swizzled K-major FP4 layout the MMA descriptors point at.
+//              The fetches read a k-chunk-tiled copy of the sketches (128
+//              rows x 16 bytes contiguous per k-chunk), so a warp's load is
+//              512 contiguous bytes; four k-chunks are in flight per thread.
+//   warps 5+   epilogue, one or two groups of 4 warps, one query row per
+//              thread, 32 TMEM columns per tcgen05.ld.  Top-k: a closed-form
+//              bound on the union count admits only pairs that can beat the
+//              row's current k-th best, whose exact FP32 estimate then enters
+//              a per-row heap in shared memory.  Store: the count and the
+//              requested estimates of every pair are written out.
+// All waits are bounded (mbarrier try_wait against a cycle budget carried in
+// the arguments); a timeout raises BS_ERR_TIMEOUT, the block drains its
+// outstanding MMAs (again bounded), frees its TMEM and exits instead of
+// hanging.
+#pragma once
+
+#include <math.h>
+
+#include "bs_internal.cuh"
+
+namespace bs {
+namespace tc {
+
+constexpr int BM = 128;                    // query rows per block (UMMA M, TMEM lanes)
+constexpr int BN = 240;                    // database rows per tile (UMMA N)
+constexpr int BNP = 256;                   // per-column arrays padded to whole 32-column chunks
+constexpr int KCW = 4;                     // packed words per k-chunk (128 bits)
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t SF_COL = 2 * BN;        // 480: unit scale factors (A at +0, B at +16)
+constexpr int MAXG = 192;                  // most persistent blocks per launch
+constexpr int MAXJ = BS_TOPK_BATCH_MAX;    // most jobs per batched launch
+constexpr int MODE_TOPK = 0, MODE_STORE = 1;
+enum { INJECT_NONE = 0, INJECT_STALL = 1 };
+
+// threads per block with NG epilogue groups
+__host__ __device__ constexpr int threads_for(int NG) { return 32 * (5 + 4 * NG); }
+
+// Operand slot geometry for SK bytes of K per row.  One FP4 byte holds two
+// sketch bits, so a slot covers 2 SK bits: SK = 128 two 128-bit k-chunks
+// (128-byte swizzle), SK = 64 one k-chunk, SK = 32 half a k-chunk (64- and
+// 32-byte swizzles, so the same shared memory holds 2x / 4x as many slots).
+template <int SK>
+struct Geo {
+    static_assert(SK == 128 || SK == 64 || SK == 32, "slot width");
+    static constexpr int A = BM * SK;                       // query operand bytes
+    static constexpr int B = BN * SK;                       // database operand bytes
+    static constexpr int BYTES = A + B;                     // per slot
+    static constexpr int MMAS = SK / 32;                    // K = 64 (32 bytes) per MMA
+    static constexpr int WPS = SK / 16;                     // packed words per slot and row
+    static constexpr int SHIFT = SK == 128 ? 0 : (SK == 64 ? 1 : 2);
+    static constexpr uint64_t LAYOUT = SK == 128 ? 2 : (SK == 64 ? 4 : 6);   // descriptor swizzle code
+    static_assert(BYTES % (8 * SK) == 0 && A % (8 * SK) == 0, "swizzle atom alignment");
+};
+// k-chunks a tile's sweep covers (SK = 128 pairs them, so odd counts pad)
+template <int SK>
+__host__ __device__ __forceinline__ uint32_t kchunks_padded(uint32_t nKc) {
+    return SK == 128 ? ((nKc + 1) & ~1u) : nKc;
+}
+// operand slots per tile
+template <int SK>
+__host__ __device__ __forceinline__ uint32_t slots_per_tile(uint32_t nKc) {
+    return kchunks_padded<SK>(nKc) * KCW / (uint32_t)Geo<SK>::WPS;
+}
+
+constexpr int CB = 8;                      // admitted pairs a row buffers within a tile
+constexpr uint32_t NO_IDX = 0xFFFFFFFFu;
+// Admit when U' >= bound * (1 - 2^-13).  U' is an exact integer and the bound
+// carries ~1e-6 relative FP32 error (ex2.approx, the row constants, the key it
+// was derived from), so 1.2e-4 keeps every pair whose FP32 key beats the
+// threshold (checked against emulated FP32 keys one ulp above it) while
+// letting through almost none that fall a full count short.
+constexpr float FILTER_SLACK = 0.99987793f;
+
+// Shared-memory layout for NOP operand slots and NG epilogue groups (offsets
+// from the 1024-aligned base); the NG heaps of k entries per row follow.
+template <int NOP, int NG, int SK>
+struct Smem {
+    static constexpr int op = 0;
+    static constexpr int col = op + NOP * Geo<SK>::BYTES;       // [2 tiles][3][BNP] floats
+    static constexpr int bars = col + 2 * 3 * BNP * 4;
+    static constexpr int thr = bars + 256;                      // [NG][BM] key, idx, size
+    static constexpr int lock = thr + NG * BM * 12;             // [BM] shared-heap row locks
+    static constexpr int cbuf = lock + BM * 4;                  // [NG][CB][BM] admitted pairs
+    static constexpr int heap = cbuf + NG * CB * BM * 4;
+    static_assert((2 * NOP + 5) * 8 + 8 <= 256, "barrier area");
+};
+
+// One problem of the job table: nQ query rows against nDB database rows.
+struct Job {
+    const uint4 *Q, *DB;        // k-chunk-tiled sketches [ceil(n/128)][nKc][128] x 16 bytes,
+                                // or row-major [n][nKc] x 16 bytes when rowmajor
+    const uint32_t *pcQ, *pcDB;
+    float *score;               // top-k, splits == 1: [nQ][k]
+    uint32_t *idx;
+    float *ws_key;              // top-k, splits > 1: [splits][nQ][k]
+    uint32_t *ws_idx;
+    float *out;                 // store: [planes][nQ][nDB]
+    uint32_t *counts;           // store: [nQ][nDB] or NULL
+    uint64_t unit_base;         // first work unit of this job
+    uint32_t nQ, nDB, N, nKc;
+    uint32_t rbs, tiles;        // row blocks, database tiles
+    uint32_t self_off;          // exclude_self drops the pair q == self_off + j
+    int exclude_self;
+    uint32_t rowmajor;          // operands read in the caller's row-major layout
+    float invL;                 // 1 / ln(1 - 1/N)
+    float log2N;
+};
+
+template <int NJ>
+struct Args {
+    Job job[NJ];
+    uint64_t block_start[MAXG + 1];   // block c: units [block_start[c], block_start[c+1])
+    uint32_t njobs;
+    uint32_t k, splits;               // top-k: list length, parts per row list
+    uint32_t measures;                // store: BS_IP | BS_HAM | BS_JS | BS_COS
+    uint32_t inject;                  // INJECT_STALL: test-only fault injection
+    long long wait_limit;             // cycles a wait may take before it gives up
+    unsigned int *err;
+};
+
+// ---- tcgen05 wrappers -------------------------------------------------------
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// D (+)= A * B with per-32-element block scales read from TMEM
+__device__ __forceinline__ void mma_fp4(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t sfa, uint32_t sfb, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%5], [%6], p;\n\t}\n" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "r"(sfa), "r"(sfb)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 (or 16) consecutive TMEM columns of this thread's lane; completes at tmem_wait()
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 16; i < 32; ++i) r[i] = 0u;
+}
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// 32 columns of this warp's 32 lanes set to one value
+__device__ __forceinline__ void tmem_fill32(uint32_t taddr, uint32_t v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+        "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+        "r"(v)
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, SK-byte swizzle, 8-row groups
+// 8 * SK bytes apart (SBO), leading offset unused for this layout (1).
+template <int SK>
+__device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;                     // LBO (ignored for swizzled K-major)
+    d |= (uint64_t)((8 * SK) >> 4) << 32;       // SBO
+    d |= (uint64_t)1 << 46;                     // descriptor version for tcgen05
+    d |= Geo<SK>::LAYOUT << 61;                 // swizzle mode
+    return d;
+}
+
+// Instruction descriptor of the block-scaled MMA: A = B = E2M1 (code 1 of the
+// mxf4 kind), both K-major, scale factors UE8M0 (bit 23), N = 240, M = 128,
+// scale-factor selectors 0, dense K = 64.
+constexpr uint32_t IDESC = (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | (1u << 23) |
+                           ((uint32_t)(BM >> 4) << 24);
+constexpr uint32_t UNIT_SCALES = 0x7F7F7F7Fu;   // four UE8M0 2^0
+
+// Widen WPS packed words x[] of one row into FP4 and store them into the
+// SK-byte-swizzled K-major tile: row r at (r / 8) * 8 SK + (r % 8) * SK, the
+// 16-byte chunk of word c at position c ^ ((r % 8) >> SHIFT).
+template <int SK>
+__device__ __forceinline__ void widen_store(uint8_t *op_tile, int r, const uint32_t *x) {
+    uint8_t *row = op_tile + (r >> 3) * (8 * SK) + (r & 7) * SK;
+    const int sw = (r & 7) >> Geo<SK>::SHIFT;
+#pragma unroll
+    for (int c = 0; c < Geo<SK>::WPS; ++c) {
+        const uint32_t v = x[c];
+        uint4 o;
+        o.x = (v << 1) & 0x22222222u;
+        o.y = v & 0x22222222u;
+        o.z = (v >> 1) & 0x22222222u;
+        o.w = (v >> 2) & 0x22222222u;
+        *reinterpret_cast<uint4 *>(row + ((c ^ sw) << 4)) = o;
+    }
+}
+
+// ---- per-row heap of the k best (root = worst), interleaved across rows ------
+struct Heap {
+    float *key;      // key[i * BM + t]
+    uint32_t *ix;
+    int t, size, cap;
+    __device__ float k_at(int i) const { return key[i * BM + t]; }
+    __device__ uint32_t i_at(int i) const { return ix[i * BM + t]; }
+    __device__ void put(int i, float kk, uint32_t ii) { key[i * BM + t] = kk; ix[i * BM + t] = ii; }
+    // append and sift up: parents that rank below the new entry move down
+    __device__ void push(float kk, uint32_t ii) {
+        int i = size++;
+        while (i > 0) {
+            const int p = (i - 1) >> 1;
+            const float pk = k_at(p);
+            const uint32_t pi = i_at(p);
+            if (!better(pk, pi, kk, ii)) break;
+            put(i, pk, pi);
+            i = p;
+        }
+        put(i, kk, ii);
+    }
+    // sift (kk, ii) down from slot i over the first n slots: the worse child
+    // moves up while the new entry ranks above it
+    __device__ void sift_down(int i, float kk, uint32_t ii, int n) {
+        for (;;) {
+            const int l = 2 * i + 1;
+            if (l >= n) break;
+            int m = l;
+            float mk = k_at(l);
+            uint32_t mi = i_at(l);
+            if (l + 1 < n) {
+                const float rk = k_at(l + 1);
+                const uint32_t ri = i_at(l + 1);
+                if (better(mk, mi, rk, ri)) { m = l + 1; mk = rk; mi = ri; }
+            }
+            if (!better(kk, ii, mk, mi)) break;
+            put(i, mk, mi);
+            i = m;
+        }
+        put(i, kk, ii);
+    }
+    __device__ void replace_root(float kk, uint32_t ii) { sift_down(0, kk, ii, size); }
+    // in-place heapsort: best first in slots [0, size)
+    __device__ void sort_best_first() {
+        for (int end = size - 1; end > 0; --end) {
+            const float rk = k_at(0);
+            const uint32_t ri = i_at(0);
+            const float ek = k_at(end);
+            const uint32_t ei = i_at(end);
+            put(end, rk, ri);
+            sift_down(0, ek, ei, end);
+        }
+    }
+};
+
+// Per-row constants of the admission bound (see make_filter).
+struct RowFilter {
+    float c0, c1;
+    bool all;       // heap not full (or bound not applicable): admit everything
+};
+
+// Bound on U' = N - min(a+b-c, N-1) that a pair must reach to beat key theta:
+//   JS : log2 U' >= (log2 A' + log2 B' + (theta-1) log2 N) / (1 + theta)   (theta > -1/2)
+//   COS: log2 U' >= (theta s_a s_b - s_a^2 - s_b^2) / ln 2 + log2 N,  s = sqrt(-ln(X'/N))
+//   IP : U' >= A' B' exp(-theta L) / N
+//   HAM: U' >= sqrt(A' B') exp(-theta L / 2)            (theta = -Ham)
+// Column values: JS f0 = log2 B'; COS f0 = s_b; IP f0 = B'; HAM f0 = sqrt(B').
+// Row value (row_const): JS log2 A'; COS s_a; IP A'/N; HAM sqrt(A').
+template <int M>
+__device__ __forceinline__ float row_const(float A, uint32_t N) {
+    if (M == M_JS) return log2f(A);
+    if (M == M_COS) return sqrtf(fmaxf(-logf(A / (float)N), 0.0f));
+    if (M == M_IP) return A / (float)N;
+    return sqrtf(A);
+}
+
+template <int M>
+__device__ __forceinline__ RowFilter make_filter(float theta, float rc, float invL, float log2N) {
+    RowFilter f;
+    f.all = false;
+    const float ln2 = 0.69314718056f;
+    if (M == M_JS) {
+        if (!(theta > -0.5f)) { f.all = true; f.c0 = f.c1 = 0.f; return f; }
+        const float e = 1.0f / (1.0f + theta);
+        f.c0 = e;
+        f.c1 = (rc + (theta - 1.0f) * log2N) * e;
+    } else if (M == M_COS) {
+        f.c0 = theta * rc / ln2;
+        f.c1 = log2N - rc * rc / ln2;
+    } else if (M == M_IP) {
+        // L < 0, invL = 1/L
+        f.c0 = rc * expf(-theta / invL);
+        f.c1 = 0.f;
+    } else {
+        f.c0 = rc * expf(-0.5f * theta / invL);
+        f.c1 = 0.f;
+    }
+    if (!isfinite(f.c0) || !isfinite(f.c1)) f.all = true;
+    return f;
+}
+
+// 2^x on the special-function unit (relative error ~2^-22, far inside the
+// 2^-13 slack of the bound)
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <int M>
+__device__ __forceinline__ bool admit(const RowFilter &f, float U, float f0) {
+    if (f.all) return true;
+    float bound;
+    if (M == M_JS) bound = ex2_approx(fmaf(f.c0, f0, f.c1));
+    else if (M == M_COS) bound = ex2_approx(fmaf(f0, f.c0 - f0 * 1.44269504089f, f.c1));
+    else bound = f.c0 * f0;
+    return U >= bound * FILTER_SLACK;
+}
+
+// Running state of one query row in the epilogue.
+struct RowState {
+    float thr_k;       // key and index of the heap root once the heap is full,
+    uint32_t thr_i;    // else (-inf, none)
+    int size;          // entries in the heap
+};
+
+// A pair that passed the bound: exact FP32 key, then the heap.
+// (eff_k, eff_i) is the better of this heap's root (when full) and the other
+// group's; a pair not ranking above it cannot reach the final list.
+template <int M>
+__device__ __forceinline__ RowState consider(RowState st, float *hkey, uint32_t *hix, int t, uint32_t col,
+                                             uint32_t c, uint32_t b, uint32_t a, float lnA, float eff_k,
+                                             uint32_t eff_i, uint32_t N, float invL, int cap) {
+    const float lnB = M == M_COS ? row_log(b, N) : 0.0f;
+    const float key = rank_key<M>(a, b, c, N, lnA, lnB, invL);
+    if (!better(key, col, eff_k, eff_i)) return st;
+    Heap h;
+    h.key = hkey; h.ix = hix; h.t = t; h.size = st.size; h.cap = cap;
+    if (h.size < h.cap) {
+        h.push(key, col);
+        st.size = h.size;
+        if (h.size == h.cap) { st.thr_k = h.k_at(0); st.thr_i = h.i_at(0); }
+    } else {
+        h.replace_root(key, col);
+        st.thr_k = h.k_at(0); st.thr_i = h.i_at(0);
+    }
+    return st;
+}
+
+// Shared-heap variant: both epilogue groups insert into one heap per row,
+// serialised by a per-row lock (the two threads of a row sit in different
+// warps; within a warp every lane has its own row).  The root key is
+// published for the filters outside the lock: it only ever improves, so a
+// stale value admits more pairs, never fewer, and the exact test against the
+// root is repeated under the lock.  Returns the root key once the heap is
+// full, else -inf.
+template <int M>
+__device__ __noinline__ float consider_shared(float *hkey, uint32_t *hix, float *root_key, int *hsize,
+                                              unsigned int *lock, int t, uint32_t col, uint32_t c,
+                                              uint32_t b, uint32_t a, float lnA, float eff_k,
+                                              uint32_t N, float invL, int cap, unsigned int *err) {
+    const float lnB = M == M_COS ? row_log(b, N) : 0.0f;
+    const float key = rank_key<M>(a, b, c, N, lnA, lnB, invL);
+    if (!(key >= eff_k)) return eff_k;            // below the row's known root: cannot enter
+    uint32_t spins = 0;
+    while (atomicCAS(&lock[t], 0u, 1u) != 0u) {
+        if (++spins > (1u << 22)) {               // never expected: report, drop the pair
+            raise_error(err, BS_ERR_TIMEOUT);
+            return eff_k;
+        }
+    }
+    __threadfence_block();
+    Heap h;
+    h.key = hkey; h.ix = hix; h.t = t; h.size = hsize[t]; h.cap = cap;
+    float root = -INFINITY;
+    if (h.size < cap) {
+        h.push(key, col);
+        hsize[t] = h.size;
+        if (h.size == cap) root = h.k_at(0);
+    } else {
+        if (better(key, col, h.k_at(0), h.i_at(0))) h.replace_root(key, col);
+        root = h.k_at(0);
+    }
+    if (root != -INFINITY) *reinterpret_cast<volatile float *>(&root_key[t]) = root;
+    __threadfence_block();
+    atomicExch(&lock[t], 0u);
+    return root;
+}
+
+// v[j] for a per-lane index j, by a select tree over registers (no local memory)
+__device__ __forceinline__ uint32_t select32(const uint32_t (&v)[32], uint32_t j) {
+    uint32_t t16[16], t8[8], t4[4], t2[2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) t16[i] = (j & 16) ? v[i + 16] : v[i];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t8[i] = (j & 8) ? t16[i + 8] : t16[i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t4[i] = (j & 4) ? t8[i + 4] : t8[i];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) t2[i] = (j & 2) ? t4[i + 2] : t4[i];
+    return (j & 1) ? t2[1] : t2[0];
+}
+
+// Position in the job table: job j, row block rb, database tile `tile`.
+struct Cursor {
+    uint32_t j, rb, tile;
+    __device__ void start(const Job *jobs, uint32_t njobs, uint64_t u) {
+        j = 0;
+        while (j + 1 < njobs && jobs[j + 1].unit_base <= u) ++j;
+        const uint64_t l = u - jobs[j].unit_base;
+        rb = (uint32_t)(l / jobs[j].tiles);
+        tile = (uint32_t)(l % jobs[j].tiles);
+    }
+    __device__ void step(const Job *jobs) {
+        if (++tile == jobs[j].tiles) {
+            tile = 0;
+            if (++rb == jobs[j].rbs) { rb = 0; ++j; }
+        }
+    }
+};
+
+// The block holding unit x: the last block whose range starts at or before x.
+template <int NJ>
+__device__ __forceinline__ uint32_t block_of(const Args<NJ> &p, uint64_t x, uint32_t nblocks) {
+    uint32_t lo = 0, hi = nblocks - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (p.block_start[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int MODE, int M, int NOP, int NG, int SK, bool SHARED, int NJ>
+__global__ void __launch_bounds__(threads_for(NG), 1)
+    pair_tc_kernel(const __grid_constant__ Args<NJ> p) {
+    using Smem = tc::Smem<NOP, NG, SK>;
+    using G = Geo<SK>;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *op = base + Smem::op;
+    float *colv = reinterpret_cast<float *>(base + Smem::col);      // [2][3][BNP]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + Smem::bars);
+    uint64_t *op_full = bars, *op_empty = bars + NOP;
+    uint64_t *acc_full = bars + 2 * NOP, *acc_empty = acc_full + 2;
+    uint64_t *drain_bar = acc_empty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain_bar + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    float *thr_key = reinterpret_cast<float *>(base + Smem::thr);     // [NG][BM]
+    uint32_t *thr_idx = reinterpret_cast<uint32_t *>(thr_key + NG * BM);
+    int *heap_size = reinterpret_cast<int *>(thr_idx + NG * BM);
+    unsigned int *row_lock = reinterpret_cast<unsigned int *>(base + Smem::lock);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // The job table: one job is read from parameter memory at constant
+    // offsets; a batch's table is copied to shared memory once (reads of
+    // parameter memory at a run-time index are slow).
+    const Job *jobs = p.job;
+    if (NJ > 1) {
+        Job *sj = reinterpret_cast<Job *>(base + Smem::heap + (size_t)(SHARED ? 1 : NG) * p.k * BM * 8);
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(p.job);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(sj);
+        for (uint32_t i = tid; i < p.njobs * (uint32_t)(sizeof(Job) / 4); i += blockDim.x) dst[i] = src[i];
+        jobs = sj;
+    }
+    const uint32_t njobs = NJ > 1 ? p.njobs : 1u;
+    const uint64_t u_lo = p.block_start[blockIdx.x];
+    const uint32_t n_my_tiles = (uint32_t)(p.block_start[blockIdx.x + 1] - u_lo);
+
+    if (tid == 0) {
+        for (int i = 0; i < NOP; ++i) {
+            mbar_init(&op_full[i], 4);
+            mbar_init(&op_empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], 4 * NG);
+        }
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(tmem_slot, TMEM_COLS);
+        tmem_relinquish();
+    }
+    for (int i = tid; i < NG * BM; i += blockDim.x) {   // published thresholds start empty
+        thr_key[i] = -INFINITY;
+        thr_idx[i] = NO_IDX;
+        heap_size[i] = 0;
+    }
+    for (int i = tid; i < BM; i += blockDim.x) row_lock[i] = 0u;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    // unit block scales (all 128 lanes of columns SF_COL ..) before any MMA
+    if (warp >= 5 && warp < 9) tmem_fill32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + SF_COL, UNIT_SCALES);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    auto wait = [&](uint64_t *bar, uint32_t parity) {
+        if (*abort_flag) return;
+        if (!mbar_wait(bar, parity, p.wait_limit)) {
+            raise_error(p.err, BS_ERR_TIMEOUT);
+            *abort_flag = 1;
+        }
+    };
+
+    if (warp == 0) {
+        // ----------------------------- MMA issuer -----------------------------
+        if (lane == 0) {
+            uint32_t sl = 0;   // operand slots consumed
+            Cursor cur;
+            cur.start(jobs, njobs, u_lo);
+            const uint32_t sfa = tmem + SF_COL, sfb = tmem + SF_COL + 16;
+            for (uint32_t t = 0; t < n_my_tiles; ++t) {
+                const uint32_t nsl = slots_per_tile<SK>(jobs[cur.j].nKc);
+                const uint32_t ab = t & 1;
+                if (t >= 2) wait(&acc_empty[ab], ((t >> 1) - 1) & 1);
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + ab * BN;
+                for (uint32_t c = 0; c < nsl; ++c, ++sl) {
+                    const uint32_t o = sl % NOP;
+                    wait(&op_full[o], (sl / NOP) & 1);
+                    tc_fence_after();
+                    if (!*abort_flag) {
+                        const uint32_t a_addr = smem_u32(op + o * G::BYTES);
+                        const uint32_t b_addr = a_addr + G::A;
+#pragma unroll
+                        for (int kk = 0; kk < G::MMAS; ++kk)
+                            mma_fp4(d_tmem, sw_desc<SK>(a_addr + kk * 32), sw_desc<SK>(b_addr + kk * 32),
+                                    IDESC, sfa, sfb, (c | (uint32_t)kk) != 0);
+                    }
+                    mma_commit(&op_empty[o]);
+                }
+                // fault injection (tests only): the first accumulator is never
+                // announced, as if this role had died
+                if (!(p.inject == INJECT_STALL && t == 0)) mma_commit(&acc_full[ab]);
+                cur.step(jobs);
+            }
+            // every MMA issued here completes before the TMEM is freed
+            mma_commit(drain_bar);
+            if (!mbar_wait(drain_bar, 0, p.wait_limit)) raise_error(p.err, BS_ERR_TIMEOUT);
+        }
+    } else if (warp < 5) {
+        // ------------------------------ widening ------------------------------
+        // thread e owns query row e and database rows e and e + 128 of a tile
+        const int e = tid - 32;   // 0..127
+        const bool two_b = e + 128 < BN;
+        const uint4 z = make_uint4(0, 0, 0, 0);
+        // k-chunks of this block's sweep (each tile padded to whole slots)
+        uint32_t total = 0;
+        if (NJ == 1) {
+            total = n_my_tiles * kchunks_padded<SK>(jobs[0].nKc);
+        } else {
+            Cursor w;
+            w.start(jobs, njobs, u_lo);
+            for (uint32_t t = 0; t < n_my_tiles; ++t) {
+                total += kchunks_padded<SK>(jobs[w.j].nKc);
+                w.step(jobs);
+            }
+        }
+        // fetch cursor (job, row block, tile, k-chunk) of the next k-chunk;
+        // fetch() is called for g = 0, 1, 2, ... in order, so it only steps
+        Cursor fc;
+        fc.start(jobs, njobs, u_lo);
+        uint32_t f_kc = 0;
+        auto fetch = [&](uint32_t g, uint4 &a_, uint4 &b0_, uint4 &b1_) {
+            if (g >= total) return;
+            const Job &J = jobs[fc.j];
+            const uint32_t kc = f_kc, rb = fc.rb, tile = fc.tile, nKc = J.nKc;
+            if (++f_kc == kchunks_padded<SK>(nKc)) {
+                f_kc = 0;
+                fc.step(jobs);
+            }
+            a_ = b0_ = b1_ = z;
+            if (kc < nKc) {
+                const uint32_t R0 = tile * BN + e, R1 = R0 + 128;
+                if (J.rowmajor) {   // rows past the matrix end read as zero
+                    const uint32_t qr = rb * BM + e;
+                    if (qr < J.nQ) a_ = __ldg(J.Q + (size_t)qr * nKc + kc);
+                    if (R0 < J.nDB) b0_ = __ldg(J.DB + (size_t)R0 * nKc + kc);
+                    if (two_b && R1 < J.nDB) b1_ = __ldg(J.DB + (size_t)R1 * nKc + kc);
+                } else {            // the tiled copies hold whole 128-row blocks
+                    const uint32_t nblk = (J.nDB + 127) / 128;
+                    a_ = __ldg(J.Q + ((size_t)rb * nKc + kc) * 128 + e);
+                    if ((R0 >> 7) < nblk) b0_ = __ldg(J.DB + ((size_t)(R0 >> 7) * nKc + kc) * 128 + (R0 & 127));
+                    if (two_b && (R1 >> 7) < nblk)
+                        b1_ = __ldg(J.DB + ((size_t)(R1 >> 7) * nKc + kc) * 128 + (R1 & 127));
+                }
+            }
+        };
+        auto publish = [&](uint32_t o) {
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&op_full[o]);
+        };
+        // four k-chunks in flight; a fixed rotation keeps them in registers
+        uint4 ra[4], rb0[4], rb1[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) fetch(u, ra[u], rb0[u], rb1[u]);
+        for (uint32_t g0 = 0; g0 < total; g0 += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t g = g0 + u;
+                if (g >= total) break;
+                if (SK == 128) {
+                    if (u & 1) {   // k-chunks g - 1 and g fill one slot
+                        const uint32_t sl = g >> 1;
+                        const uint32_t o = sl % NOP;
+                        if (sl >= NOP) wait(&op_empty[o], ((sl / NOP) - 1) & 1);
+                        uint8_t *oA = op + o * G::BYTES;
+                        uint8_t *oB = oA + G::A;
+                        {
+                            const uint32_t x[8] = {ra[u - 1].x, ra[u - 1].y, ra[u - 1].z, ra[u - 1].w,
+                                                   ra[u].x,     ra[u].y,     ra[u].z,     ra[u].w};
+                            widen_store<SK>(oA, e, x);
+                        }
+                        {
+                            const uint32_t x[8] = {rb0[u - 1].x, rb0[u - 1].y, rb0[u - 1].z, rb0[u - 1].w,
+                                                   rb0[u].x,     rb0[u].y,     rb0[u].z,     rb0[u].w};
+                            widen_store<SK>(oB, e, x);
+                        }
+                        if (two_b) {
+                            const uint32_t x[8] = {rb1[u - 1].x, rb1[u - 1].y, rb1[u - 1].z, rb1[u - 1].w,
+                                                   rb1[u].x,     rb1[u].y,     rb1[u].z,     rb1[u].w};
+                            widen_store<SK>(oB, e + 128, x);
+                        }
+                        publish(o);
+                        fetch(g + 3, ra[u - 1], rb0[u - 1], rb1[u - 1]);
+                        fetch(g + 4, ra[u], rb0[u], rb1[u]);
+                    }
+                } else {
+                    constexpr int SPK = KCW / G::WPS;   // slots per k-chunk: 1 or 2
+#pragma unroll
+                    for (int h = 0; h < SPK; ++h) {
+                        const uint32_t sl = g * SPK + h;
+                        const uint32_t o = sl % NOP;
+                        if (sl >= NOP) wait(&op_empty[o], ((sl / NOP) - 1) & 1);
+                        uint8_t *oA = op + o * G::BYTES;
+                        uint8_t *oB = oA + G::A;
+                        const uint32_t xa[4] = {ra[u].x, ra[u].y, ra[u].z, ra[u].w};
+                        const uint32_t xb0[4] = {rb0[u].x, rb0[u].y, rb0[u].z, rb0[u].w};
+                        const uint32_t xb1[4] = {rb1[u].x, rb1[u].y, rb1[u].z, rb1[u].w};
+                        widen_store<SK>(oA, e, xa + h * G::WPS);
+                        widen_store<SK>(oB, e, xb0 + h * G::WPS);
+                        if (two_b) widen_store<SK>(oB, e + 128, xb1 + h * G::WPS);
+                        publish(o);
+                    }
+                    fetch(g + 4, ra[u], rb0[u], rb1[u]);
+                }
+            }
+        }
+    } else {
+        // ------------------------------ epilogue ------------------------------
+        const int grp = (warp - 5) >> 2;           // epilogue group
+        const int e = tid - 160 - 128 * grp;       // 0..127 within the group
+        const int quarter = warp & 3;              // TMEM lanes this warp may access
+        const int r = quarter * 32 + lane;         // row within the block
+        // tile columns of this group
+        const int c_lo = NG == 1 ? 0 : grp * 128;
+        const int c_hi = (NG == 1 || grp == 1) ? BN : 128;
+        // row constants of the current row block (set at each segment start)
+        uint32_t q = 0, a = 0;
+        bool row_ok = false;
+        float rc = 0.0f, lnA = 0.0f, Na = 0.0f;
+        float *hkey = reinterpret_cast<float *>(base + Smem::heap) + (size_t)(SHARED ? 0 : grp) * p.k * BM * 2;
+        uint32_t *hix = reinterpret_cast<uint32_t *>(hkey + (size_t)p.k * BM);
+        RowState st;
+        st.thr_k = -INFINITY; st.thr_i = NO_IDX; st.size = 0;
+        // this row's buffer of admitted pairs, (count << 8) | column in tile
+        uint32_t *cb = reinterpret_cast<uint32_t *>(base + Smem::cbuf) + (size_t)grp * CB * BM;
+        int nbuf = 0;
+        uint32_t d_col0 = 0;          // first column of the tile the buffer belongs to
+        const float *d_cv = colv;     // that tile's column values
+        float eff_k = -INFINITY;                   // threshold the filter was built from
+        uint32_t eff_i = NO_IDX;
+        RowFilter filt;
+        filt.all = true; filt.c0 = filt.c1 = 0.f;
+        Cursor cur;
+        cur.start(jobs, njobs, u_lo);
+        uint32_t N = jobs[cur.j].N;
+        float invL = jobs[cur.j].invL;
+        // insert every buffered pair of this row into its heap (warp-wide loop)
+        auto drain = [&]() {
+            while (__any_sync(0xffffffffu, nbuf > 0)) {
+                if (nbuf > 0) {
+                    --nbuf;
+                    const uint32_t ent = cb[nbuf * BM + r];
+                    const uint32_t j = ent & 255u;
+                    st = consider<M>(st, hkey, hix, r, d_col0 + j, ent >> 8, (uint32_t)d_cv[j], a, lnA,
+                                     eff_k, eff_i, N, invL, (int)p.k);
+                    if (st.thr_i != NO_IDX && better(st.thr_k, st.thr_i, eff_k, eff_i)) {
+                        eff_k = st.thr_k; eff_i = st.thr_i;
+                    }
+                }
+            }
+        };
+
+        for (uint32_t t = 0; t < n_my_tiles; ++t) {
+            if (t > 0) cur.step(jobs);
+            const Job &J = jobs[cur.j];
+            const uint32_t tile = cur.tile;
+            if (t == 0 || tile == 0) {
+                // a new row block: its row constants, empty heaps, empty
+                // published thresholds (the other group reads them after the
+                // barrier below)
+                N = J.N;
+                invL = J.invL;
+                q = cur.rb * BM + r;
+                row_ok = q < J.nQ;
+                a = row_ok ? __ldg(J.pcQ + q) : 0u;
+                const uint32_t a_cl = a < N - 1 ? a : N - 1;
+                if (MODE == MODE_TOPK) rc = row_const<M>((float)(N - a_cl), N);   // from A' >= 1
+                lnA = row_log(a, N);
+                Na = (float)(N - a);                         // N - a (raw)
+                st.thr_k = -INFINITY; st.thr_i = NO_IDX; st.size = 0;
+                eff_k = -INFINITY; eff_i = NO_IDX;
+                filt.all = true; filt.c0 = filt.c1 = 0.f;
+                if (MODE == MODE_TOPK && (!SHARED || grp == 0)) {
+                    thr_key[(SHARED ? 0 : grp) * BM + r] = -INFINITY;
+                    thr_idx[(SHARED ? 0 : grp) * BM + r] = NO_IDX;
+                    heap_size[(SHARED ? 0 : grp) * BM + r] = 0;
+                }
+                if (MODE == MODE_TOPK && NG == 2) named_sync(5, 128 * NG);
+            }
+            float *cv = colv + (t & 1) * 3 * BNP;
+            // per-column values of this group's columns (128 threads, 112-240 columns)
+            for (int j = c_lo + e; j < c_hi; j += 128) {
+                const uint32_t col = tile * BN + j;
+                const uint32_t b = col < J.nDB ? __ldg(J.pcDB + col) : 0u;
+                const uint32_t b_cl = b < N - 1 ? b : N - 1;
+                const float Bf = (float)(N - b_cl);
+                float f0;
+                if (MODE == MODE_STORE) f0 = row_log(b, N);
+                else if (M == M_JS) f0 = log2f(Bf);
+                else if (M == M_COS) f0 = sqrtf(fmaxf(-logf(Bf / (float)N), 0.0f));
+                else if (M == M_IP) f0 = Bf;
+                else f0 = sqrtf(Bf);
+                cv[j] = (float)b;         // raw count: U' is formed from the raw a, b, c
+                cv[BNP + j] = f0;
+            }
+            named_sync(2 + grp, 128);
+            const uint32_t ab = t & 1;
+            wait(&acc_full[ab], (t >> 1) & 1);
+            tc_fence_after();
+            const uint32_t col0 = tile * BN;
+            d_col0 = col0;
+            d_cv = cv;
+            // every lane stays in the loops below (they vote); dead rows admit nothing
+            const bool live = row_ok && !*abort_flag;
+            const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + ab * BN;
+#pragma unroll 1
+            for (int ch = c_lo / 32; ch * 32 < c_hi; ++ch) {
+                const int width = c_hi - ch * 32 < 32 ? c_hi - ch * 32 : 32;   // 32, or 16 at the end
+                uint32_t v[32];
+                if (width == 32) tmem_ld32_async(trow + ch * 32, v);
+                else tmem_ld16_async(trow + ch * 32, v);
+                const uint32_t col_c = col0 + ch * 32;
+                if (MODE == MODE_STORE) {
+                    tmem_wait();
+                    if (live) {
+                        const size_t plane = (size_t)J.nQ * J.nDB;
+                        const size_t o0 = (size_t)q * J.nDB + col_c;
+#pragma unroll 4
+                        for (int jj = 0; jj < 32; ++jj) {
+                            if (jj >= width || col_c + jj >= J.nDB) break;
+                            const int j = ch * 32 + jj;
+                            const uint32_t c = (uint32_t)__uint_as_float(v[jj]);
+                            const uint32_t b = (uint32_t)cv[j];
+                            const float lnB = cv[BNP + j];
+                            const size_t o = o0 + jj;
+                            if (J.counts) J.counts[o] = c;
+                            float *out = J.out + o;
+                            if (p.measures & BS_IP) { *out = estimate_one<M_IP>(a, b, c, N, lnA, lnB, invL); out += plane; }
+                            if (p.measures & BS_HAM) { *out = estimate_one<M_HAM>(a, b, c, N, lnA, lnB, invL); out += plane; }
+                            if (p.measures & BS_JS) { *out = estimate_one<M_JS>(a, b, c, N, lnA, lnB, invL); out += plane; }
+                            if (p.measures & BS_COS) *out = estimate_one<M_COS>(a, b, c, N, lnA, lnB, invL);
+                        }
+                    }
+                    continue;
+                }
+                // the threshold to beat: this heap's root or the other group's
+                // (shared heap: the published root key, ties admitted)
+                float tk = st.thr_k;
+                uint32_t ti = st.thr_i;
+                if (SHARED) {
+                    tk = *reinterpret_cast<volatile float *>(&thr_key[r]);
+                    ti = tk == -INFINITY ? NO_IDX : 0xFFFFFFFEu;
+                } else if (NG == 2) {
+                    const float ok = thr_key[(1 - grp) * BM + r];
+                    const uint32_t oi = thr_idx[(1 - grp) * BM + r];
+                    if (better(ok, oi, tk, ti)) { tk = ok; ti = oi; }
+                }
+                if (tk != eff_k || ti != eff_i) {
+                    eff_k = tk; eff_i = ti;
+                    if (ti == NO_IDX) { filt.all = true; }
+                    else filt = make_filter<M>(tk, rc, invL, J.log2N);
+                }
+                tmem_wait();
+                // pass 1: which of these 32 pairs can beat the threshold
+                uint32_t mask = 0;
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) {
+                    const int j = ch * 32 + jj;
+                    const float cf = __uint_as_float(v[jj]);   // exact count
+                    // U' = N - min(a + b - c, N - 1) = max(N - a - b + c, 1), exact in FP32
+                    const float U = fmaxf(Na - cv[j] + cf, 1.0f);
+                    if (admit<M>(filt, U, cv[BNP + j])) mask |= 1u << jj;
+                }
+                if (width < 32) mask &= 0xFFFFu;
+                // columns past the database end and the self pair never rank
+                if (col_c + 32 > J.nDB)
+                    mask &= col_c >= J.nDB ? 0u : (0xFFFFFFFFu >> (32 - (J.nDB - col_c)));
+                if (J.exclude_self) {
+                    const long long qs = (long long)q - (long long)J.self_off - (long long)col_c;
+                    if (qs >= 0 && qs < 32) mask &= ~(1u << (uint32_t)qs);
+                }
+                if (!live) mask = 0;
+                // pass 2: exact keys for the admitted pairs.  Per-group heaps: the
+                // pairs are buffered per row and inserted once per tile (the
+                // warp loops as often as its busiest row needs); a chunk that
+                // does not fit some row's buffer empties the buffers and is
+                // inserted directly.
+                const int size_before = st.size;
+                const uint32_t root_before = st.thr_i;
+                const float rootk_before = st.thr_k;
+                auto insert_direct = [&](uint32_t m) {
+                    while (__any_sync(0xffffffffu, m != 0)) {
+                        if (m) {
+                            const uint32_t jj = __ffs(m) - 1;
+                            m &= m - 1;
+                            const uint32_t c = (uint32_t)__uint_as_float(select32(v, jj));
+                            const int j = ch * 32 + (int)jj;
+                            if (SHARED) {
+                                const float root = consider_shared<M>(hkey, hix, thr_key, heap_size, row_lock,
+                                                                      r, col_c + jj, c, (uint32_t)cv[j], a, lnA,
+                                                                      eff_k, N, invL, (int)p.k, p.err);
+                                if (root > eff_k) { eff_k = root; eff_i = 0xFFFFFFFEu; }
+                            } else {
+                                st = consider<M>(st, hkey, hix, r, col_c + jj, c, (uint32_t)cv[j], a, lnA,
+                                                 eff_k, eff_i, N, invL, (int)p.k);
+                                if (st.thr_i != NO_IDX && better(st.thr_k, st.thr_i, eff_k, eff_i)) {
+                                    eff_k = st.thr_k; eff_i = st.thr_i;
+                                }
+                            }
+                        }
+                    }
+                };
+                if (SHARED) {
+                    insert_direct(mask);
+                } else if (__any_sync(0xffffffffu, __popc(mask) > CB - nbuf)) {
+                    drain();
+                    insert_direct(mask);
+                } else {
+                    while (__any_sync(0xffffffffu, mask != 0)) {
+                        if (mask) {
+                            const uint32_t jj = __ffs(mask) - 1;
+                            mask &= mask - 1;
+                            const uint32_t c = (uint32_t)__uint_as_float(select32(v, jj));
+                            cb[nbuf * BM + r] = (c << 8) | (uint32_t)(ch * 32 + (int)jj);
+                            ++nbuf;
+                        }
+                    }
+                }
+                // publish a changed root to the other group
+                if (!SHARED && NG == 2 && (st.size != size_before || st.thr_i != root_before ||
+                                           st.thr_k != rootk_before)) {
+                    thr_key[grp * BM + r] = st.thr_k;
+                    thr_idx[grp * BM + r] = st.thr_i;
+                }
+                if (eff_i != NO_IDX) filt = make_filter<M>(eff_k, rc, invL, J.log2N);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[ab]);
+            if (MODE == MODE_STORE) continue;
+            if (!SHARED) {   // this tile's buffered pairs (TMEM no longer needed)
+                const int sz0 = st.size;
+                const uint32_t ri0 = st.thr_i;
+                const float rk0 = st.thr_k;
+                drain();
+                if (NG == 2 && (st.size != sz0 || st.thr_i != ri0 || st.thr_k != rk0)) {
+                    thr_key[grp * BM + r] = st.thr_k;
+                    thr_idx[grp * BM + r] = st.thr_i;
+                }
+                if (eff_i != NO_IDX) filt = make_filter<M>(eff_k, rc, invL, J.log2N);
+            }
+            if (t + 1 < n_my_tiles && tile + 1 < J.tiles) continue;
+            // ---- end of this row block's segment: its list for part `part`
+            const uint64_t x0 = J.unit_base + (uint64_t)cur.rb * J.tiles;   // first unit of this row block
+            const uint32_t part = blockIdx.x - block_of(p, x0, gridDim.x);
+            // sort each heap best first; with two groups the first merges both lists
+            // (shared heap: one list, sorted by the first group once both are done)
+            if (SHARED && NG == 2) named_sync(4, 128 * NG);
+            if (SHARED) st.size = heap_size[r];
+            Heap h;
+            h.key = hkey; h.ix = hix; h.t = r; h.size = st.size; h.cap = (int)p.k;
+            if (row_ok && (!SHARED || grp == 0)) h.sort_best_first();
+            if (!SHARED && NG == 2) {
+                heap_size[grp * BM + r] = st.size;
+                named_sync(4, 128 * NG);
+            }
+            if (grp == 0 && row_ok) {
+                const float *k1 = reinterpret_cast<float *>(base + Smem::heap) + (size_t)p.k * BM * 2;
+                const uint32_t *i1 = reinterpret_cast<const uint32_t *>(k1 + (size_t)p.k * BM);
+                const int n0 = st.size, n1 = (!SHARED && NG == 2) ? heap_size[BM + r] : 0;
+                int x = 0, y = 0;
+                for (int s = 0; s < (int)p.k; ++s) {
+                    float kk = -INFINITY;
+                    uint32_t ii = NO_IDX;
+                    const bool hx = x < n0, hy = y < n1;
+                    if (hx || hy) {
+                        const float xk = hx ? h.k_at(x) : -INFINITY;
+                        const uint32_t xi = hx ? h.i_at(x) : NO_IDX;
+                        const float yk = hy ? k1[y * BM + r] : -INFINITY;
+                        const uint32_t yi = hy ? i1[y * BM + r] : NO_IDX;
+                        if (hx && (!hy || better(xk, xi, yk, yi))) { kk = xk; ii = xi; ++x; }
+                        else { kk = yk; ii = yi; ++y; }
+                    }
+                    if (p.splits == 1) {
+                        const size_t o = (size_t)q * p.k + s;
+                        J.score[o] = M == M_HAM ? -kk : kk;
+                        J.idx[o] = ii;
+                    } else {
+                        const size_t o = ((size_t)part * J.nQ + q) * p.k + s;
+                        J.ws_key[o] = kk;
+                        J.ws_idx[o] = ii;
+                    }
+                }
+                // the block holding a row block's last tile also writes empty
+                // lists for the part slots this row block does not use
+                if (p.splits > 1 && tile + 1 == J.tiles) {
+                    for (uint32_t pp = part + 1; pp < p.splits; ++pp)
+                        for (int s = 0; s < (int)p.k; ++s) {
+                            const size_t o = ((size_t)pp * J.nQ + q) * p.k + s;
+                            J.ws_key[o] = -INFINITY;
+                            J.ws_idx[o] = NO_IDX;
+                        }
+                }
+            }
+            // every heap read of this segment is done before the next one resets them
+            if (NG == 2) named_sync(6, 128 * NG);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block configurations (operand slots, epilogue groups, slot K bytes, one heap
+// per row shared by the groups); the index is the c of BS_VARIANT_TC_CFG(c).
+// ---------------------------------------------------------------------------
+#define BS_TC_CONFIGS(X)         \
+    X(0, 3, 2, 128, false)       \
+    X(1, 2, 2, 128, false)       \
+    X(2, 3, 1, 128, false)       \
+    X(3, 2, 1, 128, false)       \
+    X(4, 4, 2, 64, false)        \
+    X(5, 8, 2, 32, false)        \
+    X(6, 6, 1, 64, false)        \
+    X(7, 4, 1, 64, false)        \
+    X(8, 3, 2, 128, true)        \
+    X(9, 2, 2, 128, true)
+constexpr int kTcConfigs = 10;
+constexpr size_t kSmemLimit = 232448;   // 227 KB per block
+
+template <int NOP, int NG, int SK, bool SH>
+__host__ __device__ constexpr size_t smem_bytes(uint32_t k) {
+    return 1024 + Smem<NOP, NG, SK>::heap + (size_t)(SH ? 1 : NG) * k * BM * 8;
+}
+
+// Launch of one configuration for one measure (defined in the per-measure
+// translation units); cudaErrorInvalidConfiguration when it does not fit k.
+template <int M, int NJ>
+cudaError_t launch_topk(int cfg, const Args<NJ> &p, uint32_t grid, cudaStream_t stream);
+// Store of the full count / estimate matrices (bs_tc_store.cu).
+cudaError_t launch_store(const Args<1> &p, uint32_t grid, cudaStream_t stream);
+
+}  // namespace tc
+}  // namespace bs

@@ -9,10 +9,14 @@
 // memory when it splits the database across blocks; this entry point keeps
 // that scratch in a fixed array in the library's own device memory instead.
 //
-// The array is BS_TOPK_NOALLOC_SCRATCH_BYTES large and exists on every GPU
-// that loads the library, until the process exits.  Its device address is
-// looked up once per device, on the first call made while that device is
-// current, so make that first call before any stream capture.  All calls
+// The array is BS_TOPK_NOALLOC_SCRATCH_BYTES large.  CUDA loads a library's
+// device code lazily, one module per translation unit, so the array is
+// reserved on a device when this file's module is first loaded there -- at
+// the first bs_topk_noalloc call made while that device is current, which
+// also looks up the array's address.  Make that first call before the
+// caller's own arena takes the whole device and before any stream capture;
+// it may synchronise.  The reservation then lasts until the process exits.
+// All calls
 // share the one array: two calls whose kernels overlap on the GPU (for
 // example on two streams) race on it and must be serialised by the caller.
 // Nothing in it needs to start at zero: every slot a call reads was written
@@ -34,7 +38,10 @@ static void *topk_scratch_address() {
     std::lock_guard<std::mutex> g(mu);
     if (!addr[dev]) {
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_topk_scratch) != cudaSuccess) return nullptr;
+        if (cudaGetSymbolAddress(&p, g_topk_scratch) != cudaSuccess) {
+            cudaGetLastError();   // leave no error behind for the next call's launch check
+            return nullptr;
+        }
         addr[dev] = p;
     }
     return addr[dev];

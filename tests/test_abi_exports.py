@@ -55,15 +55,17 @@ def test_env_variant_override_in_plan():
 
 def test_tensor_core_plan_parts_match_the_persistent_schedule():
     # bs_topk_plan is host-only; without a GPU the library assumes 148 SMs.
-    # Parts = the most blocks any 128-row query block is spread over when
-    # 256-row database tiles are dealt out as equal contiguous ranges.
+    # Parts = the most blocks any 128-row query block is spread over when the
+    # U = row blocks x 240-row database tiles are dealt out as equal contiguous
+    # ranges, block c starting at unit ceil(c U / G): unit x then sits in block
+    # floor(x G / U).
     from paper_1910_04658_gb300 import binding as B
 
     def parts(nq, ndb, G=148):
-        rbs, T = (nq + 127) // 128, (ndb + 255) // 256
+        rbs, T = (nq + 127) // 128, (ndb + 239) // 240
         U = rbs * T
         G = min(G, U)
-        first = lambda x: ((x + 1) * G - 1) // U
+        first = lambda x: (x * G) // U
         return max(first(rb * T + T - 1) - first(rb * T) + 1 for rb in range(rbs))
 
     for nq, ndb in ((100_000, 100_000), (4096, 1_000_000), (1000, 1000), (37, 20_000), (129, 257)):

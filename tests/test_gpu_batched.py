@@ -67,3 +67,41 @@ def test_batched_results_match_oracle(datasets):
         s, i = s.cpu().numpy(), u32(i)
         for t, r in enumerate(rows):
             check_topk_row(s[r], i[r], oest[3, t], 20, 3, exclude_q=int(r))
+
+
+def test_persistent_batch_equals_per_dataset_calls(datasets):
+    # one persistent ranking launch over every tensor-core dataset (the N = 96
+    # dataset goes through its own CUDA-core call) gives, list for list and
+    # bit for bit, what one bs_topk_ex per dataset gives
+    per = BatchedJob(datasets, k=20, by="cos", mode="per_dataset")
+    per.run_eager()
+    job = BatchedJob(datasets, k=20, by="cos")
+    job.run_eager()
+    torch.cuda.synchronize()
+    assert B.bs_get_async_error() == 0
+    assert job.side == [j for j, d in enumerate(datasets) if d.N == 96]
+    for j in range(len(datasets)):
+        s0, i0 = per.results(j)
+        s1, i1 = job.results(j)
+        assert torch.equal(i0, i1) and torch.equal(s0, s1), j
+    # launches: the batched sketch, the re-layout, the ranking, (a merge), and
+    # the side dataset's own calls -- far fewer than one top-k per dataset
+    assert job.launches() < per.launches()
+    splits, n_launch = B.bs_topk_batched_plan(job.tjobs, 20)
+    assert n_launch == 2 + (splits > 1)
+
+
+def test_batched_topk_rejects_bad_tables(datasets):
+    job = BatchedJob(datasets, k=20, by="cos")
+    ws = torch.empty((job.bwsb,), dtype=torch.uint8, device="cuda")
+    with pytest.raises(B.BinSketchError) as e:     # workspace too small
+        B.bs_topk_batched(job.tjobs, B.BS_COS, 20, ws[:64], 64, 0)
+    assert e.value.code == 5
+    d = datasets[job.side[0]]
+    j96 = job.side[0]
+    bad = B._job_table([dict(Q=job.sk[j96], pcQ=job.pc[j96], DB=job.sk[j96], pcDB=job.pc[j96],
+                             score=job.score[j96], idx=job.idx[j96], nQ=d.n, nDB=d.n, N=d.N,
+                             exclude_self=True, k=20)])
+    with pytest.raises(B.BinSketchError) as e:     # N = 96: not a tensor-core shape
+        B.bs_topk_batched(bad, B.BS_COS, 20, ws, job.bwsb, 0)
+    assert e.value.code == 7

@@ -64,3 +64,9 @@ def test_noalloc_topk_refuses_shapes_beyond_its_scratch():
     with pytest.raises(B.BinSketchError) as e:
         B.bs_topk_noalloc(q, qpc, nQ, db, dpc, nDB, N, B.BS_JS, k, 0, s, i)
     assert e.value.code == 5   # BS_ERR_NO_MEMORY
+    # a refusal leaves nothing behind: the next call on the stream succeeds
+    s2 = torch.empty((3, 5), dtype=torch.float32, device="cuda")
+    i2 = torch.empty((3, 5), dtype=torch.int32, device="cuda")
+    B.bs_topk_noalloc(q[:3], qpc[:3], 3, db[:1000], dpc[:1000], 1000, N, B.BS_JS, 5, 0, s2, i2)
+    torch.cuda.synchronize()
+    assert B.bs_get_async_error() == 0
