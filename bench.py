@@ -346,6 +346,22 @@ def run_ours(args, rank, world, dist):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
     }
+    if rank == 0 and world == 1 and not args.no_serving and n == WORKLOAD["n"]:
+        # third leg of the metric: query p50 / p99 at fixed MSE (N = 4096, closed
+        # form) against a resident 1,000,000-sketch database, Poisson arrivals at
+        # 0.8 x a saturation measured on the same request mix (outside the timed region)
+        del ws, flush
+        torch.cuda.empty_cache()
+        sat, mean_q, lat = serving_run(SERVING["db_rows"], args.serving_leg_requests, [0.8],
+                                       args.slots, args.max_batch)
+        st = lat[0.8]
+        line["components"].update({
+            "serving_p50_ms": st["p50_ms"], "serving_p99_ms": st["p99_ms"],
+            "serving_qps": st["queries_per_s"], "serving_saturation_qps": sat,
+            "serving_load": 0.8, "serving_requests": st["requests"],
+            "serving_mean_request_queries": mean_q, "serving_db_rows": SERVING["db_rows"],
+            "serving_N": SERVING["N"], "serving_k": SERVING["k"],
+            "serving_fixed_mse": "N = 4096 bits, closed-form JS estimator"})
     if rank == 0 and world == 1 and not args.no_cpu_baseline and n == WORKLOAD["n"]:
         v, pps, gbs, rows, secs, thr = oracle_sample(csr, N, k, args.cpu_budget)
         line["cpu_baseline"] = {
@@ -365,7 +381,11 @@ SERVING = dict(workload="serving: top-k against a resident sketch database", db_
                arrivals="Poisson")
 
 
-def run_serving(args):
+def serving_run(db_rows, n_requests, loads, slots, max_q, seed=7):
+    """Build the resident database of db_rows sketches, measure saturation
+    (every request queued at t = 0), then serve a Poisson stream at each load
+    (fraction of saturation).  Returns (saturation q/s, mean request size,
+    {load: latency stats})."""
     import torch
 
     from paper_1910_04658_gb300 import binding as B, build, inputs
@@ -377,14 +397,15 @@ def run_serving(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     N, k = SERVING["N"], SERVING["k"]
-    rp, col = inputs.bow_corpus_device(0, args.db_rows, SERVING["d"])
+    rp, col = inputs.bow_corpus_device(0, db_rows, SERVING["d"])
     db = SketchDB(rp, col, SERVING["d"], N, seed=0)
+    del rp, col
     torch.cuda.synchronize()
     assert B.bs_get_async_error() == 0
-    rng = np.random.default_rng(7)
-    zc = inputs.ZipfColumns(np.random.default_rng(8), SERVING["d"])
+    rng = np.random.default_rng(seed)
+    zc = inputs.ZipfColumns(np.random.default_rng(seed + 1), SERVING["d"])
     make = lambda r, q: inputs.query_batch(r, q, zc)
-    slots, max_q, arena = args.slots, args.max_batch, 6 << 30
+    arena = 6 << 30
 
     def serve(reqs):
         ex = GpuExecutor(db, k=k, by="js", slots=slots, arena_bytes=arena, max_queries=max_q)
@@ -396,21 +417,31 @@ def run_serving(args):
 
     # warm-up, then saturation: every request queued at t = 0
     serve(poisson_requests(rng, 12, 1e9, make))
-    sat_reqs = poisson_requests(rng, args.serving_requests, 1e9, make)
+    sat_reqs = poisson_requests(rng, n_requests, 1e9, make)
     for r in sat_reqs:
         r.arrival = 0.0
     res, wall, _ = serve(sat_reqs)
     sat_qps = sum(r.n_queries for r in sat_reqs) / wall
-    mean_q = np.mean([r.n_queries for r in sat_reqs])
+    mean_q = float(np.mean([r.n_queries for r in sat_reqs]))
     lines = {}
-    for load in args.loads:
-        reqs = poisson_requests(rng, args.serving_requests, load * sat_qps / mean_q, make)
+    for load in loads:
+        reqs = poisson_requests(rng, n_requests, load * sat_qps / mean_q, make)
         res, wall, sch = serve(reqs)
         st = latency_stats(res, wall)
         st["batches"] = sch.batches_launched
         st["max_inflight"] = sch.max_inflight
         lines[load] = st
     assert B.bs_get_async_error() == 0
+    del db
+    torch.cuda.empty_cache()
+    return sat_qps, mean_q, lines
+
+
+def run_serving(args):
+    from paper_1910_04658_gb300 import binding as B
+
+    slots, max_q = args.slots, args.max_batch
+    sat_qps, mean_q, lines = serving_run(args.db_rows, args.serving_requests, args.loads, slots, max_q)
     head = lines[0.8] if 0.8 in lines else lines[args.loads[-1]]
     line = {
         "metric": METRIC, "value": head["p99_ms"], "unit": "ms (query p99 at 0.8 x saturation)",
@@ -695,6 +726,9 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=300)
     ap.add_argument("--loads", type=float, nargs="+", default=[0.5, 0.8, 0.95])
     ap.add_argument("--slots", type=int, default=3, help="serving: concurrent micro-batches")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="default workload: skip the serving leg (p50/p99 on the 1M-sketch database)")
+    ap.add_argument("--serving-leg-requests", type=int, default=100)
     ap.add_argument("--max-batch", type=int, default=4096, help="serving: queries per micro-batch")
     args = ap.parse_args()
     if args.workload == "serving":

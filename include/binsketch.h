@@ -221,22 +221,22 @@ bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
  *   BS_VARIANT_TC    0/1 bits widened to 4-bit E2M1 elements (1.0 / 0) and
  *                    multiplied on the tensor cores (tcgen05.mma block-scaled
  *                    FP4 with unit scales, exact FP32 accumulation), for
- *                    N % 128 == 0, 256 <= N <= 8192, k up to the largest
- *                    configuration's heap (k <= 121) and 16-byte aligned Q and
- *                    DB; BS_ERR_UNSUPPORTED otherwise;
+ *                    N % 128 == 0, 256 <= N <= 8192 and 16-byte aligned Q
+ *                    and DB; BS_ERR_UNSUPPORTED otherwise;
  *   BS_VARIANT_AUTO  the tensor-core kernel where it applies, else POPC
  *                    (this is what bs_topk does).
  * For the tensor-core kernel, BS_VARIANT_TC_CFG(c) OR-ed into `variant` picks
- * its block configuration c (an autotuner's knob): epilogue groups, operand
- * slots, and K bytes per row in a slot (128: 256 sketch bits per slot;
- * 64 / 32: 128 / 64 bits, so more slots fit the same memory):
- *   c = 0: 2 groups, 3 slots x 128    c = 1: 2 groups, 2 slots x 128
- *   c = 2: 1 group,  3 slots x 128    c = 3: 1 group,  2 slots x 128
- *   c = 4: 2 groups, 4 slots x 64     c = 5: 2 groups, 8 slots x 32
- *   c = 6: 1 group,  6 slots x 64     c = 7: 1 group,  4 slots x 64
- *   c = 8: 2 groups, 3 slots x 128, one heap per row shared by the groups
- *   c = 9: 2 groups, 2 slots x 128, shared heap
- * (otherwise each group keeps its own heap for its half of the columns).
+ * its block configuration c (an autotuner's knob): operand slots (widened
+ * 256-bit pieces of K), epilogue groups, the depth of the ring the tensor-map
+ * copies fill, and whether the two groups share one heap per row:
+ *   c = 0: 3 slots, 2 groups, ring 4     c = 1: 2 slots, 2 groups, ring 4
+ *   c = 2: 3 slots, 2 groups, ring 4, shared heap
+ *   c = 3: 2 slots, 2 groups, ring 4, shared heap
+ *   c = 4: 2 slots, 1 group,  ring 4     c = 5: 2 slots, 2 groups, ring 6
+ *   c = 6: 2 slots, 2 groups, ring 6, shared heap
+ *   c = 7: 2 slots, 2 groups, ring 2     c = 8: 2 slots, 1 group,  ring 2
+ *   c = 9: 1 slot,  1 group,  ring 2 (the smallest: every k up to
+ *          BS_TOPK_K_MAX fits)
  * The default is the first that fits in the order 0, 1, ..., 9.
  * Environment: for calls that pass BS_VARIANT_AUTO (bs_topk among them) the
  * variable BS_VARIANT, read once, overrides the choice: "popc" forces the
@@ -366,12 +366,13 @@ bs_status bs_topk_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, uint32
                        int same_matrix, uint32_t *uses_tc, uint32_t *splits, uint32_t *launches);
 
 /*
- * bs_tiled_bytes / bs_tile_sketches -- keep a sketch database in the layout
- * the tensor-core kernel reads (row blocks of 128, 16-byte k-chunks of a
- * block contiguous), so repeated searches against it skip the re-layout.
+ * bs_tiled_bytes / bs_tile_sketches -- a copy of a sketch database in the
+ * layout the tensor-core kernel reads.  That kernel fetches 256-bit pieces of
+ * 128 query / 240 database rows straight from row-major sketches with tensor
+ * maps, so the layout is the row-major one and the copy is a plain copy;
+ * bs_topk_pretiled also accepts the original sketches themselves.
  *  sketch  uint32[n_rows][N/32] in (16-byte aligned), N % 128 == 0
- *  tiled   bs_tiled_bytes(n_rows, N) bytes out (16-byte aligned); rows
- *          rounded up to 128 are zero.  Same paper content as the sketches.
+ *  tiled   bs_tiled_bytes(n_rows, N) = n_rows * N / 8 bytes out (16-byte aligned)
  */
 size_t bs_tiled_bytes(uint32_t n_rows, uint32_t N);
 bs_status bs_tile_sketches(const uint32_t *sketch, uint32_t n_rows, uint32_t N, void *tiled,
@@ -379,9 +380,10 @@ bs_status bs_tile_sketches(const uint32_t *sketch, uint32_t n_rows, uint32_t N, 
 
 /*
  * bs_topk_pretiled -- bs_topk (tensor-core kernel) of nQ row-major query
- * sketches against a database kept tiled by bs_tile_sketches: the ranking of
- * Experiment 2 (Sec. 4) for a query stream against a resident corpus.
- * Requires N % 128 == 0, 256 <= N <= 8192, k <= 121 (BS_ERR_UNSUPPORTED
+ * sketches against a resident database (its sketches, or a copy made by
+ * bs_tile_sketches): the ranking of Experiment 2 (Sec. 4) for a query stream
+ * against a resident corpus.
+ * Requires N % 128 == 0, 256 <= N <= 8192 (BS_ERR_UNSUPPORTED
  * otherwise); no self-exclusion.  Workspace: bs_topk_pretiled_workspace_bytes.
  */
 size_t bs_topk_pretiled_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k);

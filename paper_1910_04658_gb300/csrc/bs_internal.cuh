@@ -277,21 +277,21 @@ bs_status launch_merge(int measure, const float *ws_key, const uint32_t *ws_idx,
 // tensor-core variant (bs_pairs_tc.cu)
 bool tc_supported(const uint32_t *Q, const uint32_t *DB, uint32_t N, uint32_t k);
 uint32_t tc_splits(uint32_t nQ, uint32_t nDB);
-// bytes of the k-chunk-tiled copy of an n-row sketch matrix
+// bytes of a copy of an n-row sketch matrix in the layout the tensor-core
+// kernel reads (row-major: the kernel's tensor maps read rows directly)
 size_t tc_tiled_bytes(uint32_t n, uint32_t N);
 // wait budget of the tensor-core kernel's bounded waits (cycles), and the
 // shortened budget of a fault-injected call
 constexpr long long kTcWaitLimit = kWaitLimitCycles;
 constexpr long long kTcInjectWaitLimit = 2000000ll;
-// tiled: scratch for the tiled copies, tc_tiled_bytes(nQ) + tc_tiled_bytes(nDB)
-// bytes (only the first part is used when Q and DB are the same matrix)
+// db_copy: a database kept by bs_tile_sketches (used instead of DB when set)
 // inject: test-only fault injection (0 = none, 1 = the MMA issuer never
 // announces its first accumulator; waits give up after kTcInjectWaitLimit)
 bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
                   const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
                   int exclude_self, uint32_t self_off, float *score, uint32_t *idx, float *ws_key,
-                  uint32_t *ws_idx, uint32_t splits, void *tiled, const void *db_tiled, int cfg,
-                  uint32_t inject, unsigned int *err, cudaStream_t stream);
+                  uint32_t *ws_idx, uint32_t splits, const void *db_copy, int cfg, uint32_t inject,
+                  unsigned int *err, cudaStream_t stream);
 // full count / estimate matrices on the tensor cores (N % 128 == 0, 256 <= N
 // <= 8192, 16-byte aligned A and B), reading the row-major sketches directly
 bool tc_store_supported(const uint32_t *A, const uint32_t *B, uint32_t N);

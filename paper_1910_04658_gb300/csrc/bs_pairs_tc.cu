@@ -13,68 +13,32 @@
 namespace bs {
 namespace tc {
 
-// Re-layout of one block of a packed sketch matrix [n][W] (W = 4 nKc words)
-// into k-chunk tiles: 16-byte chunk kc of row r goes to
-// dst[((r / 128) * nKc + kc) * 128 + r % 128]; rows past n are zero.  One
-// block moves 128 rows x 8 chunks through shared memory so that both the
-// reads (128-byte row pieces) and the writes (2 KB runs) are coalesced.
-__device__ __forceinline__ void tile_block(const uint4 *__restrict__ src, uint32_t n, uint32_t nKc,
-                                           uint4 *__restrict__ dst, uint32_t blk, uint32_t kc0,
-                                           uint4 (&buf)[8][129]) {
-    const int t = threadIdx.x;
-    // read: 8 consecutive threads take 8 consecutive chunks of one row
-    for (int i = t; i < 128 * 8; i += 256) {
-        const uint32_t r = i >> 3, c = i & 7;
-        const uint32_t row = blk * 128 + r, kc = kc0 + c;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (row < n && kc < nKc) v = src[(size_t)row * nKc + kc];
-        buf[c][r] = v;
-    }
-    __syncthreads();
-    // write: 128 consecutive threads cover one 2 KB run
-    for (int i = t; i < 128 * 8; i += 256) {
-        const uint32_t c = i >> 7, r = i & 127;
-        const uint32_t kc = kc0 + c;
-        if (kc < nKc) dst[((size_t)blk * nKc + kc) * 128 + r] = buf[c][r];
-    }
-}
-
-__global__ void __launch_bounds__(256)
-    tile_kchunks_kernel(const uint4 *__restrict__ src, uint32_t n, uint32_t nKc, uint4 *__restrict__ dst) {
-    __shared__ uint4 buf[8][129];
-    tile_block(src, n, nKc, dst, blockIdx.x, blockIdx.y * 8, buf);
-}
-
-// The re-layout of many matrices in one launch: matrix m owns the grid blocks
-// [blk_base[m], blk_base[m+1]), ceil(n/128) row blocks x ceil(nKc/8) chunk groups.
-struct TileJobs {
-    const uint4 *src[2 * MAXJ];
-    uint4 *dst[2 * MAXJ];
-    uint32_t n[2 * MAXJ], nKc[2 * MAXJ];
-    uint32_t blk_base[2 * MAXJ + 1];
-    uint32_t count;
-};
-
-__global__ void __launch_bounds__(256) tile_batched_kernel(const __grid_constant__ TileJobs tj) {
-    __shared__ uint4 buf[8][129];
-    const uint32_t b = blockIdx.x;
-    uint32_t lo = 0, hi = tj.count - 1;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (tj.blk_base[mid] <= b) lo = mid;
-        else hi = mid - 1;
-    }
-    const uint32_t local = b - tj.blk_base[lo];
-    const uint32_t nkg = (tj.nKc[lo] + 7) / 8;
-    tile_block(tj.src[lo], tj.n[lo], tj.nKc[lo], tj.dst[lo], local / nkg, (local % nkg) * 8, buf);
+// 2-D tensor map over a row-major sketch matrix [rows][N/32] of uint32 words:
+// boxes of SW words (256 bits) x box_rows rows, no swizzle, out-of-range rows
+// and words read as zero.  The row stride N/8 bytes is a multiple of 16 for
+// N % 128 == 0, and the box's first word index is always a multiple of SW,
+// so every copy starts on a 16-byte boundary.
+static bool make_map(CUtensorMap *m, const uint32_t *ptr, uint32_t rows, uint32_t N, uint32_t box_rows) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc || rows == 0) return false;
+    cuuint64_t dims[2] = {N / 32, rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(N / 8)};
+    cuuint32_t box[2] = {(cuuint32_t)SW, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, (void *)ptr, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // ---- persistent schedule ------------------------------------------------------
-// Cost of one work unit in k-chunks: the MMA / widening sweep over nKc
-// k-chunks plus the epilogue's fixed share of a tile (measured at a few
-// k-chunks' worth).  Only the batched form mixes costs; a single problem's
-// units all cost the same.
-constexpr uint64_t EPI_KC = 4;
+// Cost of one work unit in k-chunks.  The MMA / widening sweep over nKc
+// k-chunks and the epilogue of the previous tile run at the same time, so a
+// tile costs the larger of the two plus a fixed part; the epilogue of a
+// 128 x 240 tile was measured at about EPI_KC k-chunks of sweep (a tile of
+// N = 256..1024 bits costs the same), the fixed part at FIX_KC.  Only the
+// batched form mixes costs; a single problem's units all cost the same.
+constexpr uint64_t EPI_KC = 24, FIX_KC = 8;
+static uint64_t unit_cost(uint32_t nKc) { return (nKc > EPI_KC ? nKc : EPI_KC) + FIX_KC; }
 
 struct Schedule {
     uint32_t grid = 0, splits = 1;
@@ -150,9 +114,9 @@ static void single_schedule(uint32_t nQ, uint32_t nDB, Schedule &s, uint64_t *un
     make_schedule(1, &rbs, &tiles, &cost, unit_base, s);
 }
 
-static void fill_job(Job &J, const uint4 *tQ, const uint4 *tDB, const uint32_t *pcQ, const uint32_t *pcDB,
-                     uint32_t nQ, uint32_t nDB, uint32_t N) {
-    J.Q = tQ; J.DB = tDB; J.pcQ = pcQ; J.pcDB = pcDB;
+static void fill_job(Job &J, const uint32_t *pcQ, const uint32_t *pcDB, uint32_t nQ, uint32_t nDB,
+                     uint32_t N) {
+    J.pcQ = pcQ; J.pcDB = pcDB;
     J.nQ = nQ; J.nDB = nDB; J.N = N; J.nKc = N / 128;
     J.rbs = (nQ + BM - 1) / BM;
     J.tiles = (nDB + BN - 1) / BN;
@@ -168,8 +132,8 @@ static void fill_job(Job &J, const uint4 *tQ, const uint4 *tDB, const uint32_t *
 
 static size_t tc_cfg_smem(int cfg, uint32_t k) {
     switch (cfg) {
-#define X(c, nop, ng, sk, sh) \
-    case c: return tc::smem_bytes<nop, ng, sk, sh>(k);
+#define X(c, nop, ng, rd, sh) \
+    case c: return tc::smem_bytes<nop, ng, rd, sh>(k);
         BS_TC_CONFIGS(X)
 #undef X
     }
@@ -178,9 +142,8 @@ static size_t tc_cfg_smem(int cfg, uint32_t k) {
 
 bool tc_cfg_fits(int cfg, uint32_t k) { return tc_cfg_smem(cfg, k) <= tc::kSmemLimit; }
 
-// default: the first configuration in this order that fits -- two epilogue
-// groups before one, whole-128-byte slots (each slot hand-off has a fixed
-// cost) before finer ones
+// default: the first configuration in table order that fits -- deeper
+// operand rings and two epilogue groups first
 int tc_default_cfg(uint32_t k) {
     for (int c = 0; c < tc::kTcConfigs; ++c)
         if (tc_cfg_fits(c, k)) return c;
@@ -188,7 +151,7 @@ int tc_default_cfg(uint32_t k) {
 }
 
 bool tc_shape_ok(uint32_t N, uint32_t k) {
-    return (N % 128) == 0 && N >= 256 && N <= 8192 && k >= 1 && tc_cfg_fits(3, k);
+    return (N % 128) == 0 && N >= 256 && N <= 8192 && k >= 1 && tc_cfg_fits(tc::kTcConfigs - 1, k);
 }
 
 bool tc_supported(const uint32_t *Q, const uint32_t *DB, uint32_t N, uint32_t k) {
@@ -209,16 +172,14 @@ uint32_t tc_splits(uint32_t nQ, uint32_t nDB) {
     return s.splits;
 }
 
-size_t tc_tiled_bytes(uint32_t n, uint32_t N) {
-    return (size_t)((n + 127) / 128) * 128 * (N / 8);
-}
+// The tensor-core kernel reads row-major sketches through tensor maps, so a
+// database kept "in the kernel's layout" is a plain copy of its rows.
+size_t tc_tiled_bytes(uint32_t n, uint32_t N) { return (size_t)n * (N / 8); }
 
 bs_status tile_sketches(const uint32_t *sk, uint32_t n, uint32_t N, void *tiled, cudaStream_t stream) {
-    const uint32_t nKc = N / 128;
-    dim3 g((n + 127) / 128, (nKc + 7) / 8);
-    tc::tile_kchunks_kernel<<<g, 256, 0, stream>>>(reinterpret_cast<const uint4 *>(sk), n, nKc,
-                                                   reinterpret_cast<uint4 *>(tiled));
-    return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+    return cudaMemcpyAsync(tiled, sk, tc_tiled_bytes(n, N), cudaMemcpyDeviceToDevice, stream) == cudaSuccess
+               ? BS_OK
+               : BS_ERR_CUDA;
 }
 
 template <int NJ>
@@ -235,32 +196,15 @@ static cudaError_t launch_measure(int measure, int cfg, const tc::Args<NJ> &p, u
 bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
                   const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
                   int exclude_self, uint32_t self_off, float *score, uint32_t *idx, float *ws_key,
-                  uint32_t *ws_idx, uint32_t splits, void *tiled, const void *db_tiled, int cfg_req,
-                  uint32_t inject, unsigned int *err, cudaStream_t stream) {
-    const uint32_t nKc = N / 128;
+                  uint32_t *ws_idx, uint32_t splits, const void *db_copy, int cfg_req, uint32_t inject,
+                  unsigned int *err, cudaStream_t stream) {
     const int cfg = cfg_req >= 0 ? cfg_req : tc_default_cfg(k);
     if (cfg < 0 || !tc_cfg_fits(cfg, k)) return BS_ERR_UNSUPPORTED;
-    // k-chunk-tiled copies of the operands (one copy when Q and DB coincide;
-    // none for DB when the caller keeps it tiled)
-    uint4 *tQ = reinterpret_cast<uint4 *>(tiled);
-    uint4 *tDB = tQ;
-    const bool same = (Q == DB && nQ == nDB && !db_tiled);
-    {
-        dim3 g((nQ + 127) / 128, (nKc + 7) / 8);
-        tc::tile_kchunks_kernel<<<g, 256, 0, stream>>>(reinterpret_cast<const uint4 *>(Q), nQ, nKc, tQ);
-    }
-    if (db_tiled) {
-        tDB = const_cast<uint4 *>(reinterpret_cast<const uint4 *>(db_tiled));
-    } else if (!same) {
-        tDB = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(tiled) + tc_tiled_bytes(nQ, N));
-        dim3 g((nDB + 127) / 128, (nKc + 7) / 8);
-        tc::tile_kchunks_kernel<<<g, 256, 0, stream>>>(reinterpret_cast<const uint4 *>(DB), nDB, nKc, tDB);
-    }
-    if (cudaGetLastError() != cudaSuccess) return BS_ERR_CUDA;
+    if (db_copy) DB = reinterpret_cast<const uint32_t *>(db_copy);
     static thread_local tc::Args<1> p;   // ~2 KB of launch arguments, rebuilt per call
     memset(&p, 0, sizeof(p));
     tc::Job &J = p.job[0];
-    tc::fill_job(J, tQ, tDB, pcQ, pcDB, nQ, nDB, N);
+    tc::fill_job(J, pcQ, pcDB, nQ, nDB, N);
     J.exclude_self = exclude_self;
     J.self_off = self_off;
     J.score = score; J.idx = idx; J.ws_key = ws_key; J.ws_idx = ws_idx;
@@ -268,6 +212,8 @@ bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uin
     tc::single_schedule(nQ, nDB, s, &J.unit_base);
     if (s.units == 0) return BS_OK;
     if (s.splits != splits) return BS_ERR_INVALID_ARG;   // workspace planned for another shape
+    if (!tc::make_map(&p.maps[0], Q, nQ, N, tc::BM) || !tc::make_map(&p.maps[1], DB, nDB, N, tc::BN))
+        return BS_ERR_CUDA;
     memcpy(p.block_start, s.block_start, sizeof(uint64_t) * (s.grid + 1));
     p.njobs = 1;
     p.k = k; p.splits = splits;
@@ -285,14 +231,14 @@ bs_status estimate_tc(const uint32_t *A, const uint32_t *pcA, uint32_t nA, const
     static thread_local tc::Args<1> p;
     memset(&p, 0, sizeof(p));
     tc::Job &J = p.job[0];
-    tc::fill_job(J, reinterpret_cast<const uint4 *>(A), reinterpret_cast<const uint4 *>(B), pcA, pcB, nA,
-                 nB, N);
-    J.rowmajor = 1;
+    tc::fill_job(J, pcA, pcB, nA, nB, N);
     J.out = out;
     J.counts = counts;
     tc::Schedule s;
     tc::single_schedule(nA, nB, s, &J.unit_base);
     if (s.units == 0) return BS_OK;
+    if (!tc::make_map(&p.maps[0], A, nA, N, tc::BM) || !tc::make_map(&p.maps[1], B, nB, N, tc::BN))
+        return BS_ERR_CUDA;
     memcpy(p.block_start, s.block_start, sizeof(uint64_t) * (s.grid + 1));
     p.njobs = 1;
     p.splits = 1;
@@ -328,19 +274,15 @@ bs_status plan_batch(const bs_topk_job *jobs, uint32_t n, uint32_t k, BatchPlan 
         bp.src[j] = i;
         bp.rbs[j] = (jb.nQ + tc::BM - 1) / tc::BM;
         bp.tiles[j] = (jb.nDB + tc::BN - 1) / tc::BN;
-        bp.cost[j] = jb.N / 128 + tc::EPI_KC;
+        bp.cost[j] = tc::unit_cost(jb.N / 128);
     }
     tc::make_schedule(bp.nj, bp.rbs, bp.tiles, bp.cost, bp.unit_base, bp.s);
     return BS_OK;
 }
 
-// workspace of job i: [split lists][tiled Q][tiled DB]
+// workspace of job i: its split lists (none when no row block is split)
 size_t job_ws(const bs_topk_job &jb, uint32_t k, uint32_t splits) {
-    size_t b = 0;
-    if (splits > 1) b += align256((size_t)splits * jb.nQ * k * 8);
-    b += align256(tc_tiled_bytes(jb.nQ, jb.N));
-    if (!(jb.Q == jb.DB && jb.nQ == jb.nDB)) b += align256(tc_tiled_bytes(jb.nDB, jb.N));
-    return b;
+    return splits > 1 ? align256((size_t)splits * jb.nQ * k * 8) : 0;
 }
 }  // namespace
 
@@ -379,27 +321,15 @@ bs_status topk_tc_batched(const bs_topk_job *jobs, uint32_t n, int measure, uint
     if (bp.nj == 0) return BS_OK;
     size_t need = 0;
     for (uint32_t j = 0; j < bp.nj; ++j) need += job_ws(jobs[bp.src[j]], k, bp.s.splits);
-    if (!workspace || workspace_bytes < need) return BS_ERR_NO_MEMORY;
-    if (reinterpret_cast<uintptr_t>(workspace) & 255u) return BS_ERR_INVALID_ARG;
+    if (need > 0 && (!workspace || workspace_bytes < need)) return BS_ERR_NO_MEMORY;
+    if (need > 0 && (reinterpret_cast<uintptr_t>(workspace) & 255u)) return BS_ERR_INVALID_ARG;
 
     static thread_local tc::Args<tc::MAXJ> p;
-    static thread_local tc::TileJobs tj;
     static thread_local MergeJobs mj;
     memset(&p, 0, sizeof(p));
-    memset(&tj, 0, sizeof(tj));
     memset(&mj, 0, sizeof(mj));
     const uint32_t splits = bp.s.splits;
     uint8_t *w = reinterpret_cast<uint8_t *>(workspace);
-    uint32_t blk = 0;
-    auto add_tile = [&](const uint32_t *src, uint32_t rows, uint32_t N, uint4 *dst) {
-        const uint32_t m = tj.count++;
-        tj.src[m] = reinterpret_cast<const uint4 *>(src);
-        tj.dst[m] = dst;
-        tj.n[m] = rows;
-        tj.nKc[m] = N / 128;
-        tj.blk_base[m] = blk;
-        blk += ((rows + 127) / 128) * ((N / 128 + 7) / 8);
-    };
     for (uint32_t j = 0; j < bp.nj; ++j) {
         const bs_topk_job &jb = jobs[bp.src[j]];
         tc::Job &J = p.job[j];
@@ -410,16 +340,10 @@ bs_status topk_tc_batched(const bs_topk_job *jobs, uint32_t n, int measure, uint
             ws_idx = reinterpret_cast<uint32_t *>(ws_key + (size_t)splits * jb.nQ * k);
             w += align256((size_t)splits * jb.nQ * k * 8);
         }
-        uint4 *tQ = reinterpret_cast<uint4 *>(w);
-        w += align256(tc_tiled_bytes(jb.nQ, jb.N));
-        add_tile(jb.Q, jb.nQ, jb.N, tQ);
-        uint4 *tDB = tQ;
-        if (!(jb.Q == jb.DB && jb.nQ == jb.nDB)) {
-            tDB = reinterpret_cast<uint4 *>(w);
-            w += align256(tc_tiled_bytes(jb.nDB, jb.N));
-            add_tile(jb.DB, jb.nDB, jb.N, tDB);
-        }
-        tc::fill_job(J, tQ, tDB, jb.pcQ, jb.pcDB, jb.nQ, jb.nDB, jb.N);
+        if (!tc::make_map(&p.maps[2 * j], jb.Q, jb.nQ, jb.N, tc::BM) ||
+            !tc::make_map(&p.maps[2 * j + 1], jb.DB, jb.nDB, jb.N, tc::BN))
+            return BS_ERR_CUDA;
+        tc::fill_job(J, jb.pcQ, jb.pcDB, jb.nQ, jb.nDB, jb.N);
         J.exclude_self = jb.exclude_self;
         J.self_off = 0;
         J.score = jb.score; J.idx = jb.idx; J.ws_key = ws_key; J.ws_idx = ws_idx;
@@ -430,9 +354,6 @@ bs_status topk_tc_batched(const bs_topk_job *jobs, uint32_t n, int measure, uint
         mj.row_base[j + 1] = mj.row_base[j] + jb.nQ;
     }
     mj.njobs = bp.nj;
-    tj.blk_base[tj.count] = blk;
-    tc::tile_batched_kernel<<<blk, 256, 0, stream>>>(tj);
-    if (cudaGetLastError() != cudaSuccess) return BS_ERR_CUDA;
     memcpy(p.block_start, bp.s.block_start, sizeof(uint64_t) * (bp.s.grid + 1));
     p.njobs = bp.nj;
     p.k = k;

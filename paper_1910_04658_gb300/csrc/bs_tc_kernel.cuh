@@ -21,18 +21,21 @@
 // row block by row block; block c takes the contiguous range
 // [block_start[c], block_start[c+1]) that the host balanced by cost.  A row
 // block cut between blocks yields one partial list per block ("part"), merged
-// afterwards.
+// afterwards.  Every operand slot covers 256 sketch bits (two 128-bit
+// k-chunks) of a tile's 128 query and 240 database rows.
 //   warp 0     TMEM owner (512 columns: two 240-column accumulators and the
 //              unit scale factors) and single-thread MMA issuer:
 //              tcgen05.mma.kind::mxf4.block_scale (M=128, N=240, K=64), four
-//              per 128-byte operand slot
-//   warps 1-4  fetch the packed bits of up to three rows each (query row e,
-//              database rows e and e + 128 of the tile) and widen them into
-//              the swizzled K-major FP4 layout the MMA descriptors point at.
-//              The fetches read a k-chunk-tiled copy of the sketches (128
-//              rows x 16 bytes contiguous per k-chunk), so a warp's load is
-//              512 contiguous bytes; four k-chunks are in flight per thread.
-//   warps 5+   epilogue, one or two groups of 4 warps, one query row per
+//              per operand slot
+//   warp 1     TMA producer (one thread): for every slot, two 2-D tensor-map
+//              loads of the packed bits straight from the row-major sketch
+//              matrices (a 32-byte x 128-row box of Q, a 32-byte x 240-row box
+//              of DB; rows and words past the matrix end arrive as zeros) into
+//              a RD-deep ring of raw slots, completion on mbarriers
+//   warps 2-5  widening: query row e and database rows e and e + 128 of a
+//              raw slot, read from shared memory and written as FP4 into the
+//              128-byte-swizzled K-major layout the MMA descriptors point at
+//   warps 6+   epilogue, one or two groups of 4 warps, one query row per
 //              thread, 32 TMEM columns per tcgen05.ld.  Top-k: a closed-form
 //              bound on the union count admits only pairs that can beat the
 //              row's current k-th best, whose exact FP32 estimate then enters
@@ -55,6 +58,7 @@ constexpr int BM = 128;                    // query rows per block (UMMA M, TMEM
 constexpr int BN = 240;                    // database rows per tile (UMMA N)
 constexpr int BNP = 256;                   // per-column arrays padded to whole 32-column chunks
 constexpr int KCW = 4;                     // packed words per k-chunk (128 bits)
+constexpr int SW = 8;                      // packed words per operand slot (256 bits)
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t SF_COL = 2 * BN;        // 480: unit scale factors (A at +0, B at +16)
 constexpr int MAXG = 192;                  // most persistent blocks per launch
@@ -63,34 +67,22 @@ constexpr int MODE_TOPK = 0, MODE_STORE = 1;
 enum { INJECT_NONE = 0, INJECT_STALL = 1 };
 
 // threads per block with NG epilogue groups
-__host__ __device__ constexpr int threads_for(int NG) { return 32 * (5 + 4 * NG); }
+__host__ __device__ constexpr int threads_for(int NG) { return 32 * (6 + 4 * NG); }
 
-// Operand slot geometry for SK bytes of K per row.  One FP4 byte holds two
-// sketch bits, so a slot covers 2 SK bits: SK = 128 two 128-bit k-chunks
-// (128-byte swizzle), SK = 64 one k-chunk, SK = 32 half a k-chunk (64- and
-// 32-byte swizzles, so the same shared memory holds 2x / 4x as many slots).
-template <int SK>
-struct Geo {
-    static_assert(SK == 128 || SK == 64 || SK == 32, "slot width");
-    static constexpr int A = BM * SK;                       // query operand bytes
-    static constexpr int B = BN * SK;                       // database operand bytes
-    static constexpr int BYTES = A + B;                     // per slot
-    static constexpr int MMAS = SK / 32;                    // K = 64 (32 bytes) per MMA
-    static constexpr int WPS = SK / 16;                     // packed words per slot and row
-    static constexpr int SHIFT = SK == 128 ? 0 : (SK == 64 ? 1 : 2);
-    static constexpr uint64_t LAYOUT = SK == 128 ? 2 : (SK == 64 ? 4 : 6);   // descriptor swizzle code
-    static_assert(BYTES % (8 * SK) == 0 && A % (8 * SK) == 0, "swizzle atom alignment");
-};
-// k-chunks a tile's sweep covers (SK = 128 pairs them, so odd counts pad)
-template <int SK>
-__host__ __device__ __forceinline__ uint32_t kchunks_padded(uint32_t nKc) {
-    return SK == 128 ? ((nKc + 1) & ~1u) : nKc;
-}
-// operand slots per tile
-template <int SK>
-__host__ __device__ __forceinline__ uint32_t slots_per_tile(uint32_t nKc) {
-    return kchunks_padded<SK>(nKc) * KCW / (uint32_t)Geo<SK>::WPS;
-}
+// Operand slot: 256 bits of K per row as FP4 = 128 bytes, 128-byte swizzle.
+constexpr int OP_A = BM * 128;             // query operand bytes
+constexpr int OP_B = BN * 128;             // database operand bytes
+constexpr int OP_BYTES = OP_A + OP_B;      // per slot
+constexpr int MMAS = 4;                    // K = 64 (32 bytes) per MMA
+// Raw slot: the same 256 bits packed, [row][32 bytes], as the TMA box lands.
+constexpr int RAW_A = BM * 32;
+constexpr int RAW_B = BN * 32;
+constexpr int RAW_SLOT = 12288;            // RAW_A + RAW_B rounded up to 1 KB
+static_assert(OP_BYTES % 1024 == 0 && OP_A % 1024 == 0, "swizzle atom alignment");
+static_assert(RAW_A + RAW_B <= RAW_SLOT && RAW_A % 1024 == 0, "raw slot alignment");
+
+// operand slots per tile (k-chunks paired; an odd count pads with zeros)
+__host__ __device__ __forceinline__ uint32_t slots_per_tile(uint32_t nKc) { return (nKc + 1) / 2; }
 
 constexpr int CB = 8;                      // admitted pairs a row buffers within a tile
 constexpr uint32_t NO_IDX = 0xFFFFFFFFu;
@@ -101,24 +93,24 @@ constexpr uint32_t NO_IDX = 0xFFFFFFFFu;
 // letting through almost none that fall a full count short.
 constexpr float FILTER_SLACK = 0.99987793f;
 
-// Shared-memory layout for NOP operand slots and NG epilogue groups (offsets
-// from the 1024-aligned base); the NG heaps of k entries per row follow.
-template <int NOP, int NG, int SK>
+// Shared-memory layout for NOP operand slots, RD raw slots and NG epilogue
+// groups (offsets from the 1024-aligned base); the heaps follow.
+template <int NOP, int NG, int RD>
 struct Smem {
     static constexpr int op = 0;
-    static constexpr int col = op + NOP * Geo<SK>::BYTES;       // [2 tiles][3][BNP] floats
+    static constexpr int raw = op + NOP * OP_BYTES;
+    static constexpr int col = raw + RD * RAW_SLOT;             // [2 tiles][3][BNP] floats
     static constexpr int bars = col + 2 * 3 * BNP * 4;
     static constexpr int thr = bars + 256;                      // [NG][BM] key, idx, size
     static constexpr int lock = thr + NG * BM * 12;             // [BM] shared-heap row locks
     static constexpr int cbuf = lock + BM * 4;                  // [NG][CB][BM] admitted pairs
     static constexpr int heap = cbuf + NG * CB * BM * 4;
-    static_assert((2 * NOP + 5) * 8 + 8 <= 256, "barrier area");
+    static_assert((2 * NOP + 2 * RD + 5) * 8 + 8 <= 256, "barrier area");
 };
 
-// One problem of the job table: nQ query rows against nDB database rows.
+// One problem of the job table: nQ query rows against nDB database rows.  The
+// sketches themselves are reached through the tensor maps of Args.
 struct Job {
-    const uint4 *Q, *DB;        // k-chunk-tiled sketches [ceil(n/128)][nKc][128] x 16 bytes,
-                                // or row-major [n][nKc] x 16 bytes when rowmajor
     const uint32_t *pcQ, *pcDB;
     float *score;               // top-k, splits == 1: [nQ][k]
     uint32_t *idx;
@@ -131,13 +123,13 @@ struct Job {
     uint32_t rbs, tiles;        // row blocks, database tiles
     uint32_t self_off;          // exclude_self drops the pair q == self_off + j
     int exclude_self;
-    uint32_t rowmajor;          // operands read in the caller's row-major layout
     float invL;                 // 1 / ln(1 - 1/N)
     float log2N;
 };
 
 template <int NJ>
 struct Args {
+    CUtensorMap maps[2 * NJ];         // job j: Q at 2j (box 8 words x 128 rows), DB at 2j + 1 (x 240)
     Job job[NJ];
     uint64_t block_start[MAXG + 1];   // block c: units [block_start[c], block_start[c+1])
     uint32_t njobs;
@@ -216,16 +208,15 @@ __device__ __forceinline__ void tmem_fill32(uint32_t taddr, uint32_t v) {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, SK-byte swizzle, 8-row groups
-// 8 * SK bytes apart (SBO), leading offset unused for this layout (1).
-template <int SK>
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), leading offset unused for this layout (1).
 __device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
     d |= (uint64_t)1 << 16;                     // LBO (ignored for swizzled K-major)
-    d |= (uint64_t)((8 * SK) >> 4) << 32;       // SBO
+    d |= (uint64_t)(1024 >> 4) << 32;           // SBO
     d |= (uint64_t)1 << 46;                     // descriptor version for tcgen05
-    d |= Geo<SK>::LAYOUT << 61;                 // swizzle mode
+    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
     return d;
 }
 
@@ -236,15 +227,14 @@ constexpr uint32_t IDESC = (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) 
                            ((uint32_t)(BM >> 4) << 24);
 constexpr uint32_t UNIT_SCALES = 0x7F7F7F7Fu;   // four UE8M0 2^0
 
-// Widen WPS packed words x[] of one row into FP4 and store them into the
-// SK-byte-swizzled K-major tile: row r at (r / 8) * 8 SK + (r % 8) * SK, the
-// 16-byte chunk of word c at position c ^ ((r % 8) >> SHIFT).
-template <int SK>
-__device__ __forceinline__ void widen_store(uint8_t *op_tile, int r, const uint32_t *x) {
-    uint8_t *row = op_tile + (r >> 3) * (8 * SK) + (r & 7) * SK;
-    const int sw = (r & 7) >> Geo<SK>::SHIFT;
+// Widen the 8 packed words x[] of one row (256 bits) into FP4 and store them
+// into the 128-byte-swizzled K-major tile: row r at (r / 8) * 1024 + (r % 8) *
+// 128, the 16-byte chunk of word c at position c ^ (r % 8).
+__device__ __forceinline__ void widen_store(uint8_t *op_tile, int r, const uint32_t (&x)[SW]) {
+    uint8_t *row = op_tile + (r >> 3) * 1024 + (r & 7) * 128;
+    const int sw = r & 7;
 #pragma unroll
-    for (int c = 0; c < Geo<SK>::WPS; ++c) {
+    for (int c = 0; c < SW; ++c) {
         const uint32_t v = x[c];
         uint4 o;
         o.x = (v << 1) & 0x22222222u;
@@ -253,6 +243,14 @@ __device__ __forceinline__ void widen_store(uint8_t *op_tile, int r, const uint3
         o.w = (v >> 2) & 0x22222222u;
         *reinterpret_cast<uint4 *>(row + ((c ^ sw) << 4)) = o;
     }
+}
+
+// The 8 packed words of raw row r (rows are 32 bytes apart).
+__device__ __forceinline__ void raw_row(const uint8_t *raw, int r, uint32_t (&x)[SW]) {
+    const uint4 a = *reinterpret_cast<const uint4 *>(raw + r * 32);
+    const uint4 b = *reinterpret_cast<const uint4 *>(raw + r * 32 + 16);
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+    x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
 }
 
 // ---- per-row heap of the k best (root = worst), interleaved across rows ------
@@ -488,19 +486,20 @@ __device__ __forceinline__ uint32_t block_of(const Args<NJ> &p, uint64_t x, uint
     return lo;
 }
 
-template <int MODE, int M, int NOP, int NG, int SK, bool SHARED, int NJ>
+template <int MODE, int M, int NOP, int NG, int RD, bool SHARED, int NJ>
 __global__ void __launch_bounds__(threads_for(NG), 1)
     pair_tc_kernel(const __grid_constant__ Args<NJ> p) {
-    using Smem = tc::Smem<NOP, NG, SK>;
-    using G = Geo<SK>;
+    using Smem = tc::Smem<NOP, NG, RD>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *op = base + Smem::op;
+    uint8_t *raw = base + Smem::raw;
     float *colv = reinterpret_cast<float *>(base + Smem::col);      // [2][3][BNP]
     uint64_t *bars = reinterpret_cast<uint64_t *>(base + Smem::bars);
     uint64_t *op_full = bars, *op_empty = bars + NOP;
-    uint64_t *acc_full = bars + 2 * NOP, *acc_empty = acc_full + 2;
+    uint64_t *raw_full = bars + 2 * NOP, *raw_empty = raw_full + RD;
+    uint64_t *acc_full = raw_empty + RD, *acc_empty = acc_full + 2;
     uint64_t *drain_bar = acc_empty + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain_bar + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
@@ -530,6 +529,10 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
             mbar_init(&op_full[i], 4);
             mbar_init(&op_empty[i], 1);
         }
+        for (int i = 0; i < RD; ++i) {
+            mbar_init(&raw_full[i], 1);
+            mbar_init(&raw_empty[i], 4);
+        }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&acc_full[i], 1);
             mbar_init(&acc_empty[i], 4 * NG);
@@ -553,7 +556,7 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     // unit block scales (all 128 lanes of columns SF_COL ..) before any MMA
-    if (warp >= 5 && warp < 9) tmem_fill32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + SF_COL, UNIT_SCALES);
+    if (warp >= 6 && warp < 10) tmem_fill32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + SF_COL, UNIT_SCALES);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -574,7 +577,7 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
             cur.start(jobs, njobs, u_lo);
             const uint32_t sfa = tmem + SF_COL, sfb = tmem + SF_COL + 16;
             for (uint32_t t = 0; t < n_my_tiles; ++t) {
-                const uint32_t nsl = slots_per_tile<SK>(jobs[cur.j].nKc);
+                const uint32_t nsl = slots_per_tile(jobs[cur.j].nKc);
                 const uint32_t ab = t & 1;
                 if (t >= 2) wait(&acc_empty[ab], ((t >> 1) - 1) & 1);
                 tc_fence_after();
@@ -584,12 +587,12 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                     wait(&op_full[o], (sl / NOP) & 1);
                     tc_fence_after();
                     if (!*abort_flag) {
-                        const uint32_t a_addr = smem_u32(op + o * G::BYTES);
-                        const uint32_t b_addr = a_addr + G::A;
+                        const uint32_t a_addr = smem_u32(op + o * OP_BYTES);
+                        const uint32_t b_addr = a_addr + OP_A;
 #pragma unroll
-                        for (int kk = 0; kk < G::MMAS; ++kk)
-                            mma_fp4(d_tmem, sw_desc<SK>(a_addr + kk * 32), sw_desc<SK>(b_addr + kk * 32),
-                                    IDESC, sfa, sfb, (c | (uint32_t)kk) != 0);
+                        for (int kk = 0; kk < MMAS; ++kk)
+                            mma_fp4(d_tmem, sw_desc(a_addr + kk * 32), sw_desc(b_addr + kk * 32), IDESC, sfa, sfb,
+                                    (c | (uint32_t)kk) != 0);
                     }
                     mma_commit(&op_empty[o]);
                 }
@@ -602,119 +605,69 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
             mma_commit(drain_bar);
             if (!mbar_wait(drain_bar, 0, p.wait_limit)) raise_error(p.err, BS_ERR_TIMEOUT);
         }
-    } else if (warp < 5) {
-        // ------------------------------ widening ------------------------------
-        // thread e owns query row e and database rows e and e + 128 of a tile
-        const int e = tid - 32;   // 0..127
-        const bool two_b = e + 128 < BN;
-        const uint4 z = make_uint4(0, 0, 0, 0);
-        // k-chunks of this block's sweep (each tile padded to whole slots)
-        uint32_t total = 0;
-        if (NJ == 1) {
-            total = n_my_tiles * kchunks_padded<SK>(jobs[0].nKc);
-        } else {
-            Cursor w;
-            w.start(jobs, njobs, u_lo);
-            for (uint32_t t = 0; t < n_my_tiles; ++t) {
-                total += kchunks_padded<SK>(jobs[w.j].nKc);
-                w.step(jobs);
+    } else if (warp == 1) {
+        // ----------------------------- TMA producer -----------------------------
+        if (lane == 0) {
+            uint32_t rs = 0;   // raw slots issued
+            Cursor cur;
+            cur.start(jobs, njobs, u_lo);
+            for (uint32_t t = 0; t < n_my_tiles && !*abort_flag; ++t) {
+                const uint32_t nsl = slots_per_tile(jobs[cur.j].nKc);
+                const CUtensorMap *mq = &p.maps[2 * cur.j];
+                const CUtensorMap *md = mq + 1;
+                const int yq = (int)(cur.rb * BM), yd = (int)(cur.tile * BN);
+                for (uint32_t c = 0; c < nsl; ++c) {
+                    const uint32_t o = rs % RD;
+                    if (rs >= RD) wait(&raw_empty[o], ((rs / RD) - 1) & 1);
+                    if (*abort_flag) break;
+                    uint8_t *dst = raw + o * RAW_SLOT;
+                    mbar_arrive_expect_tx(&raw_full[o], RAW_A + RAW_B);
+                    tma_load_2d(dst, mq, &raw_full[o], (int)(SW * c), yq);
+                    tma_load_2d(dst + RAW_A, md, &raw_full[o], (int)(SW * c), yd);
+                    ++rs;
+                }
+                cur.step(jobs);
             }
+            // every copy issued here has landed before the block may exit
+            for (uint32_t i = rs > (uint32_t)RD ? rs - RD : 0; i < rs; ++i)
+                if (!mbar_wait(&raw_full[i % RD], (i / RD) & 1, p.wait_limit)) raise_error(p.err, BS_ERR_TIMEOUT);
         }
-        // fetch cursor (job, row block, tile, k-chunk) of the next k-chunk;
-        // fetch() is called for g = 0, 1, 2, ... in order, so it only steps
-        Cursor fc;
-        fc.start(jobs, njobs, u_lo);
-        uint32_t f_kc = 0;
-        auto fetch = [&](uint32_t g, uint4 &a_, uint4 &b0_, uint4 &b1_) {
-            if (g >= total) return;
-            const Job &J = jobs[fc.j];
-            const uint32_t kc = f_kc, rb = fc.rb, tile = fc.tile, nKc = J.nKc;
-            if (++f_kc == kchunks_padded<SK>(nKc)) {
-                f_kc = 0;
-                fc.step(jobs);
+    } else if (warp < 6) {
+        // ------------------------------ widening ------------------------------
+        // thread e owns query row e and database rows e and e + 128 of a slot
+        const int e = tid - 64;   // 0..127
+        const bool two_b = e + 128 < BN;
+        uint32_t sl = 0;
+        Cursor cur;
+        cur.start(jobs, njobs, u_lo);
+        for (uint32_t t = 0; t < n_my_tiles; ++t) {
+            const uint32_t nsl = slots_per_tile(jobs[cur.j].nKc);
+            for (uint32_t c = 0; c < nsl; ++c, ++sl) {
+                const uint32_t ro = sl % RD, o = sl % NOP;
+                wait(&raw_full[ro], (sl / RD) & 1);
+                const uint8_t *src = raw + ro * RAW_SLOT;
+                uint32_t xa[SW], xb0[SW], xb1[SW];
+                raw_row(src, e, xa);
+                raw_row(src + RAW_A, e, xb0);
+                if (two_b) raw_row(src + RAW_A, e + 128, xb1);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&raw_empty[ro]);   // the raw slot may be refilled
+                if (sl >= (uint32_t)NOP) wait(&op_empty[o], ((sl / NOP) - 1) & 1);
+                uint8_t *oA = op + o * OP_BYTES;
+                uint8_t *oB = oA + OP_A;
+                widen_store(oA, e, xa);
+                widen_store(oB, e, xb0);
+                if (two_b) widen_store(oB, e + 128, xb1);
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&op_full[o]);
             }
-            a_ = b0_ = b1_ = z;
-            if (kc < nKc) {
-                const uint32_t R0 = tile * BN + e, R1 = R0 + 128;
-                if (J.rowmajor) {   // rows past the matrix end read as zero
-                    const uint32_t qr = rb * BM + e;
-                    if (qr < J.nQ) a_ = __ldg(J.Q + (size_t)qr * nKc + kc);
-                    if (R0 < J.nDB) b0_ = __ldg(J.DB + (size_t)R0 * nKc + kc);
-                    if (two_b && R1 < J.nDB) b1_ = __ldg(J.DB + (size_t)R1 * nKc + kc);
-                } else {            // the tiled copies hold whole 128-row blocks
-                    const uint32_t nblk = (J.nDB + 127) / 128;
-                    a_ = __ldg(J.Q + ((size_t)rb * nKc + kc) * 128 + e);
-                    if ((R0 >> 7) < nblk) b0_ = __ldg(J.DB + ((size_t)(R0 >> 7) * nKc + kc) * 128 + (R0 & 127));
-                    if (two_b && (R1 >> 7) < nblk)
-                        b1_ = __ldg(J.DB + ((size_t)(R1 >> 7) * nKc + kc) * 128 + (R1 & 127));
-                }
-            }
-        };
-        auto publish = [&](uint32_t o) {
-            fence_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&op_full[o]);
-        };
-        // four k-chunks in flight; a fixed rotation keeps them in registers
-        uint4 ra[4], rb0[4], rb1[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) fetch(u, ra[u], rb0[u], rb1[u]);
-        for (uint32_t g0 = 0; g0 < total; g0 += 4) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const uint32_t g = g0 + u;
-                if (g >= total) break;
-                if (SK == 128) {
-                    if (u & 1) {   // k-chunks g - 1 and g fill one slot
-                        const uint32_t sl = g >> 1;
-                        const uint32_t o = sl % NOP;
-                        if (sl >= NOP) wait(&op_empty[o], ((sl / NOP) - 1) & 1);
-                        uint8_t *oA = op + o * G::BYTES;
-                        uint8_t *oB = oA + G::A;
-                        {
-                            const uint32_t x[8] = {ra[u - 1].x, ra[u - 1].y, ra[u - 1].z, ra[u - 1].w,
-                                                   ra[u].x,     ra[u].y,     ra[u].z,     ra[u].w};
-                            widen_store<SK>(oA, e, x);
-                        }
-                        {
-                            const uint32_t x[8] = {rb0[u - 1].x, rb0[u - 1].y, rb0[u - 1].z, rb0[u - 1].w,
-                                                   rb0[u].x,     rb0[u].y,     rb0[u].z,     rb0[u].w};
-                            widen_store<SK>(oB, e, x);
-                        }
-                        if (two_b) {
-                            const uint32_t x[8] = {rb1[u - 1].x, rb1[u - 1].y, rb1[u - 1].z, rb1[u - 1].w,
-                                                   rb1[u].x,     rb1[u].y,     rb1[u].z,     rb1[u].w};
-                            widen_store<SK>(oB, e + 128, x);
-                        }
-                        publish(o);
-                        fetch(g + 3, ra[u - 1], rb0[u - 1], rb1[u - 1]);
-                        fetch(g + 4, ra[u], rb0[u], rb1[u]);
-                    }
-                } else {
-                    constexpr int SPK = KCW / G::WPS;   // slots per k-chunk: 1 or 2
-#pragma unroll
-                    for (int h = 0; h < SPK; ++h) {
-                        const uint32_t sl = g * SPK + h;
-                        const uint32_t o = sl % NOP;
-                        if (sl >= NOP) wait(&op_empty[o], ((sl / NOP) - 1) & 1);
-                        uint8_t *oA = op + o * G::BYTES;
-                        uint8_t *oB = oA + G::A;
-                        const uint32_t xa[4] = {ra[u].x, ra[u].y, ra[u].z, ra[u].w};
-                        const uint32_t xb0[4] = {rb0[u].x, rb0[u].y, rb0[u].z, rb0[u].w};
-                        const uint32_t xb1[4] = {rb1[u].x, rb1[u].y, rb1[u].z, rb1[u].w};
-                        widen_store<SK>(oA, e, xa + h * G::WPS);
-                        widen_store<SK>(oB, e, xb0 + h * G::WPS);
-                        if (two_b) widen_store<SK>(oB, e + 128, xb1 + h * G::WPS);
-                        publish(o);
-                    }
-                    fetch(g + 4, ra[u], rb0[u], rb1[u]);
-                }
-            }
+            cur.step(jobs);
         }
     } else {
         // ------------------------------ epilogue ------------------------------
-        const int grp = (warp - 5) >> 2;           // epilogue group
-        const int e = tid - 160 - 128 * grp;       // 0..127 within the group
+        const int grp = (warp - 6) >> 2;           // epilogue group
+        const int e = tid - 192 - 128 * grp;       // 0..127 within the group
         const int quarter = warp & 3;              // TMEM lanes this warp may access
         const int r = quarter * 32 + lane;         // row within the block
         // tile columns of this group
@@ -1013,26 +966,29 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
 }
 
 // ---------------------------------------------------------------------------
-// Block configurations (operand slots, epilogue groups, slot K bytes, one heap
-// per row shared by the groups); the index is the c of BS_VARIANT_TC_CFG(c).
+// Block configurations (operand slots, epilogue groups, raw-slot ring depth,
+// one heap per row shared by the groups); the index is the c of
+// BS_VARIANT_TC_CFG(c).  The default is the first that fits k in this order.
+// The last, a single operand slot, keeps k up to BS_TOPK_K_MAX on the tensor
+// cores at the cost of overlap between widening and MMA.
 // ---------------------------------------------------------------------------
-#define BS_TC_CONFIGS(X)         \
-    X(0, 3, 2, 128, false)       \
-    X(1, 2, 2, 128, false)       \
-    X(2, 3, 1, 128, false)       \
-    X(3, 2, 1, 128, false)       \
-    X(4, 4, 2, 64, false)        \
-    X(5, 8, 2, 32, false)        \
-    X(6, 6, 1, 64, false)        \
-    X(7, 4, 1, 64, false)        \
-    X(8, 3, 2, 128, true)        \
-    X(9, 2, 2, 128, true)
+#define BS_TC_CONFIGS(X)       \
+    X(0, 3, 2, 4, false)       \
+    X(1, 2, 2, 4, false)       \
+    X(2, 3, 2, 4, true)        \
+    X(3, 2, 2, 4, true)        \
+    X(4, 2, 1, 4, false)       \
+    X(5, 2, 2, 6, false)       \
+    X(6, 2, 2, 6, true)        \
+    X(7, 2, 2, 2, false)       \
+    X(8, 2, 1, 2, false)       \
+    X(9, 1, 1, 2, false)
 constexpr int kTcConfigs = 10;
 constexpr size_t kSmemLimit = 232448;   // 227 KB per block
 
-template <int NOP, int NG, int SK, bool SH>
+template <int NOP, int NG, int RD, bool SH>
 __host__ __device__ constexpr size_t smem_bytes(uint32_t k) {
-    return 1024 + Smem<NOP, NG, SK>::heap + (size_t)(SH ? 1 : NG) * k * BM * 8;
+    return 1024 + Smem<NOP, NG, RD>::heap + (size_t)(SH ? 1 : NG) * k * BM * 8;
 }
 
 // Launch of one configuration for one measure (defined in the per-measure

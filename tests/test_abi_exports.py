@@ -71,7 +71,9 @@ def test_tensor_core_plan_parts_match_the_persistent_schedule():
     for nq, ndb in ((100_000, 100_000), (4096, 1_000_000), (1000, 1000), (37, 20_000), (129, 257)):
         uses_tc, splits, launches = B.bs_topk_plan(nq, ndb, 4096, 50, B.BS_VARIANT_TC, nq == ndb)
         assert uses_tc and splits == parts(nq, ndb), (nq, ndb, splits, parts(nq, ndb))
-        assert launches == 1 + (splits > 1) + (1 if nq == ndb else 2)
+        # the ranking kernel reads row-major sketches through tensor maps: no
+        # re-layout launch, only the merge when some row block is split
+        assert launches == 1 + (splits > 1)
 
 
 def test_header_is_plain_c_and_a_c_program_links(tmp_path):

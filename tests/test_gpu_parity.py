@@ -205,8 +205,6 @@ def test_estimates_measure_subsets_and_counts_only(tiny):
 @pytest.mark.parametrize("k", [1, 20, 50, 100, 128])
 def test_topk_all_pairs_tiny(tiny, by, m, k, variant):
     N = 1024
-    if variant == "tc" and k > 121:
-        pytest.skip("tensor-core top-k keeps k <= 121 rows in shared memory")
     sk, pc, osk = _sketch_both(tiny, N, 0)
     score, idx = api.topk(sk, pc, sk, pc, N, k, by=by, exclude_self=True, variant=variant)
     oest, _ = oracle.estimate_pairs(osk, osk, N)

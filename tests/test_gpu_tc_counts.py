@@ -103,11 +103,9 @@ def test_tc_topk_odd_kchunk_counts(N, by, m):
 
 
 def test_tc_topk_largest_k():
-    # the largest k whose heaps still fit one block configuration
-    N, k = 1024, 120
+    # k = BS_TOPK_K_MAX: only the single-operand-slot configuration fits its heaps
+    N, k = 1024, B.BS_TOPK_K_MAX
     assert B.bs_topk_plan(500, 500, N, k, B.BS_VARIANT_TC)[0]
-    with pytest.raises(B.BinSketchError):
-        B.bs_topk_plan(500, 500, N, 128, B.BS_VARIANT_TC)
     c = inputs.random_csr(15, 500, 200_000, 1, 400)
     sk, pc, osk = _sketch_both(c, N, 2)
     score, idx = api.topk(sk, pc, sk, pc, N, k, by="js", exclude_self=True, variant="tc")
