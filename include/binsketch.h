@@ -179,8 +179,8 @@ bs_status bs_estimate_pairs_ex(const uint32_t *A, const uint32_t *pcA, uint32_t 
  * this shape, whichever kernel runs: partial top-k lists when a query row's
  * database is divided between blocks (the CUDA-core kernel splits the
  * database; the tensor-core kernel's persistent blocks cut some row blocks
- * in two), and for the tensor-core kernel a
- * k-chunk-tiled copy of Q and DB (N/8 bytes per row, rows rounded up to 128).
+ * in two), and for the tensor-core kernel k-chunk-tiled copies of Q (rows
+ * rounded up to 128) and DB (rows rounded up to 240), N/8 bytes per row.
  */
 size_t bs_topk_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k);
 
@@ -366,13 +366,15 @@ bs_status bs_topk_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, uint32
                        int same_matrix, uint32_t *uses_tc, uint32_t *splits, uint32_t *launches);
 
 /*
- * bs_tiled_bytes / bs_tile_sketches -- a copy of a sketch database in the
- * layout the tensor-core kernel reads.  That kernel fetches 256-bit pieces of
- * 128 query / 240 database rows straight from row-major sketches with tensor
- * maps, so the layout is the row-major one and the copy is a plain copy;
- * bs_topk_pretiled also accepts the original sketches themselves.
+ * bs_tiled_bytes / bs_tile_sketches -- keep a sketch database in the layout
+ * the tensor-core kernel reads for its database operand, so repeated searches
+ * against it skip the re-layout: row blocks of 240, each block's 16-byte
+ * k-chunks contiguous ([block][k-chunk][240 rows] x 16 bytes), so one 256-bit
+ * operand slot of a database tile is a single contiguous run for the
+ * kernel's bulk copies.
  *  sketch  uint32[n_rows][N/32] in (16-byte aligned), N % 128 == 0
- *  tiled   bs_tiled_bytes(n_rows, N) = n_rows * N / 8 bytes out (16-byte aligned)
+ *  tiled   bs_tiled_bytes(n_rows, N) bytes out (16-byte aligned); rows
+ *          rounded up to 240 are zero.  Same paper content as the sketches.
  */
 size_t bs_tiled_bytes(uint32_t n_rows, uint32_t N);
 bs_status bs_tile_sketches(const uint32_t *sketch, uint32_t n_rows, uint32_t N, void *tiled,
@@ -380,9 +382,8 @@ bs_status bs_tile_sketches(const uint32_t *sketch, uint32_t n_rows, uint32_t N, 
 
 /*
  * bs_topk_pretiled -- bs_topk (tensor-core kernel) of nQ row-major query
- * sketches against a resident database (its sketches, or a copy made by
- * bs_tile_sketches): the ranking of Experiment 2 (Sec. 4) for a query stream
- * against a resident corpus.
+ * sketches against a database kept tiled by bs_tile_sketches: the ranking of
+ * Experiment 2 (Sec. 4) for a query stream against a resident corpus.
  * Requires N % 128 == 0, 256 <= N <= 8192 (BS_ERR_UNSUPPORTED
  * otherwise); no self-exclusion.  Workspace: bs_topk_pretiled_workspace_bytes.
  */

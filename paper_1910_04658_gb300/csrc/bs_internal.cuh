@@ -166,6 +166,16 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+// contiguous global -> shared copy of `bytes` (a multiple of 16; both
+// addresses 16-byte aligned), completion counted on the mbarrier
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // consumer-warps-only named barrier
 __device__ __forceinline__ void named_sync(uint32_t id, uint32_t nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
@@ -274,24 +284,28 @@ bs_status topk_popc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const u
 bs_status launch_merge(int measure, const float *ws_key, const uint32_t *ws_idx, uint32_t nQ,
                        uint32_t k, uint32_t splits, float *score, uint32_t *idx, cudaStream_t stream);
 
-// tensor-core variant (bs_pairs_tc.cu)
+// tensor-core variant (bs_pairs_tc.cu): query blocks of 128 rows (the MMA's
+// M, one TMEM lane per row), database tiles of 208 rows (the MMA's N)
+constexpr uint32_t kTcQueryRows = 128, kTcTileRows = 208;
 bool tc_supported(const uint32_t *Q, const uint32_t *DB, uint32_t N, uint32_t k);
 uint32_t tc_splits(uint32_t nQ, uint32_t nDB);
-// bytes of a copy of an n-row sketch matrix in the layout the tensor-core
-// kernel reads (row-major: the kernel's tensor maps read rows directly)
-size_t tc_tiled_bytes(uint32_t n, uint32_t N);
+// bytes of a k-chunk-tiled copy of an n-row sketch matrix in R-row blocks
+// (R = 128 for queries, 208 for a database)
+size_t tc_tiled_bytes(uint32_t n, uint32_t N, uint32_t R);
 // wait budget of the tensor-core kernel's bounded waits (cycles), and the
 // shortened budget of a fault-injected call
 constexpr long long kTcWaitLimit = kWaitLimitCycles;
 constexpr long long kTcInjectWaitLimit = 2000000ll;
-// db_copy: a database kept by bs_tile_sketches (used instead of DB when set)
+// tiled: scratch for the tiled copies, tc_tiled_bytes(nQ, N, 128) rounded up
+// to 256 bytes, then tc_tiled_bytes(nDB, N, 208) (the second part unused when
+// db_tiled, a database kept tiled by bs_tile_sketches, is given)
 // inject: test-only fault injection (0 = none, 1 = the MMA issuer never
 // announces its first accumulator; waits give up after kTcInjectWaitLimit)
 bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
                   const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
                   int exclude_self, uint32_t self_off, float *score, uint32_t *idx, float *ws_key,
-                  uint32_t *ws_idx, uint32_t splits, const void *db_copy, int cfg, uint32_t inject,
-                  unsigned int *err, cudaStream_t stream);
+                  uint32_t *ws_idx, uint32_t splits, void *tiled, const void *db_tiled, int cfg,
+                  uint32_t inject, unsigned int *err, cudaStream_t stream);
 // full count / estimate matrices on the tensor cores (N % 128 == 0, 256 <= N
 // <= 8192, 16-byte aligned A and B), reading the row-major sketches directly
 bool tc_store_supported(const uint32_t *A, const uint32_t *B, uint32_t N);
@@ -311,8 +325,9 @@ bs_status topk_tc_batched(const bs_topk_job *jobs, uint32_t n, int measure, uint
 int tc_default_cfg(uint32_t k);
 bool tc_cfg_fits(int cfg, uint32_t k);
 bool tc_shape_ok(uint32_t N, uint32_t k);
-// row-major sketches [n][N/32] -> k-chunk tiles (N % 128 == 0)
-bs_status tile_sketches(const uint32_t *sk, uint32_t n, uint32_t N, void *tiled, cudaStream_t stream);
+// row-major sketches [n][N/32] -> k-chunk tiles of R-row blocks (N % 128 == 0)
+bs_status tile_sketches(const uint32_t *sk, uint32_t n, uint32_t N, uint32_t R, void *tiled,
+                        cudaStream_t stream);
 
 // Batched merge of split lists: for job j, lists key[j]/ix[j] [splits][nQ[j]][k]
 // into score[j]/idx[j] [nQ[j]][k]; rows numbered job by job from row_base.

@@ -707,15 +707,16 @@ bs_status bs_estimate_pairs(const uint32_t *A, const uint32_t *pcA, uint32_t nA,
 // both operands; each part starts on a 256-byte boundary.
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static size_t tc_workspace(uint32_t nQ, uint32_t k, uint32_t splits) {
-    return align256(ws_bytes(splits, nQ, k));
+static size_t tc_workspace(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, uint32_t splits) {
+    return align256(ws_bytes(splits, nQ, k)) + align256(tc_tiled_bytes(nQ, N, kTcQueryRows)) +
+           align256(tc_tiled_bytes(nDB, N, kTcTileRows));
 }
 
 size_t bs_topk_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k) {
     if (nQ == 0 || nDB == 0 || k == 0) return 0;
     size_t need = ws_bytes(popc_splits(nQ, nDB), nQ, k);
     if (valid_N(N) && tc_shape_ok(N, k)) {
-        const size_t t = tc_workspace(nQ, k, tc_splits(nQ, nDB));
+        const size_t t = tc_workspace(nQ, nDB, N, k, tc_splits(nQ, nDB));
         if (t > need) need = t;
     }
     return need;
@@ -755,9 +756,10 @@ static bs_status topk_impl(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, 
     }
     if (inject && !use_tc) return BS_ERR_UNSUPPORTED;   // the injector lives in the tensor-core kernel
     const uint32_t splits = use_tc ? tc_splits(nQ, nDB) : popc_splits(nQ, nDB);
-    const size_t need = use_tc ? tc_workspace(nQ, k, splits) : ws_bytes(splits, nQ, k);
+    const size_t need = use_tc ? tc_workspace(nQ, nDB, N, k, splits) : ws_bytes(splits, nQ, k);
     float *ws_key = nullptr;
     uint32_t *ws_idx = nullptr;
+    void *tiled = nullptr;
     if (need > 0) {
         if (!workspace || workspace_bytes < need) return BS_ERR_NO_MEMORY;
         if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return BS_ERR_INVALID_ARG;
@@ -766,9 +768,10 @@ static bs_status topk_impl(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, 
             ws_key = reinterpret_cast<float *>(w);
             ws_idx = reinterpret_cast<uint32_t *>(ws_key + (size_t)splits * nQ * k);
         }
+        tiled = w + align256(ws_bytes(splits, nQ, k));
     }
     bs_status s1 = use_tc ? topk_tc(Q, pcQ, nQ, DB, pcDB, nDB, N, m, k, exclude_self, self_off, score,
-                                    idx, ws_key, ws_idx, splits, nullptr, tc_cfg, inject, err, st)
+                                    idx, ws_key, ws_idx, splits, tiled, nullptr, tc_cfg, inject, err, st)
                           : topk_popc(Q, pcQ, nQ, DB, pcDB, nDB, N, m, k, exclude_self, self_off,
                                       score, idx, ws_key, ws_idx, splits, err, st);
     if (s1 != BS_OK || splits <= 1) return s1;
@@ -824,8 +827,10 @@ bs_status bs_topk_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, uint32
     }
     const uint32_t s = (nQ == 0) ? 0 : (tc ? tc_splits(nQ, nDB) : popc_splits(nQ, nDB));
     uint32_t l = 0;
-    if (nQ > 0) l = 1 + (s > 1 ? 1 : 0);
-    (void)same_matrix;   // no re-layout launches: the tensor-core kernel reads row-major sketches
+    // the tensor-core path re-lays out Q (128-row blocks) and DB (208-row
+    // blocks) separately, even when they are the same matrix
+    (void)same_matrix;
+    if (nQ > 0) l = 1 + (s > 1 ? 1 : 0) + (tc ? 2 : 0);
     if (uses_tc) *uses_tc = tc ? 1 : 0;
     if (splits) *splits = s;
     if (launches) *launches = l;
@@ -834,7 +839,7 @@ bs_status bs_topk_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, uint32
 
 size_t bs_tiled_bytes(uint32_t n, uint32_t N) {
     if (!valid_N(N) || (N % 128) != 0) return 0;
-    return tc_tiled_bytes(n, N);
+    return tc_tiled_bytes(n, N, kTcTileRows);
 }
 
 bs_status bs_tile_sketches(const uint32_t *sketch, uint32_t n_rows, uint32_t N, void *tiled,
@@ -844,12 +849,12 @@ bs_status bs_tile_sketches(const uint32_t *sketch, uint32_t n_rows, uint32_t N, 
     if (!sketch || !tiled) return BS_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(sketch) & 15u) || (reinterpret_cast<uintptr_t>(tiled) & 15u))
         return BS_ERR_INVALID_ARG;
-    return tile_sketches(sketch, n_rows, N, tiled, (cudaStream_t)stream);
+    return tile_sketches(sketch, n_rows, N, kTcTileRows, tiled, (cudaStream_t)stream);
 }
 
 size_t bs_topk_pretiled_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k) {
     if (nQ == 0 || nDB == 0 || !valid_N(N) || !tc_shape_ok(N, k)) return 0;
-    return align256(ws_bytes(tc_splits(nQ, nDB), nQ, k));
+    return align256(ws_bytes(tc_splits(nQ, nDB), nQ, k)) + align256(tc_tiled_bytes(nQ, N, kTcQueryRows));
 }
 
 bs_status bs_topk_pretiled(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const void *DB_tiled,
@@ -869,17 +874,19 @@ bs_status bs_topk_pretiled(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, 
     if (!err) return BS_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     const uint32_t splits = tc_splits(nQ, nDB);
-    const size_t need = align256(ws_bytes(splits, nQ, k));
+    const size_t need = align256(ws_bytes(splits, nQ, k)) + align256(tc_tiled_bytes(nQ, N, kTcQueryRows));
+    if (!workspace || workspace_bytes < need) return BS_ERR_NO_MEMORY;
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return BS_ERR_INVALID_ARG;
+    uint8_t *w = reinterpret_cast<uint8_t *>(workspace);
     float *ws_key = nullptr;
     uint32_t *ws_idx = nullptr;
-    if (need > 0) {
-        if (!workspace || workspace_bytes < need) return BS_ERR_NO_MEMORY;
-        if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return BS_ERR_INVALID_ARG;
-        ws_key = reinterpret_cast<float *>(workspace);
+    if (splits > 1) {
+        ws_key = reinterpret_cast<float *>(w);
         ws_idx = reinterpret_cast<uint32_t *>(ws_key + (size_t)splits * nQ * k);
     }
+    void *tiled = w + align256(ws_bytes(splits, nQ, k));
     bs_status s1 = topk_tc(Q, pcQ, nQ, nullptr, pcDB, nDB, N, m, k, 0, 0, score, idx, ws_key,
-                           ws_idx, splits, DB_tiled, -1, 0, err, st);
+                           ws_idx, splits, tiled, DB_tiled, -1, 0, err, st);
     if (s1 != BS_OK || splits <= 1) return s1;
     return launch_merge(m, ws_key, ws_idx, nQ, k, splits, score, idx, st);
 }

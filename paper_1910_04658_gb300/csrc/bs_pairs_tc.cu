@@ -13,17 +13,76 @@
 namespace bs {
 namespace tc {
 
+// Re-layout of one block of a packed sketch matrix [n][W] (W = 4 nKc words)
+// into k-chunk tiles of R-row blocks (R = 128 for queries, 208 for a
+// database): 16-byte chunk kc of row r goes to dst[((r / R) * nKc + kc) * R +
+// r % R]; rows past n are zero.  One block moves R rows x 8 chunks through
+// shared memory so that both the reads (128-byte row pieces) and the writes
+// (R x 16-byte runs) are coalesced.
+__device__ __forceinline__ void tile_block(const uint4 *__restrict__ src, uint32_t n, uint32_t nKc,
+                                           uint4 *__restrict__ dst, uint32_t R, uint32_t blk, uint32_t kc0,
+                                           uint4 (&buf)[8][BN + 1]) {
+    const int t = threadIdx.x;
+    // read: 8 consecutive threads take 8 consecutive chunks of one row
+    for (uint32_t i = t; i < R * 8; i += 256) {
+        const uint32_t r = i >> 3, c = i & 7;
+        const uint32_t row = blk * R + r, kc = kc0 + c;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (row < n && kc < nKc) v = src[(size_t)row * nKc + kc];
+        buf[c][r] = v;
+    }
+    __syncthreads();
+    // write: R consecutive threads cover one run
+    for (uint32_t i = t; i < R * 8; i += 256) {
+        const uint32_t c = i / R, r = i % R;
+        const uint32_t kc = kc0 + c;
+        if (kc < nKc) dst[((size_t)blk * nKc + kc) * R + r] = buf[c][r];
+    }
+}
+
+__global__ void __launch_bounds__(256)
+    tile_kchunks_kernel(const uint4 *__restrict__ src, uint32_t n, uint32_t nKc, uint32_t R,
+                        uint4 *__restrict__ dst) {
+    __shared__ uint4 buf[8][BN + 1];
+    tile_block(src, n, nKc, dst, R, blockIdx.x, blockIdx.y * 8, buf);
+}
+
+// The re-layout of many matrices in one launch: matrix m owns the grid blocks
+// [blk_base[m], blk_base[m+1]), ceil(n/R) row blocks x ceil(nKc/8) chunk groups.
+struct TileJobs {
+    const uint4 *src[2 * MAXJ];
+    uint4 *dst[2 * MAXJ];
+    uint32_t n[2 * MAXJ], nKc[2 * MAXJ], R[2 * MAXJ];
+    uint32_t blk_base[2 * MAXJ + 1];
+    uint32_t count;
+};
+
+__global__ void __launch_bounds__(256) tile_batched_kernel(const __grid_constant__ TileJobs tj) {
+    __shared__ uint4 buf[8][BN + 1];
+    const uint32_t b = blockIdx.x;
+    uint32_t lo = 0, hi = tj.count - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (tj.blk_base[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const uint32_t local = b - tj.blk_base[lo];
+    const uint32_t nkg = (tj.nKc[lo] + 7) / 8;
+    tile_block(tj.src[lo], tj.n[lo], tj.nKc[lo], tj.dst[lo], tj.R[lo], local / nkg, (local % nkg) * 8, buf);
+}
+
 // 2-D tensor map over a row-major sketch matrix [rows][N/32] of uint32 words:
-// boxes of SW words (256 bits) x box_rows rows, no swizzle, out-of-range rows
-// and words read as zero.  The row stride N/8 bytes is a multiple of 16 for
-// N % 128 == 0, and the box's first word index is always a multiple of SW,
-// so every copy starts on a 16-byte boundary.
-static bool make_map(CUtensorMap *m, const uint32_t *ptr, uint32_t rows, uint32_t N, uint32_t box_rows) {
+// boxes of box_words words (one operand slot: 4 or 8) x box_rows rows, no
+// swizzle, out-of-range rows and words read as zero.  The row stride N/8
+// bytes is a multiple of 16 for N % 128 == 0, and every box starts at a word
+// index that is a multiple of box_words, i.e. on a 16-byte boundary.
+static bool make_map(CUtensorMap *m, const uint32_t *ptr, uint32_t rows, uint32_t N, uint32_t box_words,
+                     uint32_t box_rows) {
     EncodeTiledFn enc = encode_tiled();
     if (!enc || rows == 0) return false;
     cuuint64_t dims[2] = {N / 32, rows};
     cuuint64_t strides[1] = {(cuuint64_t)(N / 8)};
-    cuuint32_t box[2] = {(cuuint32_t)SW, box_rows};
+    cuuint32_t box[2] = {box_words, box_rows};
     cuuint32_t estr[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, (void *)ptr, dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -34,7 +93,7 @@ static bool make_map(CUtensorMap *m, const uint32_t *ptr, uint32_t rows, uint32_
 // Cost of one work unit in k-chunks.  The MMA / widening sweep over nKc
 // k-chunks and the epilogue of the previous tile run at the same time, so a
 // tile costs the larger of the two plus a fixed part; the epilogue of a
-// 128 x 240 tile was measured at about EPI_KC k-chunks of sweep (a tile of
+// 128 x 208 tile was measured at about EPI_KC k-chunks of sweep (a tile of
 // N = 256..1024 bits costs the same), the fixed part at FIX_KC.  Only the
 // batched form mixes costs; a single problem's units all cost the same.
 constexpr uint64_t EPI_KC = 24, FIX_KC = 8;
@@ -132,8 +191,8 @@ static void fill_job(Job &J, const uint32_t *pcQ, const uint32_t *pcDB, uint32_t
 
 static size_t tc_cfg_smem(int cfg, uint32_t k) {
     switch (cfg) {
-#define X(c, nop, ng, rd, sh) \
-    case c: return tc::smem_bytes<nop, ng, rd, sh>(k);
+#define X(c, nop, ng, sk, rd, sh) \
+    case c: return tc::smem_bytes<nop, ng, sk, rd, sh>(k);
         BS_TC_CONFIGS(X)
 #undef X
     }
@@ -172,14 +231,17 @@ uint32_t tc_splits(uint32_t nQ, uint32_t nDB) {
     return s.splits;
 }
 
-// The tensor-core kernel reads row-major sketches through tensor maps, so a
-// database kept "in the kernel's layout" is a plain copy of its rows.
-size_t tc_tiled_bytes(uint32_t n, uint32_t N) { return (size_t)n * (N / 8); }
+// Bytes of a k-chunk-tiled copy of n rows in R-row blocks (R = tc::BM for
+// queries, tc::BN for a database).
+size_t tc_tiled_bytes(uint32_t n, uint32_t N, uint32_t R) { return (size_t)((n + R - 1) / R) * R * (N / 8); }
 
-bs_status tile_sketches(const uint32_t *sk, uint32_t n, uint32_t N, void *tiled, cudaStream_t stream) {
-    return cudaMemcpyAsync(tiled, sk, tc_tiled_bytes(n, N), cudaMemcpyDeviceToDevice, stream) == cudaSuccess
-               ? BS_OK
-               : BS_ERR_CUDA;
+bs_status tile_sketches(const uint32_t *sk, uint32_t n, uint32_t N, uint32_t R, void *tiled, cudaStream_t stream) {
+    if (n == 0) return BS_OK;
+    const uint32_t nKc = N / 128;
+    dim3 g((n + R - 1) / R, (nKc + 7) / 8);
+    tc::tile_kchunks_kernel<<<g, 256, 0, stream>>>(reinterpret_cast<const uint4 *>(sk), n, nKc, R,
+                                                   reinterpret_cast<uint4 *>(tiled));
+    return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
 }
 
 template <int NJ>
@@ -196,15 +258,26 @@ static cudaError_t launch_measure(int measure, int cfg, const tc::Args<NJ> &p, u
 bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
                   const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
                   int exclude_self, uint32_t self_off, float *score, uint32_t *idx, float *ws_key,
-                  uint32_t *ws_idx, uint32_t splits, const void *db_copy, int cfg_req, uint32_t inject,
-                  unsigned int *err, cudaStream_t stream) {
+                  uint32_t *ws_idx, uint32_t splits, void *tiled, const void *db_tiled, int cfg_req,
+                  uint32_t inject, unsigned int *err, cudaStream_t stream) {
     const int cfg = cfg_req >= 0 ? cfg_req : tc_default_cfg(k);
     if (cfg < 0 || !tc_cfg_fits(cfg, k)) return BS_ERR_UNSUPPORTED;
-    if (db_copy) DB = reinterpret_cast<const uint32_t *>(db_copy);
+    // k-chunk-tiled copies: Q in 128-row blocks, DB in 208-row blocks (none for
+    // DB when the caller keeps it tiled)
+    uint4 *tQ = reinterpret_cast<uint4 *>(tiled);
+    if (tile_sketches(Q, nQ, N, tc::BM, tQ, stream) != BS_OK) return BS_ERR_CUDA;
+    const uint4 *tDB = reinterpret_cast<const uint4 *>(db_tiled);
+    if (!db_tiled) {
+        uint4 *t = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(tiled) +
+                                             ((tc_tiled_bytes(nQ, N, tc::BM) + 255) & ~(size_t)255));
+        if (tile_sketches(DB, nDB, N, tc::BN, t, stream) != BS_OK) return BS_ERR_CUDA;
+        tDB = t;
+    }
     static thread_local tc::Args<1> p;   // ~2 KB of launch arguments, rebuilt per call
     memset(&p, 0, sizeof(p));
     tc::Job &J = p.job[0];
     tc::fill_job(J, pcQ, pcDB, nQ, nDB, N);
+    J.tQ = tQ; J.tDB = tDB;
     J.exclude_self = exclude_self;
     J.self_off = self_off;
     J.score = score; J.idx = idx; J.ws_key = ws_key; J.ws_idx = ws_idx;
@@ -212,8 +285,6 @@ bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uin
     tc::single_schedule(nQ, nDB, s, &J.unit_base);
     if (s.units == 0) return BS_OK;
     if (s.splits != splits) return BS_ERR_INVALID_ARG;   // workspace planned for another shape
-    if (!tc::make_map(&p.maps[0], Q, nQ, N, tc::BM) || !tc::make_map(&p.maps[1], DB, nDB, N, tc::BN))
-        return BS_ERR_CUDA;
     memcpy(p.block_start, s.block_start, sizeof(uint64_t) * (s.grid + 1));
     p.njobs = 1;
     p.k = k; p.splits = splits;
@@ -237,7 +308,8 @@ bs_status estimate_tc(const uint32_t *A, const uint32_t *pcA, uint32_t nA, const
     tc::Schedule s;
     tc::single_schedule(nA, nB, s, &J.unit_base);
     if (s.units == 0) return BS_OK;
-    if (!tc::make_map(&p.maps[0], A, nA, N, tc::BM) || !tc::make_map(&p.maps[1], B, nB, N, tc::BN))
+    // the store kernel runs 256-bit operand slots (8-word boxes)
+    if (!tc::make_map(&p.maps[0], A, nA, N, 8, tc::BM) || !tc::make_map(&p.maps[1], B, nB, N, 8, tc::BN))
         return BS_ERR_CUDA;
     memcpy(p.block_start, s.block_start, sizeof(uint64_t) * (s.grid + 1));
     p.njobs = 1;
@@ -280,9 +352,11 @@ bs_status plan_batch(const bs_topk_job *jobs, uint32_t n, uint32_t k, BatchPlan 
     return BS_OK;
 }
 
-// workspace of job i: its split lists (none when no row block is split)
+// workspace of job i: [split lists][Q tiled in 128-row blocks][DB tiled in 208-row blocks]
 size_t job_ws(const bs_topk_job &jb, uint32_t k, uint32_t splits) {
-    return splits > 1 ? align256((size_t)splits * jb.nQ * k * 8) : 0;
+    size_t b = splits > 1 ? align256((size_t)splits * jb.nQ * k * 8) : 0;
+    b += align256(tc_tiled_bytes(jb.nQ, jb.N, tc::BM)) + align256(tc_tiled_bytes(jb.nDB, jb.N, tc::BN));
+    return b;
 }
 }  // namespace
 
@@ -325,11 +399,27 @@ bs_status topk_tc_batched(const bs_topk_job *jobs, uint32_t n, int measure, uint
     if (need > 0 && (reinterpret_cast<uintptr_t>(workspace) & 255u)) return BS_ERR_INVALID_ARG;
 
     static thread_local tc::Args<tc::MAXJ> p;
+    static thread_local tc::TileJobs tj;
     static thread_local MergeJobs mj;
     memset(&p, 0, sizeof(p));
+    memset(&tj, 0, sizeof(tj));
     memset(&mj, 0, sizeof(mj));
     const uint32_t splits = bp.s.splits;
     uint8_t *w = reinterpret_cast<uint8_t *>(workspace);
+    uint32_t blk = 0;
+    auto add_tile = [&](const uint32_t *src, uint32_t rows, uint32_t N, uint32_t R) {
+        uint4 *dst = reinterpret_cast<uint4 *>(w);
+        w += align256(tc_tiled_bytes(rows, N, R));
+        const uint32_t m = tj.count++;
+        tj.src[m] = reinterpret_cast<const uint4 *>(src);
+        tj.dst[m] = dst;
+        tj.n[m] = rows;
+        tj.nKc[m] = N / 128;
+        tj.R[m] = R;
+        tj.blk_base[m] = blk;
+        blk += ((rows + R - 1) / R) * ((N / 128 + 7) / 8);
+        return dst;
+    };
     for (uint32_t j = 0; j < bp.nj; ++j) {
         const bs_topk_job &jb = jobs[bp.src[j]];
         tc::Job &J = p.job[j];
@@ -340,10 +430,9 @@ bs_status topk_tc_batched(const bs_topk_job *jobs, uint32_t n, int measure, uint
             ws_idx = reinterpret_cast<uint32_t *>(ws_key + (size_t)splits * jb.nQ * k);
             w += align256((size_t)splits * jb.nQ * k * 8);
         }
-        if (!tc::make_map(&p.maps[2 * j], jb.Q, jb.nQ, jb.N, tc::BM) ||
-            !tc::make_map(&p.maps[2 * j + 1], jb.DB, jb.nDB, jb.N, tc::BN))
-            return BS_ERR_CUDA;
         tc::fill_job(J, jb.pcQ, jb.pcDB, jb.nQ, jb.nDB, jb.N);
+        J.tQ = add_tile(jb.Q, jb.nQ, jb.N, tc::BM);
+        J.tDB = add_tile(jb.DB, jb.nDB, jb.N, tc::BN);
         J.exclude_self = jb.exclude_self;
         J.self_off = 0;
         J.score = jb.score; J.idx = jb.idx; J.ws_key = ws_key; J.ws_idx = ws_idx;
@@ -354,6 +443,9 @@ bs_status topk_tc_batched(const bs_topk_job *jobs, uint32_t n, int measure, uint
         mj.row_base[j + 1] = mj.row_base[j] + jb.nQ;
     }
     mj.njobs = bp.nj;
+    tj.blk_base[tj.count] = blk;
+    tc::tile_batched_kernel<<<blk, 256, 0, stream>>>(tj);
+    if (cudaGetLastError() != cudaSuccess) return BS_ERR_CUDA;
     memcpy(p.block_start, bp.s.block_start, sizeof(uint64_t) * (bp.s.grid + 1));
     p.njobs = bp.nj;
     p.k = k;

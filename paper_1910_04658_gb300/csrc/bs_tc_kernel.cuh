@@ -17,24 +17,31 @@
 //
 // Block (one per SM, persistent): a job table (one job for a single call,
 // up to BS_TOPK_BATCH_MAX for the batched form) is cut into work units
-// (job, 128-row query block, 240-row database tile), numbered job by job and
+// (job, 128-row query block, 208-row database tile), numbered job by job and
 // row block by row block; block c takes the contiguous range
 // [block_start[c], block_start[c+1]) that the host balanced by cost.  A row
 // block cut between blocks yields one partial list per block ("part"), merged
-// afterwards.  Every operand slot covers 256 sketch bits (two 128-bit
-// k-chunks) of a tile's 128 query and 240 database rows.
-//   warp 0     TMEM owner (512 columns: two 240-column accumulators and the
-//              unit scale factors) and single-thread MMA issuer:
-//              tcgen05.mma.kind::mxf4.block_scale (M=128, N=240, K=64), four
-//              per operand slot
-//   warp 1     TMA producer (one thread): for every slot, two 2-D tensor-map
-//              loads of the packed bits straight from the row-major sketch
-//              matrices (a 32-byte x 128-row box of Q, a 32-byte x 240-row box
-//              of DB; rows and words past the matrix end arrive as zeros) into
-//              a RD-deep ring of raw slots, completion on mbarriers
-//   warps 2-5  widening: query row e and database rows e and e + 128 of a
-//              raw slot, read from shared memory and written as FP4 into the
-//              128-byte-swizzled K-major layout the MMA descriptors point at
+// afterwards.  An operand slot covers SK * 2 sketch bits (128 or 256) of a
+// tile's 128 query and 208 database rows.  The query operand (MMA A) is fed
+// from TMEM and the database operand (MMA B) from shared memory, so shared
+// memory carries the widened bits of the 208 database rows only: per 256-bit
+// slot 26 KB written by the widening warps and 26 KB read by the MMA, about
+// the 416 cycles the MMAs themselves take.
+//   warp 0     TMEM owner (512 columns: two 208-column accumulators, the
+//              query operand slots and the unit scale factors) and
+//              single-thread MMA issuer: tcgen05.mma.kind::mxf4.block_scale
+//              with A in TMEM (M=128, N=208, K=64), 2 or 4 per slot
+//   warp 1     TMA producer (one thread): for every slot, two asynchronous
+//              copies of the packed bits into a RD-deep ring of raw slots,
+//              completion on mbarriers.  Top-k reads k-chunk-tiled copies (Q
+//              in 128-row, DB in 208-row blocks), so each operand of a slot
+//              is one contiguous run (cp.async.bulk); the full-matrix store
+//              reads the row-major sketches through 2-D tensor maps (a 128-row
+//              and a 208-row box; rows and words past the end arrive as
+//              zeros), which costs one request per row
+//   warps 2-5  widening, one query row per thread (the row of its TMEM lane,
+//              written with tcgen05.st) and database rows e and e + 128 (into
+//              the SK-byte-swizzled K-major layout the B descriptors point at)
 //   warps 6+   epilogue, one or two groups of 4 warps, one query row per
 //              thread, 32 TMEM columns per tcgen05.ld.  Top-k: a closed-form
 //              bound on the union count admits only pairs that can beat the
@@ -54,13 +61,13 @@
 namespace bs {
 namespace tc {
 
-constexpr int BM = 128;                    // query rows per block (UMMA M, TMEM lanes)
-constexpr int BN = 240;                    // database rows per tile (UMMA N)
+constexpr int BM = kTcQueryRows;           // query rows per block (UMMA M, TMEM lanes)
+constexpr int BN = kTcTileRows;            // database rows per tile (UMMA N)
 constexpr int BNP = 256;                   // per-column arrays padded to whole 32-column chunks
 constexpr int KCW = 4;                     // packed words per k-chunk (128 bits)
-constexpr int SW = 8;                      // packed words per operand slot (256 bits)
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t SF_COL = 2 * BN;        // 480: unit scale factors (A at +0, B at +16)
+constexpr uint32_t A_COL = 2 * BN;         // 416: query operand slots (SK / 4 columns each)
+constexpr uint32_t SF_COL = 480;           // unit scale factors (A at +0, B at +16)
 constexpr int MAXG = 192;                  // most persistent blocks per launch
 constexpr int MAXJ = BS_TOPK_BATCH_MAX;    // most jobs per batched launch
 constexpr int MODE_TOPK = 0, MODE_STORE = 1;
@@ -69,20 +76,36 @@ enum { INJECT_NONE = 0, INJECT_STALL = 1 };
 // threads per block with NG epilogue groups
 __host__ __device__ constexpr int threads_for(int NG) { return 32 * (6 + 4 * NG); }
 
-// Operand slot: 256 bits of K per row as FP4 = 128 bytes, 128-byte swizzle.
-constexpr int OP_A = BM * 128;             // query operand bytes
-constexpr int OP_B = BN * 128;             // database operand bytes
-constexpr int OP_BYTES = OP_A + OP_B;      // per slot
-constexpr int MMAS = 4;                    // K = 64 (32 bytes) per MMA
-// Raw slot: the same 256 bits packed, [row][32 bytes], as the TMA box lands.
-constexpr int RAW_A = BM * 32;
-constexpr int RAW_B = BN * 32;
-constexpr int RAW_SLOT = 12288;            // RAW_A + RAW_B rounded up to 1 KB
-static_assert(OP_BYTES % 1024 == 0 && OP_A % 1024 == 0, "swizzle atom alignment");
-static_assert(RAW_A + RAW_B <= RAW_SLOT && RAW_A % 1024 == 0, "raw slot alignment");
+// Operand slot geometry for SK bytes of K per row: one FP4 byte holds two
+// sketch bits, so a slot covers 2 SK bits -- SK = 128: 256 bits (two 128-bit
+// k-chunks, 128-byte swizzle, 4 MMAs), SK = 64: 128 bits (64-byte swizzle, 2
+// MMAs).  Shared memory holds the database operand (B); the query operand (A)
+// sits in TMEM, SK / 4 columns per slot.  A raw slot holds the same bits
+// packed as they arrive: tiled, [k-chunk][rows] x 16 bytes; through the tensor
+// maps, [rows][SK / 4 bytes].
+template <int SK>
+struct Geo {
+    static_assert(SK == 128 || SK == 64, "slot width");
+    static constexpr int BYTES = BN * SK;                   // database operand bytes per slot
+    static constexpr int TCOLS = SK / 4;                    // TMEM columns of a query operand slot
+    static constexpr int MMAS = SK / 32;                    // K = 64 (32 bytes) per MMA
+    static constexpr int WPS = SK / 16;                     // packed words per slot and row
+    static constexpr int KPS = WPS / KCW;                   // 128-bit k-chunks per slot (1, 2)
+    static constexpr int SHIFT = SK == 128 ? 0 : 1;         // swizzle: chunk ^ ((row % 8) >> SHIFT)
+    static constexpr uint64_t LAYOUT = SK == 128 ? 2 : 4;   // descriptor swizzle code
+    static constexpr int RAW_ROW = WPS * 4;                 // packed bytes per row
+    static constexpr int RAW_A = BM * RAW_ROW;
+    static constexpr int RAW_B = BN * RAW_ROW;
+    static constexpr int RAW_SLOT = (RAW_A + RAW_B + 1023) / 1024 * 1024;
+    static_assert(BYTES % (8 * SK) == 0, "swizzle atom alignment");
+    static_assert(RAW_A % 1024 == 0, "raw slot alignment");
+};
 
-// operand slots per tile (k-chunks paired; an odd count pads with zeros)
-__host__ __device__ __forceinline__ uint32_t slots_per_tile(uint32_t nKc) { return (nKc + 1) / 2; }
+// operand slots per tile (SK = 128 pairs the k-chunks; an odd count pads with zeros)
+template <int SK>
+__host__ __device__ __forceinline__ uint32_t slots_per_tile(uint32_t nKc) {
+    return SK == 128 ? (nKc + 1) / 2 : nKc;
+}
 
 constexpr int CB = 8;                      // admitted pairs a row buffers within a tile
 constexpr uint32_t NO_IDX = 0xFFFFFFFFu;
@@ -93,24 +116,30 @@ constexpr uint32_t NO_IDX = 0xFFFFFFFFu;
 // letting through almost none that fall a full count short.
 constexpr float FILTER_SLACK = 0.99987793f;
 
-// Shared-memory layout for NOP operand slots, RD raw slots and NG epilogue
-// groups (offsets from the 1024-aligned base); the heaps follow.
-template <int NOP, int NG, int RD>
+// Shared-memory layout for NOP operand slots and RD raw slots of SK bytes
+// per row and NG epilogue groups (offsets from the 1024-aligned base); the
+// heaps follow.
+template <int NOP, int NG, int SK, int RD>
 struct Smem {
+    static_assert(NOP * Geo<SK>::TCOLS <= (int)(SF_COL - A_COL), "query operand slots exceed their TMEM columns");
     static constexpr int op = 0;
-    static constexpr int raw = op + NOP * OP_BYTES;
-    static constexpr int col = raw + RD * RAW_SLOT;             // [2 tiles][3][BNP] floats
+    static constexpr int raw = op + NOP * Geo<SK>::BYTES;
+    static constexpr int col = raw + RD * Geo<SK>::RAW_SLOT;    // [2 tiles][3][BNP] floats
     static constexpr int bars = col + 2 * 3 * BNP * 4;
-    static constexpr int thr = bars + 256;                      // [NG][BM] key, idx, size
+    static constexpr int thr = bars + 512;                      // [NG][BM] key, idx, size
     static constexpr int lock = thr + NG * BM * 12;             // [BM] shared-heap row locks
     static constexpr int cbuf = lock + BM * 4;                  // [NG][CB][BM] admitted pairs
     static constexpr int heap = cbuf + NG * CB * BM * 4;
-    static_assert((2 * NOP + 2 * RD + 5) * 8 + 8 <= 256, "barrier area");
+    static_assert((2 * NOP + 2 * RD + 5) * 8 + 8 <= 512, "barrier area");
 };
 
-// One problem of the job table: nQ query rows against nDB database rows.  The
-// sketches themselves are reached through the tensor maps of Args.
+// One problem of the job table: nQ query rows against nDB database rows.
+// Top-k reads k-chunk-tiled copies of the sketches -- Q in 128-row blocks,
+// DB in 208-row blocks, [block][k-chunk][rows of the block] x 16 bytes -- so
+// a slot's bits of a query block or a database tile are one contiguous run;
+// the store reads the row-major sketches through the tensor maps of Args.
 struct Job {
+    const uint4 *tQ, *tDB;      // top-k: tiled copies
     const uint32_t *pcQ, *pcDB;
     float *score;               // top-k, splits == 1: [nQ][k]
     uint32_t *idx;
@@ -129,7 +158,7 @@ struct Job {
 
 template <int NJ>
 struct Args {
-    CUtensorMap maps[2 * NJ];         // job j: Q at 2j (box 8 words x 128 rows), DB at 2j + 1 (x 240)
+    CUtensorMap maps[2];              // store: A (box SK/16 words x 128 rows), B (x 208 rows)
     Job job[NJ];
     uint64_t block_start[MAXG + 1];   // block c: units [block_start[c], block_start[c+1])
     uint32_t njobs;
@@ -152,14 +181,15 @@ __device__ __forceinline__ void tmem_relinquish() {
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
-// D (+)= A * B with per-32-element block scales read from TMEM
-__device__ __forceinline__ void mma_fp4(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+// D (+)= A * B, A in TMEM at a_tmem, B in shared memory, with per-32-element
+// block scales read from TMEM
+__device__ __forceinline__ void mma_fp4(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
                                         uint32_t sfa, uint32_t sfb, uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%5], [%6], p;\n\t}\n" ::"r"(
+        "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], [%1], %2, %3, [%5], [%6], p;\n\t}\n" ::"r"(
             d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "r"(sfa), "r"(sfb)
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate), "r"(sfa), "r"(sfb)
         : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
@@ -208,33 +238,35 @@ __device__ __forceinline__ void tmem_fill32(uint32_t taddr, uint32_t v) {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (SBO), leading offset unused for this layout (1).
+// Shared-memory matrix descriptor: K-major, SK-byte swizzle, 8-row groups
+// 8 * SK bytes apart (SBO), leading offset unused for this layout (1).
+template <int SK>
 __device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
     d |= (uint64_t)1 << 16;                     // LBO (ignored for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;           // SBO
+    d |= (uint64_t)((8 * SK) >> 4) << 32;       // SBO
     d |= (uint64_t)1 << 46;                     // descriptor version for tcgen05
-    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+    d |= Geo<SK>::LAYOUT << 61;                 // swizzle mode
     return d;
 }
 
 // Instruction descriptor of the block-scaled MMA: A = B = E2M1 (code 1 of the
-// mxf4 kind), both K-major, scale factors UE8M0 (bit 23), N = 240, M = 128,
+// mxf4 kind), both K-major, scale factors UE8M0 (bit 23), N = 208, M = 128,
 // scale-factor selectors 0, dense K = 64.
 constexpr uint32_t IDESC = (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | (1u << 23) |
                            ((uint32_t)(BM >> 4) << 24);
 constexpr uint32_t UNIT_SCALES = 0x7F7F7F7Fu;   // four UE8M0 2^0
 
-// Widen the 8 packed words x[] of one row (256 bits) into FP4 and store them
-// into the 128-byte-swizzled K-major tile: row r at (r / 8) * 1024 + (r % 8) *
-// 128, the 16-byte chunk of word c at position c ^ (r % 8).
-__device__ __forceinline__ void widen_store(uint8_t *op_tile, int r, const uint32_t (&x)[SW]) {
-    uint8_t *row = op_tile + (r >> 3) * 1024 + (r & 7) * 128;
-    const int sw = r & 7;
+// Widen the WPS packed words x[] of one row into FP4 and store them into the
+// SK-byte-swizzled K-major tile: row r at (r / 8) * 8 SK + (r % 8) * SK, the
+// 16-byte chunk of word c at position c ^ ((r % 8) >> SHIFT).
+template <int SK>
+__device__ __forceinline__ void widen_store(uint8_t *op_tile, int r, const uint32_t (&x)[Geo<SK>::WPS]) {
+    uint8_t *row = op_tile + (r >> 3) * (8 * SK) + (r & 7) * SK;
+    const int sw = (r & 7) >> Geo<SK>::SHIFT;
 #pragma unroll
-    for (int c = 0; c < SW; ++c) {
+    for (int c = 0; c < Geo<SK>::WPS; ++c) {
         const uint32_t v = x[c];
         uint4 o;
         o.x = (v << 1) & 0x22222222u;
@@ -245,12 +277,53 @@ __device__ __forceinline__ void widen_store(uint8_t *op_tile, int r, const uint3
     }
 }
 
-// The 8 packed words of raw row r (rows are 32 bytes apart).
-__device__ __forceinline__ void raw_row(const uint8_t *raw, int r, uint32_t (&x)[SW]) {
-    const uint4 a = *reinterpret_cast<const uint4 *>(raw + r * 32);
-    const uint4 b = *reinterpret_cast<const uint4 *>(raw + r * 32 + 16);
-    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
-    x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+// Widen the WPS packed words x[] of this thread's query row into FP4 and
+// write them to the row's TMEM lane: widened word 4c + t (t = 0..3 as in
+// widen_store) at column taddr + 4c + t, the order the shared-memory operand
+// has once unswizzled, so both operands see the same K permutation.
+template <int SK>
+__device__ __forceinline__ void widen_tmem(uint32_t taddr, const uint32_t (&x)[Geo<SK>::WPS]) {
+    uint32_t w[4 * Geo<SK>::WPS];
+#pragma unroll
+    for (int c = 0; c < Geo<SK>::WPS; ++c) {
+        const uint32_t v = x[c];
+        w[4 * c] = (v << 1) & 0x22222222u;
+        w[4 * c + 1] = v & 0x22222222u;
+        w[4 * c + 2] = (v >> 1) & 0x22222222u;
+        w[4 * c + 3] = (v >> 2) & 0x22222222u;
+    }
+    if constexpr (SK == 128) {
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+            "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+            "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7]), "r"(w[8]),
+            "r"(w[9]), "r"(w[10]), "r"(w[11]), "r"(w[12]), "r"(w[13]), "r"(w[14]), "r"(w[15]), "r"(w[16]),
+            "r"(w[17]), "r"(w[18]), "r"(w[19]), "r"(w[20]), "r"(w[21]), "r"(w[22]), "r"(w[23]), "r"(w[24]),
+            "r"(w[25]), "r"(w[26]), "r"(w[27]), "r"(w[28]), "r"(w[29]), "r"(w[30]), "r"(w[31])
+            : "memory");
+    } else {
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+                taddr),
+            "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7]), "r"(w[8]),
+            "r"(w[9]), "r"(w[10]), "r"(w[11]), "r"(w[12]), "r"(w[13]), "r"(w[14]), "r"(w[15])
+            : "memory");
+    }
+}
+
+// The WPS packed words of raw row r: k-chunk h of the row at raw + h * plane
+// + r * stride (tiled raw slots: plane = rows x 16, stride 16; row-major raw
+// slots: plane 16, stride RAW_ROW); k-chunks from `valid` on read as zero
+// (the padding of an odd k-chunk count).
+template <int SK>
+__device__ __forceinline__ void raw_row(const uint8_t *raw, int plane, int stride, int r, int valid,
+                                        uint32_t (&x)[Geo<SK>::WPS]) {
+#pragma unroll
+    for (int h = 0; h < Geo<SK>::KPS; ++h) {
+        uint4 a = make_uint4(0, 0, 0, 0);
+        if (h < valid) a = *reinterpret_cast<const uint4 *>(raw + h * plane + r * stride);
+        x[4 * h] = a.x; x[4 * h + 1] = a.y; x[4 * h + 2] = a.z; x[4 * h + 3] = a.w;
+    }
 }
 
 // ---- per-row heap of the k best (root = worst), interleaved across rows ------
@@ -486,10 +559,11 @@ __device__ __forceinline__ uint32_t block_of(const Args<NJ> &p, uint64_t x, uint
     return lo;
 }
 
-template <int MODE, int M, int NOP, int NG, int RD, bool SHARED, int NJ>
+template <int MODE, int M, int NOP, int NG, int SK, int RD, bool SHARED, int NJ>
 __global__ void __launch_bounds__(threads_for(NG), 1)
     pair_tc_kernel(const __grid_constant__ Args<NJ> p) {
-    using Smem = tc::Smem<NOP, NG, RD>;
+    using Smem = tc::Smem<NOP, NG, SK, RD>;
+    using G = Geo<SK>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -577,7 +651,7 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
             cur.start(jobs, njobs, u_lo);
             const uint32_t sfa = tmem + SF_COL, sfb = tmem + SF_COL + 16;
             for (uint32_t t = 0; t < n_my_tiles; ++t) {
-                const uint32_t nsl = slots_per_tile(jobs[cur.j].nKc);
+                const uint32_t nsl = slots_per_tile<SK>(jobs[cur.j].nKc);
                 const uint32_t ab = t & 1;
                 if (t >= 2) wait(&acc_empty[ab], ((t >> 1) - 1) & 1);
                 tc_fence_after();
@@ -587,11 +661,11 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                     wait(&op_full[o], (sl / NOP) & 1);
                     tc_fence_after();
                     if (!*abort_flag) {
-                        const uint32_t a_addr = smem_u32(op + o * OP_BYTES);
-                        const uint32_t b_addr = a_addr + OP_A;
+                        const uint32_t a_tmem = tmem + A_COL + o * G::TCOLS;
+                        const uint32_t b_addr = smem_u32(op + o * G::BYTES);
 #pragma unroll
-                        for (int kk = 0; kk < MMAS; ++kk)
-                            mma_fp4(d_tmem, sw_desc(a_addr + kk * 32), sw_desc(b_addr + kk * 32), IDESC, sfa, sfb,
+                        for (int kk = 0; kk < G::MMAS; ++kk)
+                            mma_fp4(d_tmem, a_tmem + 8 * kk, sw_desc<SK>(b_addr + kk * 32), IDESC, sfa, sfb,
                                     (c | (uint32_t)kk) != 0);
                     }
                     mma_commit(&op_empty[o]);
@@ -612,18 +686,27 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
             Cursor cur;
             cur.start(jobs, njobs, u_lo);
             for (uint32_t t = 0; t < n_my_tiles && !*abort_flag; ++t) {
-                const uint32_t nsl = slots_per_tile(jobs[cur.j].nKc);
-                const CUtensorMap *mq = &p.maps[2 * cur.j];
-                const CUtensorMap *md = mq + 1;
-                const int yq = (int)(cur.rb * BM), yd = (int)(cur.tile * BN);
+                const Job &J = jobs[cur.j];
+                const uint32_t nKc = J.nKc;
+                const uint32_t nsl = slots_per_tile<SK>(nKc);
                 for (uint32_t c = 0; c < nsl; ++c) {
                     const uint32_t o = rs % RD;
                     if (rs >= RD) wait(&raw_empty[o], ((rs / RD) - 1) & 1);
                     if (*abort_flag) break;
-                    uint8_t *dst = raw + o * RAW_SLOT;
-                    mbar_arrive_expect_tx(&raw_full[o], RAW_A + RAW_B);
-                    tma_load_2d(dst, mq, &raw_full[o], (int)(SW * c), yq);
-                    tma_load_2d(dst + RAW_A, md, &raw_full[o], (int)(SW * c), yd);
+                    uint8_t *dst = raw + o * G::RAW_SLOT;
+                    if (MODE == MODE_STORE) {   // strided rows through the tensor maps
+                        mbar_arrive_expect_tx(&raw_full[o], G::RAW_A + G::RAW_B);
+                        tma_load_2d(dst, &p.maps[0], &raw_full[o], (int)(G::WPS * c), (int)(cur.rb * BM));
+                        tma_load_2d(dst + G::RAW_A, &p.maps[1], &raw_full[o], (int)(G::WPS * c),
+                                    (int)(cur.tile * BN));
+                    } else {                    // one contiguous run per operand
+                        const uint32_t kc0 = c * G::KPS;
+                        const uint32_t np = nKc - kc0 < (uint32_t)G::KPS ? nKc - kc0 : (uint32_t)G::KPS;
+                        mbar_arrive_expect_tx(&raw_full[o], np * (BM + BN) * 16);
+                        bulk_load(dst, J.tQ + ((size_t)cur.rb * nKc + kc0) * BM, np * BM * 16, &raw_full[o]);
+                        bulk_load(dst + G::RAW_A, J.tDB + ((size_t)cur.tile * nKc + kc0) * BN, np * BN * 16,
+                                  &raw_full[o]);
+                    }
                     ++rs;
                 }
                 cur.step(jobs);
@@ -634,31 +717,42 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
         }
     } else if (warp < 6) {
         // ------------------------------ widening ------------------------------
-        // thread e owns query row e and database rows e and e + 128 of a slot
-        const int e = tid - 64;   // 0..127
+        // thread e owns query row e -- the row of its warp's TMEM lane quarter --
+        // and database rows e and e + 128 of a slot
+        const int e = (warp & 3) * 32 + lane;   // 0..127
         const bool two_b = e + 128 < BN;
+        const uint32_t a_lane = tmem + ((uint32_t)((warp & 3) * 32) << 16) + A_COL;
         uint32_t sl = 0;
         Cursor cur;
         cur.start(jobs, njobs, u_lo);
         for (uint32_t t = 0; t < n_my_tiles; ++t) {
-            const uint32_t nsl = slots_per_tile(jobs[cur.j].nKc);
+            const uint32_t nKc = jobs[cur.j].nKc;
+            const uint32_t nsl = slots_per_tile<SK>(nKc);
             for (uint32_t c = 0; c < nsl; ++c, ++sl) {
                 const uint32_t ro = sl % RD, o = sl % NOP;
                 wait(&raw_full[ro], (sl / RD) & 1);
-                const uint8_t *src = raw + ro * RAW_SLOT;
-                uint32_t xa[SW], xb0[SW], xb1[SW];
-                raw_row(src, e, xa);
-                raw_row(src + RAW_A, e, xb0);
-                if (two_b) raw_row(src + RAW_A, e + 128, xb1);
+                const uint8_t *src = raw + ro * G::RAW_SLOT;
+                uint32_t xa[G::WPS], xb0[G::WPS], xb1[G::WPS];
+                if (MODE == MODE_STORE) {
+                    raw_row<SK>(src, 16, G::RAW_ROW, e, G::KPS, xa);
+                    raw_row<SK>(src + G::RAW_A, 16, G::RAW_ROW, e, G::KPS, xb0);
+                    if (two_b) raw_row<SK>(src + G::RAW_A, 16, G::RAW_ROW, e + 128, G::KPS, xb1);
+                } else {
+                    const int valid = (int)(nKc - c * G::KPS);
+                    raw_row<SK>(src, BM * 16, 16, e, valid, xa);
+                    raw_row<SK>(src + G::RAW_A, BN * 16, 16, e, valid, xb0);
+                    if (two_b) raw_row<SK>(src + G::RAW_A, BN * 16, 16, e + 128, valid, xb1);
+                }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&raw_empty[ro]);   // the raw slot may be refilled
                 if (sl >= (uint32_t)NOP) wait(&op_empty[o], ((sl / NOP) - 1) & 1);
-                uint8_t *oA = op + o * OP_BYTES;
-                uint8_t *oB = oA + OP_A;
-                widen_store(oA, e, xa);
-                widen_store(oB, e, xb0);
-                if (two_b) widen_store(oB, e + 128, xb1);
+                uint8_t *oB = op + o * G::BYTES;
+                widen_tmem<SK>(a_lane + o * G::TCOLS, xa);
+                widen_store<SK>(oB, e, xb0);
+                if (two_b) widen_store<SK>(oB, e + 128, xb1);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 fence_async_smem();
+                tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&op_full[o]);
             }
@@ -966,29 +1060,29 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
 }
 
 // ---------------------------------------------------------------------------
-// Block configurations (operand slots, epilogue groups, raw-slot ring depth,
-// one heap per row shared by the groups); the index is the c of
-// BS_VARIANT_TC_CFG(c).  The default is the first that fits k in this order.
+// Block configurations (operand slots, epilogue groups, slot K bytes SK,
+// raw-slot ring depth, one heap per row shared by the groups); the index is
+// the c of BS_VARIANT_TC_CFG(c).  The default is the first that fits k in this order.
 // The last, a single operand slot, keeps k up to BS_TOPK_K_MAX on the tensor
 // cores at the cost of overlap between widening and MMA.
 // ---------------------------------------------------------------------------
-#define BS_TC_CONFIGS(X)       \
-    X(0, 3, 2, 4, false)       \
-    X(1, 2, 2, 4, false)       \
-    X(2, 3, 2, 4, true)        \
-    X(3, 2, 2, 4, true)        \
-    X(4, 2, 1, 4, false)       \
-    X(5, 2, 2, 6, false)       \
-    X(6, 2, 2, 6, true)        \
-    X(7, 2, 2, 2, false)       \
-    X(8, 2, 1, 2, false)       \
-    X(9, 1, 1, 2, false)
+#define BS_TC_CONFIGS(X)          \
+    X(0, 2, 2, 128, 4, false)     \
+    X(1, 2, 2, 128, 4, true)      \
+    X(2, 4, 2, 64, 8, false)      \
+    X(3, 4, 2, 64, 8, true)       \
+    X(4, 2, 1, 128, 4, false)     \
+    X(5, 2, 2, 128, 6, false)     \
+    X(6, 2, 2, 128, 2, false)     \
+    X(7, 2, 2, 128, 6, true)      \
+    X(8, 2, 1, 128, 2, false)     \
+    X(9, 1, 1, 128, 2, false)
 constexpr int kTcConfigs = 10;
 constexpr size_t kSmemLimit = 232448;   // 227 KB per block
 
-template <int NOP, int NG, int RD, bool SH>
+template <int NOP, int NG, int SK, int RD, bool SH>
 __host__ __device__ constexpr size_t smem_bytes(uint32_t k) {
-    return 1024 + Smem<NOP, NG, RD>::heap + (size_t)(SH ? 1 : NG) * k * BM * 8;
+    return 1024 + Smem<NOP, NG, SK, RD>::heap + (size_t)(SH ? 1 : NG) * k * BM * 8;
 }
 
 // Launch of one configuration for one measure (defined in the per-measure

@@ -281,8 +281,8 @@ class SketchDB:
         self.sketch = torch.empty((n, N // 32), dtype=torch.int32, device=dev)
         self.pc = torch.empty((n,), dtype=torch.int32, device=dev)
         B.bs_sketch(row_ptr, col, n, col.numel(), d, N, seed, self.sketch, self.pc, stream)
-        # the tensor-core search reads the row-major sketches as they are
-        self.tiled = self.sketch
+        self.tiled = torch.empty((B.bs_tiled_bytes(n, N),), dtype=torch.uint8, device=dev)
+        B.bs_tile_sketches(self.sketch, n, N, self.tiled, stream)
 
     def save(self, path: str) -> None:
         """Write the sketches with their (N, seed) (checkpoint.py format)."""
@@ -292,14 +292,16 @@ class SketchDB:
     @classmethod
     def load(cls, path: str, device: str = "cuda", expect_N: int = None, expect_seed: int = None,
              stream=None) -> "SketchDB":
-        """A database from a checkpoint, ready for the tensor-core search;
+        """A database from a checkpoint, re-tiled for the tensor-core search;
         refuses one sketched with another (N, seed) than expected."""
-        from . import checkpoint
+        import torch
+        from . import binding as B, checkpoint
         sk, pc, meta = checkpoint.load_sketches(path, device, expect_N, expect_seed)
         db = cls.__new__(cls)
         db.n, db.d, db.N, db.seed = meta.n, meta.d, meta.N, meta.seed
         db.sketch, db.pc = sk, pc
-        db.tiled = db.sketch
+        db.tiled = torch.empty((B.bs_tiled_bytes(db.n, db.N),), dtype=torch.uint8, device=device)
+        B.bs_tile_sketches(db.sketch, db.n, db.N, db.tiled, stream)
         return db
 
 
