@@ -86,8 +86,6 @@ def lib():
             L.bso_topk.argtypes = [_P(u32), u32, _P(u32), u32, u32, i32, u32, i32,
                                    _P(f64), _P(u32), _P(u32)]
             L.bso_exact_pairs.argtypes = [_P(u64), _P(u32), _P(u32), _P(u32), u64, _P(f64)]
-            L.bso_theorem1_N.argtypes = [f64, f64]
-            L.bso_theorem1_N.restype = f64
             L.bso_num_threads.restype = i32
             _lib = L
     return _lib
@@ -252,6 +250,3 @@ def onehot(labels, cardinalities):
         row_ptr[i + 1] = len(cols)
     return row_ptr, np.array(cols, np.uint32), starts[-1]
 
-
-def theorem1_N(psi: float, rho: float) -> float:
-    return float(lib().bso_theorem1_N(psi, rho))

@@ -402,12 +402,6 @@ void bso_exact_pairs(const uint64_t *row_ptr, const uint32_t *col,
     }
 }
 
-/* Theorem 1: N = psi * sqrt((psi/2) ln(2/rho)). */
-double bso_theorem1_N(double psi, double rho)
-{
-    return psi * sqrt(psi / 2.0 * log(2.0 / rho));
-}
-
 int bso_num_threads(void)
 {
 #ifdef _OPENMP

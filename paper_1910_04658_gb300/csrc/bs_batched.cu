@@ -90,6 +90,7 @@ using namespace bs;
 
 extern "C" bs_status bs_sketch_batched(const bs_sketch_job *jobs, uint32_t n_jobs, uint32_t max_N,
                                        bs_stream_t stream) {
+    BS_NVTX_RANGE();
     if (n_jobs == 0) return BS_OK;
     if (!jobs || max_N < 32 || max_N > BS_N_MAX || (max_N % 32) != 0) return BS_ERR_INVALID_ARG;
     unsigned int *err = error_word();

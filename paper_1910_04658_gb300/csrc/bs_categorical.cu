@@ -37,6 +37,7 @@ using namespace bs;
 
 extern "C" bs_status bs_onehot_csr(const uint32_t *labels, uint32_t n, uint32_t F, const uint32_t *offsets,
                                    uint64_t *row_ptr, uint32_t *col, bs_stream_t stream) {
+    BS_NVTX_RANGE();
     if (F == 0) return BS_ERR_INVALID_ARG;
     if (!row_ptr || !offsets) return BS_ERR_INVALID_ARG;
     if (n > 0 && (!labels || !col)) return BS_ERR_INVALID_ARG;

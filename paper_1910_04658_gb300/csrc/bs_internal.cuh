@@ -4,11 +4,23 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "binsketch.h"
 
 namespace bs {
+
+// NVTX range around one C-ABI call, named after the call, so profiler
+// timelines attribute each kernel to the entry point that launched it (a
+// no-op unless a profiling tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define BS_NVTX_RANGE() ::bs::NvtxRange bs_nvtx_range_(__func__)
 
 // ---------------------------------------------------------------------------
 // Host-side shared state

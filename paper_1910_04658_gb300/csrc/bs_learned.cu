@@ -572,6 +572,7 @@ extern "C" {
 bs_status bs_dense_pairs(uint32_t n_pairs, uint32_t N, uint32_t d, uint32_t size_lo, uint32_t size_hi,
                          uint64_t pair_seed, uint64_t hash_seed, uint32_t *counts, uint32_t *sizes,
                          uint32_t *cols, uint32_t max_cols, bs_stream_t stream) {
+    BS_NVTX_RANGE();
     if (!valid_N_l(N) || size_lo > size_hi || d == 0 || d > (1u << 30)) return BS_ERR_INVALID_ARG;
     if (2ull * size_hi > d) return BS_ERR_INVALID_ARG;   // a and b together must fit in [0, d)
     if (n_pairs == 0) return BS_OK;
@@ -588,6 +589,7 @@ bs_status bs_dense_pairs(uint32_t n_pairs, uint32_t N, uint32_t d, uint32_t size
 
 bs_status bs_estimate_counts(const uint32_t *counts, uint32_t n, uint32_t N, float *out,
                              bs_stream_t stream) {
+    BS_NVTX_RANGE();
     if (!valid_N_l(N)) return BS_ERR_INVALID_ARG;
     if (n == 0) return BS_OK;
     if (!counts || !out) return BS_ERR_INVALID_ARG;
@@ -598,6 +600,7 @@ bs_status bs_estimate_counts(const uint32_t *counts, uint32_t n, uint32_t N, flo
 
 bs_status bs_mlp_prepare(const uint32_t *counts, const uint32_t *sizes, uint32_t n, uint32_t N, float *x,
                          float *t, bs_stream_t stream) {
+    BS_NVTX_RANGE();
     if (!valid_N_l(N)) return BS_ERR_INVALID_ARG;
     if (n == 0) return BS_OK;
     if (!counts || !x || (sizes && !t)) return BS_ERR_INVALID_ARG;
@@ -608,6 +611,7 @@ bs_status bs_mlp_prepare(const uint32_t *counts, const uint32_t *sizes, uint32_t
 bs_status bs_mlp_train_step(float *params, float *adam_m, float *adam_v, float *grad, uint32_t step,
                             float lr, const float *x, const float *t, uint32_t n, float *loss,
                             bs_stream_t stream) {
+    BS_NVTX_RANGE();
     if (n == 0 || step == 0) return BS_ERR_INVALID_ARG;
     if (!params || !adam_m || !adam_v || !grad || !x || !t) return BS_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -621,6 +625,7 @@ bs_status bs_mlp_train_step(float *params, float *adam_m, float *adam_v, float *
 
 bs_status bs_mlp_estimate_ex(const float *params, const uint32_t *counts, uint32_t n, uint32_t N,
                              float *out, uint32_t variant, bs_stream_t stream) {
+    BS_NVTX_RANGE();
     if (!valid_N_l(N)) return BS_ERR_INVALID_ARG;
     if (variant > BS_VARIANT_TC) return BS_ERR_INVALID_ARG;
     if (n == 0) return BS_OK;

@@ -673,6 +673,7 @@ extern "C" {
 bs_status bs_estimate_pairs_ex(const uint32_t *A, const uint32_t *pcA, uint32_t nA, const uint32_t *B,
                                const uint32_t *pcB, uint32_t nB, uint32_t N, uint32_t measures,
                                float *out, uint32_t *counts, uint32_t variant, bs_stream_t stream) {
+    BS_NVTX_RANGE();
     if (!valid_N(N) || (measures & ~15u) || variant > BS_VARIANT_TC) return BS_ERR_INVALID_ARG;
     if (nA == 0 || nB == 0) return BS_OK;
     if (!A || !B || !pcA || !pcB) return BS_ERR_INVALID_ARG;
@@ -782,6 +783,7 @@ bs_status bs_topk_ex(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const 
                      const uint32_t *pcDB, uint32_t nDB, uint32_t N, uint32_t by, uint32_t k,
                      int exclude_self, float *score, uint32_t *idx, void *workspace,
                      size_t workspace_bytes, uint32_t variant, bs_stream_t stream) {
+    BS_NVTX_RANGE();
     if (exclude_self && nQ > nDB) return BS_ERR_INVALID_ARG;
     return topk_impl(Q, pcQ, nQ, DB, pcDB, nDB, N, by, k, exclude_self, 0, score, idx, workspace,
                      workspace_bytes, variant, (cudaStream_t)stream);
@@ -792,6 +794,7 @@ bs_status bs_topk_shard(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, con
                         uint32_t by, uint32_t k, int exclude_self, float *score, uint32_t *idx,
                         void *workspace, size_t workspace_bytes, uint32_t variant,
                         bs_stream_t stream) {
+    BS_NVTX_RANGE();
     if ((uint64_t)db_offset + nDB > 0xFFFFFFFFull) return BS_ERR_INVALID_ARG;
     return topk_impl(Q, pcQ, nQ, DB, pcDB, nDB, N, by, k, exclude_self, db_offset, score, idx,
                      workspace, workspace_bytes, variant, (cudaStream_t)stream);
@@ -800,6 +803,7 @@ bs_status bs_topk_shard(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, con
 bs_status bs_topk_merge(const float *score_parts, const uint32_t *idx_parts, uint32_t parts,
                         uint32_t nQ, uint32_t k, const uint32_t *part_offset, uint32_t by,
                         float *score, uint32_t *idx, bs_stream_t stream) {
+    BS_NVTX_RANGE();
     const int m = measure_code(by);
     if (m < 0 || k == 0 || k > BS_TOPK_K_MAX) return BS_ERR_INVALID_ARG;
     if (parts == 0 || parts > BS_TOPK_MERGE_PARTS_MAX) return BS_ERR_INVALID_ARG;
@@ -844,6 +848,7 @@ size_t bs_tiled_bytes(uint32_t n, uint32_t N) {
 
 bs_status bs_tile_sketches(const uint32_t *sketch, uint32_t n_rows, uint32_t N, void *tiled,
                            bs_stream_t stream) {
+    BS_NVTX_RANGE();
     if (!valid_N(N) || (N % 128) != 0) return BS_ERR_INVALID_ARG;
     if (n_rows == 0) return BS_OK;
     if (!sketch || !tiled) return BS_ERR_INVALID_ARG;
@@ -861,6 +866,7 @@ bs_status bs_topk_pretiled(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, 
                            const uint32_t *pcDB, uint32_t nDB, uint32_t N, uint32_t by, uint32_t k,
                            float *score, uint32_t *idx, void *workspace, size_t workspace_bytes,
                            bs_stream_t stream) {
+    BS_NVTX_RANGE();
     if (!valid_N(N)) return BS_ERR_INVALID_ARG;
     if (k == 0 || k > BS_TOPK_K_MAX) return BS_ERR_INVALID_ARG;
     const int m = measure_code(by);
@@ -913,6 +919,7 @@ bs_status bs_topk_batched_plan(const bs_topk_job *jobs, uint32_t n_jobs, uint32_
 bs_status bs_topk_batched(const bs_topk_job *jobs, uint32_t n_jobs, uint32_t by, uint32_t k,
                           void *workspace, size_t workspace_bytes, uint32_t variant,
                           bs_stream_t stream) {
+    BS_NVTX_RANGE();
     if (!jobs || n_jobs == 0 || n_jobs > BS_TOPK_BATCH_MAX) return BS_ERR_INVALID_ARG;
     if (k == 0 || k > BS_TOPK_K_MAX) return BS_ERR_INVALID_ARG;
     const int m = measure_code(by);

@@ -165,6 +165,7 @@ bs_status bs_exact_counts(const uint64_t *q_row_ptr, const uint32_t *q_col, uint
                           const uint64_t *db_row_ptr, const uint32_t *db_col, uint32_t ndb,
                           uint64_t db_nnz, uint32_t d, uint32_t *counts, uint32_t *q_sizes,
                           uint32_t *db_sizes, bs_stream_t stream) {
+    BS_NVTX_RANGE();
     if (d == 0 || d > BS_EXACT_D_MAX) return BS_ERR_INVALID_ARG;
     if (nq == 0 || ndb == 0) return BS_OK;
     if (!q_row_ptr || !db_row_ptr || !counts || (q_nnz > 0 && !q_col) || (db_nnz > 0 && !db_col))
@@ -186,6 +187,7 @@ bs_status bs_threshold_eval(const float *est, const uint32_t *counts, const uint
                             const uint32_t *db_sizes, uint32_t nq, uint32_t ndb, uint32_t by,
                             const double *thresholds, uint32_t n_thresholds, uint32_t *out,
                             bs_stream_t stream) {
+    BS_NVTX_RANGE();
     int m = -1;
     switch (by) {
         case BS_IP: m = M_IP; break;

@@ -115,6 +115,7 @@ constexpr uint32_t NO_IDX = 0xFFFFFFFFu;
 // threshold (checked against emulated FP32 keys one ulp above it) while
 // letting through almost none that fall a full count short.
 constexpr float FILTER_SLACK = 0.99987793f;
+constexpr float LOG2_FILTER_SLACK = -1.76126e-4f;   // log2(FILTER_SLACK), folded into the bounds
 
 // Shared-memory layout for NOP operand slots and RD raw slots of SK bytes
 // per row and NG epilogue groups (offsets from the 1024-aligned base); the
@@ -327,20 +328,28 @@ __device__ __forceinline__ void raw_row(const uint8_t *raw, int plane, int strid
 }
 
 // ---- per-row heap of the k best (root = worst), interleaved across rows ------
+// Entry i of row t is the 8-byte (key bits, index) at ent[i * BM + t]: one
+// shared-memory load per child while sifting, consecutive rows in
+// consecutive entries.
 struct Heap {
-    float *key;      // key[i * BM + t]
-    uint32_t *ix;
+    uint2 *ent;
     int t, size, cap;
-    __device__ float k_at(int i) const { return key[i * BM + t]; }
-    __device__ uint32_t i_at(int i) const { return ix[i * BM + t]; }
-    __device__ void put(int i, float kk, uint32_t ii) { key[i * BM + t] = kk; ix[i * BM + t] = ii; }
+    __device__ void get(int i, float &k, uint32_t &ix) const {
+        const uint2 v = ent[i * BM + t];
+        k = __uint_as_float(v.x);
+        ix = v.y;
+    }
+    __device__ float k_at(int i) const { return __uint_as_float(ent[i * BM + t].x); }
+    __device__ uint32_t i_at(int i) const { return ent[i * BM + t].y; }
+    __device__ void put(int i, float kk, uint32_t ii) { ent[i * BM + t] = make_uint2(__float_as_uint(kk), ii); }
     // append and sift up: parents that rank below the new entry move down
     __device__ void push(float kk, uint32_t ii) {
         int i = size++;
         while (i > 0) {
             const int p = (i - 1) >> 1;
-            const float pk = k_at(p);
-            const uint32_t pi = i_at(p);
+            float pk;
+            uint32_t pi;
+            get(p, pk, pi);
             if (!better(pk, pi, kk, ii)) break;
             put(i, pk, pi);
             i = p;
@@ -354,11 +363,13 @@ struct Heap {
             const int l = 2 * i + 1;
             if (l >= n) break;
             int m = l;
-            float mk = k_at(l);
-            uint32_t mi = i_at(l);
+            float mk;
+            uint32_t mi;
+            get(l, mk, mi);
             if (l + 1 < n) {
-                const float rk = k_at(l + 1);
-                const uint32_t ri = i_at(l + 1);
+                float rk;
+                uint32_t ri;
+                get(l + 1, rk, ri);
                 if (better(mk, mi, rk, ri)) { m = l + 1; mk = rk; mi = ri; }
             }
             if (!better(kk, ii, mk, mi)) break;
@@ -371,10 +382,10 @@ struct Heap {
     // in-place heapsort: best first in slots [0, size)
     __device__ void sort_best_first() {
         for (int end = size - 1; end > 0; --end) {
-            const float rk = k_at(0);
-            const uint32_t ri = i_at(0);
-            const float ek = k_at(end);
-            const uint32_t ei = i_at(end);
+            float rk, ek;
+            uint32_t ri, ei;
+            get(0, rk, ri);
+            get(end, ek, ei);
             put(end, rk, ri);
             sift_down(0, ek, ei, end);
         }
@@ -423,6 +434,9 @@ __device__ __forceinline__ RowFilter make_filter(float theta, float rc, float in
         f.c0 = rc * expf(-0.5f * theta / invL);
         f.c1 = 0.f;
     }
+    // the slack rides in the constants: 2^(x + log2 s) = s 2^x, (s c0) f0 = s (c0 f0)
+    if (M == M_JS || M == M_COS) f.c1 += LOG2_FILTER_SLACK;
+    else f.c0 *= FILTER_SLACK;
     if (!isfinite(f.c0) || !isfinite(f.c1)) f.all = true;
     return f;
 }
@@ -438,11 +452,11 @@ __device__ __forceinline__ float ex2_approx(float x) {
 template <int M>
 __device__ __forceinline__ bool admit(const RowFilter &f, float U, float f0) {
     if (f.all) return true;
-    float bound;
+    float bound;   // already lowered by the slack (make_filter)
     if (M == M_JS) bound = ex2_approx(fmaf(f.c0, f0, f.c1));
     else if (M == M_COS) bound = ex2_approx(fmaf(f0, f.c0 - f0 * 1.44269504089f, f.c1));
     else bound = f.c0 * f0;
-    return U >= bound * FILTER_SLACK;
+    return U >= bound;
 }
 
 // Running state of one query row in the epilogue.
@@ -456,14 +470,14 @@ struct RowState {
 // (eff_k, eff_i) is the better of this heap's root (when full) and the other
 // group's; a pair not ranking above it cannot reach the final list.
 template <int M>
-__device__ __forceinline__ RowState consider(RowState st, float *hkey, uint32_t *hix, int t, uint32_t col,
+__device__ __forceinline__ RowState consider(RowState st, uint2 *hent, int t, uint32_t col,
                                              uint32_t c, uint32_t b, uint32_t a, float lnA, float eff_k,
                                              uint32_t eff_i, uint32_t N, float invL, int cap) {
     const float lnB = M == M_COS ? row_log(b, N) : 0.0f;
     const float key = rank_key<M>(a, b, c, N, lnA, lnB, invL);
     if (!better(key, col, eff_k, eff_i)) return st;
     Heap h;
-    h.key = hkey; h.ix = hix; h.t = t; h.size = st.size; h.cap = cap;
+    h.ent = hent; h.t = t; h.size = st.size; h.cap = cap;
     if (h.size < h.cap) {
         h.push(key, col);
         st.size = h.size;
@@ -483,7 +497,7 @@ __device__ __forceinline__ RowState consider(RowState st, float *hkey, uint32_t 
 // root is repeated under the lock.  Returns the root key once the heap is
 // full, else -inf.
 template <int M>
-__device__ __noinline__ float consider_shared(float *hkey, uint32_t *hix, float *root_key, int *hsize,
+__device__ __noinline__ float consider_shared(uint2 *hent, float *root_key, int *hsize,
                                               unsigned int *lock, int t, uint32_t col, uint32_t c,
                                               uint32_t b, uint32_t a, float lnA, float eff_k,
                                               uint32_t N, float invL, int cap, unsigned int *err) {
@@ -499,7 +513,7 @@ __device__ __noinline__ float consider_shared(float *hkey, uint32_t *hix, float 
     }
     __threadfence_block();
     Heap h;
-    h.key = hkey; h.ix = hix; h.t = t; h.size = hsize[t]; h.cap = cap;
+    h.ent = hent; h.t = t; h.size = hsize[t]; h.cap = cap;
     float root = -INFINITY;
     if (h.size < cap) {
         h.push(key, col);
@@ -771,21 +785,21 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
         uint32_t q = 0, a = 0;
         bool row_ok = false;
         float rc = 0.0f, lnA = 0.0f, Na = 0.0f;
-        float *hkey = reinterpret_cast<float *>(base + Smem::heap) + (size_t)(SHARED ? 0 : grp) * p.k * BM * 2;
-        uint32_t *hix = reinterpret_cast<uint32_t *>(hkey + (size_t)p.k * BM);
+        uint2 *hent = reinterpret_cast<uint2 *>(base + Smem::heap) + (size_t)(SHARED ? 0 : grp) * p.k * BM;
         RowState st;
         st.thr_k = -INFINITY; st.thr_i = NO_IDX; st.size = 0;
         // this row's buffer of admitted pairs, (count << 8) | column in tile
         uint32_t *cb = reinterpret_cast<uint32_t *>(base + Smem::cbuf) + (size_t)grp * CB * BM;
         int nbuf = 0;
         uint32_t d_col0 = 0;          // first column of the tile the buffer belongs to
-        const float *d_cv = colv;     // that tile's column values
+        const float2 *d_cv = reinterpret_cast<const float2 *>(colv);   // that tile's (b, f0) per column
         float eff_k = -INFINITY;                   // threshold the filter was built from
         uint32_t eff_i = NO_IDX;
         RowFilter filt;
         filt.all = true; filt.c0 = filt.c1 = 0.f;
         Cursor cur;
         cur.start(jobs, njobs, u_lo);
+        uint32_t b_pre[2] = {0u, 0u};   // counts of this thread's columns of the next tile
         uint32_t N = jobs[cur.j].N;
         float invL = jobs[cur.j].invL;
         // insert every buffered pair of this row into its heap (warp-wide loop)
@@ -795,7 +809,7 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                     --nbuf;
                     const uint32_t ent = cb[nbuf * BM + r];
                     const uint32_t j = ent & 255u;
-                    st = consider<M>(st, hkey, hix, r, d_col0 + j, ent >> 8, (uint32_t)d_cv[j], a, lnA,
+                    st = consider<M>(st, hent, r, d_col0 + j, ent >> 8, (uint32_t)d_cv[j].x, a, lnA,
                                      eff_k, eff_i, N, invL, (int)p.k);
                     if (st.thr_i != NO_IDX && better(st.thr_k, st.thr_i, eff_k, eff_i)) {
                         eff_k = st.thr_k; eff_i = st.thr_i;
@@ -831,11 +845,23 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                 }
                 if (MODE == MODE_TOPK && NG == 2) named_sync(5, 128 * NG);
             }
-            float *cv = colv + (t & 1) * 3 * BNP;
-            // per-column values of this group's columns (128 threads, 112-240 columns)
-            for (int j = c_lo + e; j < c_hi; j += 128) {
-                const uint32_t col = tile * BN + j;
-                const uint32_t b = col < J.nDB ? __ldg(J.pcDB + col) : 0u;
+            float2 *cv = reinterpret_cast<float2 *>(colv + (t & 1) * 3 * BNP);
+            // per-column values (raw b, bound term f0) of this group's columns,
+            // one or two per thread; their counts were fetched during the
+            // previous tile (the first tile fetches its own)
+            if (t == 0) {
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const uint32_t j = (uint32_t)(c_lo + e + 128 * i);
+                    const uint32_t col = tile * BN + j;
+                    b_pre[i] = (j < (uint32_t)c_hi && col < J.nDB) ? __ldg(J.pcDB + col) : 0u;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int j = c_lo + e + 128 * i;
+                if (j >= c_hi) continue;
+                const uint32_t b = b_pre[i];
                 const uint32_t b_cl = b < N - 1 ? b : N - 1;
                 const float Bf = (float)(N - b_cl);
                 float f0;
@@ -844,8 +870,18 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                 else if (M == M_COS) f0 = sqrtf(fmaxf(-logf(Bf / (float)N), 0.0f));
                 else if (M == M_IP) f0 = Bf;
                 else f0 = sqrtf(Bf);
-                cv[j] = (float)b;         // raw count: U' is formed from the raw a, b, c
-                cv[BNP + j] = f0;
+                cv[j] = make_float2((float)b, f0);   // raw count: U' is formed from the raw a, b, c
+            }
+            if (t + 1 < n_my_tiles) {   // the next tile's counts, in flight during this one
+                Cursor nx = cur;
+                nx.step(jobs);
+                const Job &J2 = jobs[nx.j];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const uint32_t j = (uint32_t)(c_lo + e + 128 * i);
+                    const uint32_t col = nx.tile * BN + j;
+                    b_pre[i] = (j < (uint32_t)c_hi && col < J2.nDB) ? __ldg(J2.pcDB + col) : 0u;
+                }
             }
             named_sync(2 + grp, 128);
             const uint32_t ab = t & 1;
@@ -874,8 +910,8 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                             if (jj >= width || col_c + jj >= J.nDB) break;
                             const int j = ch * 32 + jj;
                             const uint32_t c = (uint32_t)__uint_as_float(v[jj]);
-                            const uint32_t b = (uint32_t)cv[j];
-                            const float lnB = cv[BNP + j];
+                            const uint32_t b = (uint32_t)cv[j].x;
+                            const float lnB = cv[j].y;
                             const size_t o = o0 + jj;
                             if (J.counts) J.counts[o] = c;
                             float *out = J.out + o;
@@ -912,8 +948,9 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                     const int j = ch * 32 + jj;
                     const float cf = __uint_as_float(v[jj]);   // exact count
                     // U' = N - min(a + b - c, N - 1) = max(N - a - b + c, 1), exact in FP32
-                    const float U = fmaxf(Na - cv[j] + cf, 1.0f);
-                    if (admit<M>(filt, U, cv[BNP + j])) mask |= 1u << jj;
+                    const float2 bf = cv[j];
+                    const float U = fmaxf(Na - bf.x + cf, 1.0f);
+                    if (admit<M>(filt, U, bf.y)) mask |= 1u << jj;
                 }
                 if (width < 32) mask &= 0xFFFFu;
                 // columns past the database end and the self pair never rank
@@ -940,12 +977,12 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                             const uint32_t c = (uint32_t)__uint_as_float(select32(v, jj));
                             const int j = ch * 32 + (int)jj;
                             if (SHARED) {
-                                const float root = consider_shared<M>(hkey, hix, thr_key, heap_size, row_lock,
-                                                                      r, col_c + jj, c, (uint32_t)cv[j], a, lnA,
+                                const float root = consider_shared<M>(hent, thr_key, heap_size, row_lock,
+                                                                      r, col_c + jj, c, (uint32_t)cv[j].x, a, lnA,
                                                                       eff_k, N, invL, (int)p.k, p.err);
                                 if (root > eff_k) { eff_k = root; eff_i = 0xFFFFFFFEu; }
                             } else {
-                                st = consider<M>(st, hkey, hix, r, col_c + jj, c, (uint32_t)cv[j], a, lnA,
+                                st = consider<M>(st, hent, r, col_c + jj, c, (uint32_t)cv[j].x, a, lnA,
                                                  eff_k, eff_i, N, invL, (int)p.k);
                                 if (st.thr_i != NO_IDX && better(st.thr_k, st.thr_i, eff_k, eff_i)) {
                                     eff_k = st.thr_k; eff_i = st.thr_i;
@@ -1002,15 +1039,14 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
             if (SHARED && NG == 2) named_sync(4, 128 * NG);
             if (SHARED) st.size = heap_size[r];
             Heap h;
-            h.key = hkey; h.ix = hix; h.t = r; h.size = st.size; h.cap = (int)p.k;
+            h.ent = hent; h.t = r; h.size = st.size; h.cap = (int)p.k;
             if (row_ok && (!SHARED || grp == 0)) h.sort_best_first();
             if (!SHARED && NG == 2) {
                 heap_size[grp * BM + r] = st.size;
                 named_sync(4, 128 * NG);
             }
             if (grp == 0 && row_ok) {
-                const float *k1 = reinterpret_cast<float *>(base + Smem::heap) + (size_t)p.k * BM * 2;
-                const uint32_t *i1 = reinterpret_cast<const uint32_t *>(k1 + (size_t)p.k * BM);
+                const uint2 *e1 = reinterpret_cast<const uint2 *>(base + Smem::heap) + (size_t)p.k * BM;
                 const int n0 = st.size, n1 = (!SHARED && NG == 2) ? heap_size[BM + r] : 0;
                 int x = 0, y = 0;
                 for (int s = 0; s < (int)p.k; ++s) {
@@ -1020,8 +1056,9 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                     if (hx || hy) {
                         const float xk = hx ? h.k_at(x) : -INFINITY;
                         const uint32_t xi = hx ? h.i_at(x) : NO_IDX;
-                        const float yk = hy ? k1[y * BM + r] : -INFINITY;
-                        const uint32_t yi = hy ? i1[y * BM + r] : NO_IDX;
+                        const uint2 yv = hy ? e1[y * BM + r] : make_uint2(__float_as_uint(-INFINITY), NO_IDX);
+                        const float yk = __uint_as_float(yv.x);
+                        const uint32_t yi = yv.y;
                         if (hx && (!hy || better(xk, xi, yk, yi))) { kk = xk; ii = xi; ++x; }
                         else { kk = yk; ii = yi; ++y; }
                     }

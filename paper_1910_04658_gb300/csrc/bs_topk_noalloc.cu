@@ -53,6 +53,7 @@ extern "C" bs_status bs_topk_noalloc(const uint32_t *Q, const uint32_t *pcQ, uin
                                      const uint32_t *DB, const uint32_t *pcDB, uint32_t nDB,
                                      uint32_t N, uint32_t by, uint32_t k, int exclude_self,
                                      float *score, uint32_t *idx, bs_stream_t stream) {
+    BS_NVTX_RANGE();
     const size_t need = bs_topk_workspace_bytes(nQ, nDB, N, k);
     if (need > (size_t)BS_TOPK_NOALLOC_SCRATCH_BYTES) return BS_ERR_NO_MEMORY;
     void *scratch = nullptr;

