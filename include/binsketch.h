@@ -180,7 +180,7 @@ bs_status bs_estimate_pairs_ex(const uint32_t *A, const uint32_t *pcA, uint32_t 
  * database is divided between blocks (the CUDA-core kernel splits the
  * database; the tensor-core kernel's persistent blocks cut some row blocks
  * in two), and for the tensor-core kernel k-chunk-tiled copies of Q (rows
- * rounded up to 128) and DB (rows rounded up to 240), N/8 bytes per row.
+ * rounded up to 128) and DB (rows rounded up to 208), N/8 bytes per row.
  */
 size_t bs_topk_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k);
 
@@ -227,16 +227,20 @@ bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
  *                    (this is what bs_topk does).
  * For the tensor-core kernel, BS_VARIANT_TC_CFG(c) OR-ed into `variant` picks
  * its block configuration c (an autotuner's knob): operand slots (widened
- * 256-bit pieces of K), epilogue groups, the depth of the ring the tensor-map
- * copies fill, and whether the two groups share one heap per row:
- *   c = 0: 3 slots, 2 groups, ring 4     c = 1: 2 slots, 2 groups, ring 4
- *   c = 2: 3 slots, 2 groups, ring 4, shared heap
- *   c = 3: 2 slots, 2 groups, ring 4, shared heap
- *   c = 4: 2 slots, 1 group,  ring 4     c = 5: 2 slots, 2 groups, ring 6
- *   c = 6: 2 slots, 2 groups, ring 6, shared heap
- *   c = 7: 2 slots, 2 groups, ring 2     c = 8: 2 slots, 1 group,  ring 2
- *   c = 9: 1 slot,  1 group,  ring 2 (the smallest: every k up to
- *          BS_TOPK_K_MAX fits)
+ * pieces of K of 256 or 128 sketch bits), epilogue groups, the depth of the
+ * ring the bulk copies fill, and whether the two groups share one heap per
+ * row:
+ *   c = 0: 2 slots x 256 bits, 2 groups, ring 4
+ *   c = 1: 2 slots x 256 bits, 2 groups, ring 4, shared heap
+ *   c = 2: 4 slots x 128 bits, 2 groups, ring 8
+ *   c = 3: 4 slots x 128 bits, 2 groups, ring 8, shared heap
+ *   c = 4: 2 slots x 256 bits, 1 group,  ring 4
+ *   c = 5: 2 slots x 256 bits, 2 groups, ring 6
+ *   c = 6: 2 slots x 256 bits, 2 groups, ring 2
+ *   c = 7: 2 slots x 256 bits, 2 groups, ring 6, shared heap
+ *   c = 8: 2 slots x 256 bits, 1 group,  ring 2
+ *   c = 9: 1 slot  x 256 bits, 1 group,  ring 2 (the smallest: every k up
+ *          to BS_TOPK_K_MAX fits)
  * The default is the first that fits in the order 0, 1, ..., 9.
  * Environment: for calls that pass BS_VARIANT_AUTO (bs_topk among them) the
  * variable BS_VARIANT, read once, overrides the choice: "popc" forces the
@@ -266,11 +270,14 @@ bs_status bs_topk_ex(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
 /*
  * bs_topk_batched -- bs_topk for many independent problems (datasets, each
  * with its own sketches, N, rows and self-exclusion; one measure `by` and one
- * k for all) in ONE persistent tensor-core launch: the work units (problem,
- * 128-row query block, 240-row database tile) of all problems form one
- * queue, cut into equal-cost contiguous ranges per SM, so small problems
- * fill the gaps of large ones.  The ranking of every problem is that of
- * bs_topk (Experiment 2, Sec. 4), index for index and bit for bit.
+ * k for all) in ONE persistent tensor-core launch.  The work items are the
+ * row blocks of all problems (128 queries against the whole database of
+ * their problem); the resident blocks claim them at run time from a counter
+ * in the workspace, problems in decreasing cost of one row block, so the
+ * largest items start first and small problems fill the tail.  A row block
+ * is never split, so every list is written once and no merge runs.  The
+ * ranking of every problem is that of bs_topk (Experiment 2, Sec. 4), index
+ * for index and bit for bit.
  *  jobs        HOST array of n_jobs bs_topk_job (their pointers are device
  *              memory); 1 <= n_jobs <= BS_TOPK_BATCH_MAX.  Every job needs
  *              the tensor-core shape (N % 128 == 0, 256 <= N <= 8192, 16-byte
@@ -281,10 +288,11 @@ bs_status bs_topk_ex(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
  *  variant     BS_VARIANT_AUTO or BS_VARIANT_TC, optionally with
  *              BS_VARIANT_TC_CFG(c): one block configuration for the launch
  *  workspace   device memory of at least bs_topk_batched_workspace_bytes()
- *              bytes, 256-byte aligned: tiled copies of every job's sketches
- *              and the partial lists
- * Launches: one re-layout kernel for all jobs, the persistent ranking kernel,
- * and one merge kernel when some row block is split between SMs.
+ *              bytes, 256-byte aligned: the claim counter and tiled copies
+ *              of every job's sketches
+ * Launches: one re-layout kernel for all jobs (it also zeroes the counter)
+ * and the persistent ranking kernel.  Calls that share a workspace must run
+ * in order (one stream).
  * Errors: BS_ERR_INVALID_ARG for n_jobs outside 1..BS_TOPK_BATCH_MAX, a bad
  * measure or k, NULL arrays; BS_ERR_UNSUPPORTED for a job outside the
  * tensor-core shape or a configuration that does not fit k;
@@ -308,7 +316,7 @@ bs_status bs_topk_batched(const bs_topk_job *jobs, uint32_t n_jobs, uint32_t by,
                           void *workspace, size_t workspace_bytes, uint32_t variant,
                           bs_stream_t stream);
 /* bs_topk_batched_plan -- host only: *splits = partial lists per query row
- * (the merge kernel runs when > 1), *launches = kernels one bs_topk_batched
+ * (always 1: row blocks are never split), *launches = kernels one bs_topk_batched
  * call launches (0 when every job is empty).  Errors as bs_topk_batched
  * returns them for this table and k; either output may be NULL. */
 bs_status bs_topk_batched_plan(const bs_topk_job *jobs, uint32_t n_jobs, uint32_t k, uint32_t *splits,
@@ -368,13 +376,13 @@ bs_status bs_topk_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, uint32
 /*
  * bs_tiled_bytes / bs_tile_sketches -- keep a sketch database in the layout
  * the tensor-core kernel reads for its database operand, so repeated searches
- * against it skip the re-layout: row blocks of 240, each block's 16-byte
- * k-chunks contiguous ([block][k-chunk][240 rows] x 16 bytes), so one 256-bit
+ * against it skip the re-layout: row blocks of 208, each block's 16-byte
+ * k-chunks contiguous ([block][k-chunk][208 rows] x 16 bytes), so one 256-bit
  * operand slot of a database tile is a single contiguous run for the
  * kernel's bulk copies.
  *  sketch  uint32[n_rows][N/32] in (16-byte aligned), N % 128 == 0
  *  tiled   bs_tiled_bytes(n_rows, N) bytes out (16-byte aligned); rows
- *          rounded up to 240 are zero.  Same paper content as the sketches.
+ *          rounded up to 208 are zero.  Same paper content as the sketches.
  */
 size_t bs_tiled_bytes(uint32_t n_rows, uint32_t N);
 bs_status bs_tile_sketches(const uint32_t *sketch, uint32_t n_rows, uint32_t N, void *tiled,

@@ -341,18 +341,4 @@ bool tc_shape_ok(uint32_t N, uint32_t k);
 bs_status tile_sketches(const uint32_t *sk, uint32_t n, uint32_t N, uint32_t R, void *tiled,
                         cudaStream_t stream);
 
-// Batched merge of split lists: for job j, lists key[j]/ix[j] [splits][nQ[j]][k]
-// into score[j]/idx[j] [nQ[j]][k]; rows numbered job by job from row_base.
-struct MergeJobs {
-    const float *key[BS_TOPK_BATCH_MAX];
-    const uint32_t *ix[BS_TOPK_BATCH_MAX];
-    float *score[BS_TOPK_BATCH_MAX];
-    uint32_t *idx[BS_TOPK_BATCH_MAX];
-    uint32_t nQ[BS_TOPK_BATCH_MAX];
-    uint64_t row_base[BS_TOPK_BATCH_MAX + 1];
-    uint32_t njobs;
-};
-bs_status launch_merge_batched(int measure, const MergeJobs &jobs, uint32_t k, uint32_t splits,
-                               cudaStream_t stream);
-
 }  // namespace bs

@@ -438,72 +438,6 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// Merge of the split lists of many problems in one launch (the batched
-// tensor-core top-k): one warp per query row, rows numbered problem by
-// problem (MergeJobs::row_base), the same merge as merge_topk_kernel.
-template <int M>
-__global__ void __launch_bounds__(256)
-    merge_batched_kernel(const __grid_constant__ MergeJobs mj, uint32_t k, uint32_t splits) {
-    __shared__ float skey[8][CAP];
-    __shared__ uint32_t sidx[8][CAP];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *key = skey[warp];
-    uint32_t *ix = sidx[warp];
-    const uint64_t rows = mj.row_base[mj.njobs];
-    for (uint64_t g = (uint64_t)blockIdx.x * 8 + warp; g < rows; g += (uint64_t)gridDim.x * 8) {
-        uint32_t lo = 0, hi = mj.njobs - 1;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi + 1) >> 1;
-            if (mj.row_base[mid] <= g) lo = mid;
-            else hi = mid - 1;
-        }
-        const uint32_t nQ = mj.nQ[lo];
-        const uint32_t q = (uint32_t)(g - mj.row_base[lo]);
-        const float *ws_key = mj.key[lo];
-        const uint32_t *ws_idx = mj.ix[lo];
-        int cnt = 0;
-        float tk = -INFINITY;
-        uint32_t ti = NO_IDX;
-        for (uint32_t s = 0; s < splits; ++s) {
-            const size_t o = ((size_t)s * nQ + q) * k;
-            for (uint32_t t0 = 0; t0 < k; t0 += 32) {
-                const uint32_t t = t0 + lane;
-                float kk = -INFINITY;
-                uint32_t ii = NO_IDX;
-                if (t < k) {
-                    kk = ws_key[o + t];
-                    ii = ws_idx[o + t];
-                }
-                const bool take = t < k && ii != NO_IDX && better(kk, ii, tk, ti);
-                const uint32_t m = __ballot_sync(0xffffffffu, take);
-                const int slot = cnt + __popc(m & ((1u << lane) - 1u));
-                if (take && slot < CAP) {
-                    key[slot] = kk;
-                    ix[slot] = ii;
-                }
-                cnt += __popc(m);
-            }
-            __syncwarp();
-            if (cnt > CAP - (int)k) {
-                cnt = shrink_row(key, ix, cnt, (int)k, lane);
-                if (cnt == (int)k) {
-                    tk = key[k - 1];
-                    ti = ix[k - 1];
-                }
-            }
-        }
-        const int kept = shrink_row(key, ix, cnt, (int)k, lane);
-        float *score = mj.score[lo];
-        uint32_t *idx = mj.idx[lo];
-        for (uint32_t t = lane; t < k; t += 32) {
-            const float kk = (int)t < kept ? key[t] : -INFINITY;
-            score[(size_t)q * k + t] = (M == M_HAM) ? -kk : kk;
-            idx[(size_t)q * k + t] = (int)t < kept ? ix[t] : NO_IDX;
-        }
-        __syncwarp();
-    }
-}
-
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -592,20 +526,6 @@ bs_status launch_merge(int measure, const float *ws_key, const uint32_t *ws_idx,
                        uint32_t k, uint32_t splits, float *score, uint32_t *idx, cudaStream_t st) {
     static const PartOffsets zero = {};
     return merge_lists<false>(measure, ws_key, ws_idx, nQ, k, splits, score, idx, zero, st);
-}
-
-bs_status launch_merge_batched(int measure, const MergeJobs &mj, uint32_t k, uint32_t splits,
-                               cudaStream_t st) {
-    const uint64_t rows = mj.row_base[mj.njobs];
-    if (rows == 0) return BS_OK;
-    const uint32_t blocks = (uint32_t)std::min<uint64_t>((rows + 7) / 8, 65535u * 16u);
-    switch (measure) {
-        case M_IP: merge_batched_kernel<M_IP><<<blocks, 256, 0, st>>>(mj, k, splits); break;
-        case M_HAM: merge_batched_kernel<M_HAM><<<blocks, 256, 0, st>>>(mj, k, splits); break;
-        case M_JS: merge_batched_kernel<M_JS><<<blocks, 256, 0, st>>>(mj, k, splits); break;
-        default: merge_batched_kernel<M_COS><<<blocks, 256, 0, st>>>(mj, k, splits); break;
-    }
-    return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
 }
 
 bs_status topk_popc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
@@ -912,7 +832,7 @@ bs_status bs_topk_batched_plan(const bs_topk_job *jobs, uint32_t n_jobs, uint32_
     const bs_status st = tc_batched_plan(jobs, n_jobs, k, &s, &nj);
     if (st != BS_OK) return st;
     if (splits) *splits = s;
-    if (launches) *launches = nj == 0 ? 0 : 2 + (s > 1 ? 1 : 0);
+    if (launches) *launches = nj == 0 ? 0 : 2;
     return BS_OK;
 }
 

@@ -55,11 +55,13 @@ struct TileJobs {
     uint32_t n[2 * MAXJ], nKc[2 * MAXJ], R[2 * MAXJ];
     uint32_t blk_base[2 * MAXJ + 1];
     uint32_t count;
+    unsigned int *counter;   // when set: zeroed by block 0
 };
 
 __global__ void __launch_bounds__(256) tile_batched_kernel(const __grid_constant__ TileJobs tj) {
     __shared__ uint4 buf[8][BN + 1];
     const uint32_t b = blockIdx.x;
+    if (tj.counter && b == 0 && threadIdx.x == 0) *tj.counter = 0u;
     uint32_t lo = 0, hi = tj.count - 1;
     while (lo < hi) {
         const uint32_t mid = (lo + hi + 1) >> 1;
@@ -325,38 +327,49 @@ bs_status estimate_tc(const uint32_t *A, const uint32_t *pcA, uint32_t nA, const
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 namespace {
-// The non-empty jobs of a batch and their schedule.
+// The non-empty jobs of a batch and their dynamic schedule.  The work items
+// are the row blocks of all jobs (a row block: 128 queries against the whole
+// database of its job, never split, so every list is written once and needs
+// no merge).  Jobs run in decreasing cost of one row block (tiles x
+// unit_cost) and the blocks of the grid claim items in that order from a
+// device counter: the largest items go first and the smallest fill the tail.
 struct BatchPlan {
     uint32_t nj = 0;
-    uint32_t src[BS_TOPK_BATCH_MAX];      // index in the caller's table
-    uint32_t rbs[BS_TOPK_BATCH_MAX], tiles[BS_TOPK_BATCH_MAX];
-    uint64_t cost[BS_TOPK_BATCH_MAX], unit_base[BS_TOPK_BATCH_MAX];
-    tc::Schedule s;
+    uint32_t src[BS_TOPK_BATCH_MAX];        // index in the caller's table, in run order
+    uint64_t item_base[BS_TOPK_BATCH_MAX];  // first item of each job
+    uint64_t items = 0;
+    uint32_t grid = 0;
 };
 
 bs_status plan_batch(const bs_topk_job *jobs, uint32_t n, uint32_t k, BatchPlan &bp) {
     bp.nj = 0;
+    bp.items = 0;
+    bp.grid = 0;
+    uint64_t rb_cost[BS_TOPK_BATCH_MAX];
     for (uint32_t i = 0; i < n; ++i) {
         const bs_topk_job &jb = jobs[i];
         if (jb.nQ == 0) continue;
         if (jb.nDB == 0) return BS_ERR_UNSUPPORTED;
         if (!tc_shape_ok(jb.N, k)) return BS_ERR_UNSUPPORTED;
         if (jb.exclude_self && !(jb.Q == jb.DB && jb.nQ == jb.nDB)) return BS_ERR_INVALID_ARG;
-        const uint32_t j = bp.nj++;
-        bp.src[j] = i;
-        bp.rbs[j] = (jb.nQ + tc::BM - 1) / tc::BM;
-        bp.tiles[j] = (jb.nDB + tc::BN - 1) / tc::BN;
-        bp.cost[j] = tc::unit_cost(jb.N / 128);
+        bp.src[bp.nj] = i;
+        rb_cost[i] = (uint64_t)((jb.nDB + tc::BN - 1) / tc::BN) * tc::unit_cost(jb.N / 128);
+        ++bp.nj;
     }
-    tc::make_schedule(bp.nj, bp.rbs, bp.tiles, bp.cost, bp.unit_base, bp.s);
+    std::stable_sort(bp.src, bp.src + bp.nj, [&](uint32_t x, uint32_t y) { return rb_cost[x] > rb_cost[y]; });
+    for (uint32_t j = 0; j < bp.nj; ++j) {
+        bp.item_base[j] = bp.items;
+        bp.items += (jobs[bp.src[j]].nQ + tc::BM - 1) / tc::BM;
+    }
+    bp.grid = (uint32_t)std::min<uint64_t>(tc::max_blocks(), bp.items);
     return BS_OK;
 }
 
-// workspace of job i: [split lists][Q tiled in 128-row blocks][DB tiled in 208-row blocks]
-size_t job_ws(const bs_topk_job &jb, uint32_t k, uint32_t splits) {
-    size_t b = splits > 1 ? align256((size_t)splits * jb.nQ * k * 8) : 0;
-    b += align256(tc_tiled_bytes(jb.nQ, jb.N, tc::BM)) + align256(tc_tiled_bytes(jb.nDB, jb.N, tc::BN));
-    return b;
+// workspace: [claim counter, 256 bytes] then per job [Q tiled in 128-row
+// blocks][DB tiled in 208-row blocks]
+constexpr size_t COUNTER_BYTES = 256;
+size_t job_ws(const bs_topk_job &jb) {
+    return align256(tc_tiled_bytes(jb.nQ, jb.N, tc::BM)) + align256(tc_tiled_bytes(jb.nDB, jb.N, tc::BN));
 }
 }  // namespace
 
@@ -365,16 +378,16 @@ bs_status tc_batched_plan(const bs_topk_job *jobs, uint32_t n, uint32_t k, uint3
     static thread_local BatchPlan bp;
     const bs_status st = plan_batch(jobs, n, k, bp);
     if (st != BS_OK) return st;
-    if (splits) *splits = bp.s.splits;
+    if (splits) *splits = 1;
     if (jobs_run) *jobs_run = bp.nj;
     return BS_OK;
 }
 
 size_t tc_batched_workspace(const bs_topk_job *jobs, uint32_t n, uint32_t k) {
-    BatchPlan bp;
+    static thread_local BatchPlan bp;
     if (plan_batch(jobs, n, k, bp) != BS_OK || bp.nj == 0) return 0;
-    size_t b = 0;
-    for (uint32_t j = 0; j < bp.nj; ++j) b += job_ws(jobs[bp.src[j]], k, bp.s.splits);
+    size_t b = COUNTER_BYTES;
+    for (uint32_t j = 0; j < bp.nj; ++j) b += job_ws(jobs[bp.src[j]]);
     return b;
 }
 
@@ -393,19 +406,18 @@ bs_status topk_tc_batched(const bs_topk_job *jobs, uint32_t n, int measure, uint
     const bs_status ps = plan_batch(jobs, n, k, bp);
     if (ps != BS_OK) return ps;
     if (bp.nj == 0) return BS_OK;
-    size_t need = 0;
-    for (uint32_t j = 0; j < bp.nj; ++j) need += job_ws(jobs[bp.src[j]], k, bp.s.splits);
-    if (need > 0 && (!workspace || workspace_bytes < need)) return BS_ERR_NO_MEMORY;
-    if (need > 0 && (reinterpret_cast<uintptr_t>(workspace) & 255u)) return BS_ERR_INVALID_ARG;
+    size_t need = COUNTER_BYTES;
+    for (uint32_t j = 0; j < bp.nj; ++j) need += job_ws(jobs[bp.src[j]]);
+    if (!workspace || workspace_bytes < need) return BS_ERR_NO_MEMORY;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255u) return BS_ERR_INVALID_ARG;
 
     static thread_local tc::Args<tc::MAXJ> p;
     static thread_local tc::TileJobs tj;
-    static thread_local MergeJobs mj;
     memset(&p, 0, sizeof(p));
     memset(&tj, 0, sizeof(tj));
-    memset(&mj, 0, sizeof(mj));
-    const uint32_t splits = bp.s.splits;
     uint8_t *w = reinterpret_cast<uint8_t *>(workspace);
+    unsigned int *counter = reinterpret_cast<unsigned int *>(w);
+    w += COUNTER_BYTES;
     uint32_t blk = 0;
     auto add_tile = [&](const uint32_t *src, uint32_t rows, uint32_t N, uint32_t R) {
         uint4 *dst = reinterpret_cast<uint4 *>(w);
@@ -423,40 +435,28 @@ bs_status topk_tc_batched(const bs_topk_job *jobs, uint32_t n, int measure, uint
     for (uint32_t j = 0; j < bp.nj; ++j) {
         const bs_topk_job &jb = jobs[bp.src[j]];
         tc::Job &J = p.job[j];
-        float *ws_key = nullptr;
-        uint32_t *ws_idx = nullptr;
-        if (splits > 1) {
-            ws_key = reinterpret_cast<float *>(w);
-            ws_idx = reinterpret_cast<uint32_t *>(ws_key + (size_t)splits * jb.nQ * k);
-            w += align256((size_t)splits * jb.nQ * k * 8);
-        }
         tc::fill_job(J, jb.pcQ, jb.pcDB, jb.nQ, jb.nDB, jb.N);
         J.tQ = add_tile(jb.Q, jb.nQ, jb.N, tc::BM);
         J.tDB = add_tile(jb.DB, jb.nDB, jb.N, tc::BN);
         J.exclude_self = jb.exclude_self;
         J.self_off = 0;
-        J.score = jb.score; J.idx = jb.idx; J.ws_key = ws_key; J.ws_idx = ws_idx;
-        J.unit_base = bp.unit_base[j];
-        mj.key[j] = ws_key; mj.ix[j] = ws_idx;
-        mj.score[j] = jb.score; mj.idx[j] = jb.idx;
-        mj.nQ[j] = jb.nQ;
-        mj.row_base[j + 1] = mj.row_base[j] + jb.nQ;
+        J.score = jb.score; J.idx = jb.idx; J.ws_key = nullptr; J.ws_idx = nullptr;
+        J.unit_base = bp.item_base[j];
     }
-    mj.njobs = bp.nj;
     tj.blk_base[tj.count] = blk;
+    tj.counter = counter;   // zeroed by the re-layout launch, ahead of the pair kernel on this stream
     tc::tile_batched_kernel<<<blk, 256, 0, stream>>>(tj);
     if (cudaGetLastError() != cudaSuccess) return BS_ERR_CUDA;
-    memcpy(p.block_start, bp.s.block_start, sizeof(uint64_t) * (bp.s.grid + 1));
     p.njobs = bp.nj;
     p.k = k;
-    p.splits = splits;
+    p.splits = 1;
+    p.counter = counter;
+    p.items = (uint32_t)bp.items;
     p.wait_limit = kTcWaitLimit;
     p.err = err;
-    const cudaError_t ce = launch_measure(measure, cfg, p, bp.s.grid, stream);
+    const cudaError_t ce = launch_measure(measure, cfg, p, bp.grid, stream);
     if (ce == cudaErrorInvalidConfiguration) return BS_ERR_UNSUPPORTED;
-    if (ce != cudaSuccess) return BS_ERR_CUDA;
-    if (splits <= 1) return BS_OK;
-    return launch_merge_batched(measure, mj, k, splits, stream);
+    return ce == cudaSuccess ? BS_OK : BS_ERR_CUDA;
 }
 
 }  // namespace bs

@@ -227,17 +227,20 @@ extern "C" {
 bs_status bs_sketch(const uint64_t *row_ptr, const uint32_t *col, uint32_t n_rows, uint64_t nnz,
                     uint32_t d, uint32_t N, uint64_t seed, uint32_t *sketch, uint32_t *popcnt,
                     bs_stream_t stream) {
+    BS_NVTX_RANGE();
     return launch_sketch<false>(row_ptr, col, n_rows, nnz, d, N, seed, sketch, popcnt, stream);
 }
 
 bs_status bs_sketch_parity(const uint64_t *row_ptr, const uint32_t *col, uint32_t n_rows,
                            uint64_t nnz, uint32_t d, uint32_t N, uint64_t seed, uint32_t *sketch,
                            uint32_t *popcnt, bs_stream_t stream) {
+    BS_NVTX_RANGE();
     return launch_sketch<true>(row_ptr, col, n_rows, nnz, d, N, seed, sketch, popcnt, stream);
 }
 
 bs_status bs_popcount_rows(const uint32_t *sketch, uint32_t n_rows, uint32_t N, uint32_t *popcnt,
                            bs_stream_t stream) {
+    BS_NVTX_RANGE();
     if (!valid_N(N)) return BS_ERR_INVALID_ARG;
     if (n_rows == 0) return BS_OK;
     if (!sketch || !popcnt) return BS_ERR_INVALID_ARG;

@@ -71,6 +71,8 @@ constexpr uint32_t SF_COL = 480;           // unit scale factors (A at +0, B at 
 constexpr int MAXG = 192;                  // most persistent blocks per launch
 constexpr int MAXJ = BS_TOPK_BATCH_MAX;    // most jobs per batched launch
 constexpr int MODE_TOPK = 0, MODE_STORE = 1;
+constexpr int IR = 8;                      // dynamic schedule: row blocks published ahead
+constexpr uint32_t ITEM_END = 0xFFFFFFFFu; // no row block left
 enum { INJECT_NONE = 0, INJECT_STALL = 1 };
 
 // threads per block with NG epilogue groups
@@ -131,7 +133,7 @@ struct Smem {
     static constexpr int lock = thr + NG * BM * 12;             // [BM] shared-heap row locks
     static constexpr int cbuf = lock + BM * 4;                  // [NG][CB][BM] admitted pairs
     static constexpr int heap = cbuf + NG * CB * BM * 4;
-    static_assert((2 * NOP + 2 * RD + 5) * 8 + 8 <= 512, "barrier area");
+    static_assert((2 * NOP + 2 * RD + 5 + 2 * IR) * 8 + 8 + 4 * IR <= 512, "barrier area");
 };
 
 // One problem of the job table: nQ query rows against nDB database rows.
@@ -168,6 +170,8 @@ struct Args {
     uint32_t inject;                  // INJECT_STALL: test-only fault injection
     long long wait_limit;             // cycles a wait may take before it gives up
     unsigned int *err;
+    unsigned int *counter;            // dynamic schedule: next row block to claim (zero at launch)
+    uint32_t items;                   // dynamic schedule: row blocks of all jobs
 };
 
 // ---- tcgen05 wrappers -------------------------------------------------------
@@ -561,6 +565,68 @@ struct Cursor {
     }
 };
 
+// The sequence of tiles one role of a block works through.  Static schedule:
+// the contiguous unit range [u_lo, u_lo + count) of the block.  Dynamic
+// schedule (DYN): whole row blocks ("items", numbered job by job from each
+// job's unit_base), claimed one at a time from a device counter by the TMA
+// producer and published in order through a ring of IR shared-memory slots;
+// every other role reads the same sequence from the ring.  A row block is
+// then never split between blocks.
+template <bool DYN>
+struct TileSeq {
+    const Job *jobs;
+    uint32_t njobs;
+    Cursor cur;                    // static
+    uint32_t left;
+    bool started;
+    uint64_t *item_full;           // dynamic
+    const volatile uint32_t *ring;
+    uint32_t it;                   // items read (including the end marker)
+    uint32_t j, rb, tile;          // the current tile
+    bool in_item;
+    __device__ void init_static(const Job *jb, uint32_t nj, uint64_t u_lo, uint32_t count) {
+        jobs = jb; njobs = nj; left = count; started = false; in_item = false; it = 0;
+        cur.start(jb, nj, u_lo);
+    }
+    __device__ void init_dynamic(const Job *jb, uint32_t nj, uint64_t *full, const volatile uint32_t *rg) {
+        jobs = jb; njobs = nj; item_full = full; ring = rg; it = 0; in_item = false; left = 0; started = false;
+    }
+    __device__ void set_item(uint32_t item) {
+        j = 0;
+        while (j + 1 < njobs && jobs[j + 1].unit_base <= item) ++j;
+        rb = item - (uint32_t)jobs[j].unit_base;
+        tile = 0;
+        in_item = true;
+    }
+    // the next tile; false at the end of the sequence (or once the block aborted)
+    template <class W>
+    __device__ bool next(W &wait, volatile int *abort_flag) {
+        if (!DYN) {
+            if (left == 0) return false;
+            if (started) cur.step(jobs);
+            started = true;
+            --left;
+            j = cur.j; rb = cur.rb; tile = cur.tile;
+            return true;
+        }
+        if (in_item && tile + 1 < jobs[j].tiles) { ++tile; return true; }
+        in_item = false;
+        if (*abort_flag) return false;
+        const uint32_t slot = it % IR;
+        wait(&item_full[slot], (it / IR) & 1);
+        if (*abort_flag) return false;
+        const uint32_t item = ring[slot];
+        ++it;
+        if (item == ITEM_END) return false;
+        set_item(item);
+        return true;
+    }
+    // this tile ends its row block's work in this block (its list is due)
+    __device__ bool segment_end() const { return tile + 1 == jobs[j].tiles || (!DYN && left == 0); }
+    // the ring slot of the current item (dynamic)
+    __device__ uint32_t slot() const { return (it - 1) % IR; }
+};
+
 // The block holding unit x: the last block whose range starts at or before x.
 template <int NJ>
 __device__ __forceinline__ uint32_t block_of(const Args<NJ> &p, uint64_t x, uint32_t nblocks) {
@@ -589,8 +655,13 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
     uint64_t *raw_full = bars + 2 * NOP, *raw_empty = raw_full + RD;
     uint64_t *acc_full = raw_empty + RD, *acc_empty = acc_full + 2;
     uint64_t *drain_bar = acc_empty + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain_bar + 1);
+    uint64_t *item_full = drain_bar + 1, *item_empty = item_full + IR;   // dynamic schedule
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(item_empty + IR);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    volatile uint32_t *item_ring = reinterpret_cast<volatile uint32_t *>(tmem_slot + 2);   // [IR]
+    // a batch of top-k problems claims whole row blocks at run time; one
+    // problem (and the store) deals fixed unit ranges out to the blocks
+    constexpr bool DYN = NJ > 1 && MODE == MODE_TOPK;
     float *thr_key = reinterpret_cast<float *>(base + Smem::thr);     // [NG][BM]
     uint32_t *thr_idx = reinterpret_cast<uint32_t *>(thr_key + NG * BM);
     int *heap_size = reinterpret_cast<int *>(thr_idx + NG * BM);
@@ -626,6 +697,10 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
             mbar_init(&acc_empty[i], 4 * NG);
         }
         mbar_init(drain_bar, 1);
+        for (int i = 0; i < IR; ++i) {
+            mbar_init(&item_full[i], 1);
+            mbar_init(&item_empty[i], 4 * NG);
+        }
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -661,11 +736,12 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
         // ----------------------------- MMA issuer -----------------------------
         if (lane == 0) {
             uint32_t sl = 0;   // operand slots consumed
-            Cursor cur;
-            cur.start(jobs, njobs, u_lo);
+            TileSeq<DYN> seq;
+            if (DYN) seq.init_dynamic(jobs, njobs, item_full, item_ring);
+            else seq.init_static(jobs, njobs, u_lo, n_my_tiles);
             const uint32_t sfa = tmem + SF_COL, sfb = tmem + SF_COL + 16;
-            for (uint32_t t = 0; t < n_my_tiles; ++t) {
-                const uint32_t nsl = slots_per_tile<SK>(jobs[cur.j].nKc);
+            for (uint32_t t = 0; seq.next(wait, abort_flag); ++t) {
+                const uint32_t nsl = slots_per_tile<SK>(jobs[seq.j].nKc);
                 const uint32_t ab = t & 1;
                 if (t >= 2) wait(&acc_empty[ab], ((t >> 1) - 1) & 1);
                 tc_fence_after();
@@ -687,7 +763,6 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                 // fault injection (tests only): the first accumulator is never
                 // announced, as if this role had died
                 if (!(p.inject == INJECT_STALL && t == 0)) mma_commit(&acc_full[ab]);
-                cur.step(jobs);
             }
             // every MMA issued here completes before the TMEM is freed
             mma_commit(drain_bar);
@@ -697,33 +772,54 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
         // ----------------------------- TMA producer -----------------------------
         if (lane == 0) {
             uint32_t rs = 0;   // raw slots issued
-            Cursor cur;
-            cur.start(jobs, njobs, u_lo);
-            for (uint32_t t = 0; t < n_my_tiles && !*abort_flag; ++t) {
-                const Job &J = jobs[cur.j];
+            // the raw slots of one tile
+            auto issue_tile = [&](const Job &J, uint32_t rb, uint32_t tile) {
                 const uint32_t nKc = J.nKc;
                 const uint32_t nsl = slots_per_tile<SK>(nKc);
                 for (uint32_t c = 0; c < nsl; ++c) {
                     const uint32_t o = rs % RD;
                     if (rs >= RD) wait(&raw_empty[o], ((rs / RD) - 1) & 1);
-                    if (*abort_flag) break;
+                    if (*abort_flag) return;
                     uint8_t *dst = raw + o * G::RAW_SLOT;
                     if (MODE == MODE_STORE) {   // strided rows through the tensor maps
                         mbar_arrive_expect_tx(&raw_full[o], G::RAW_A + G::RAW_B);
-                        tma_load_2d(dst, &p.maps[0], &raw_full[o], (int)(G::WPS * c), (int)(cur.rb * BM));
-                        tma_load_2d(dst + G::RAW_A, &p.maps[1], &raw_full[o], (int)(G::WPS * c),
-                                    (int)(cur.tile * BN));
+                        tma_load_2d(dst, &p.maps[0], &raw_full[o], (int)(G::WPS * c), (int)(rb * BM));
+                        tma_load_2d(dst + G::RAW_A, &p.maps[1], &raw_full[o], (int)(G::WPS * c), (int)(tile * BN));
                     } else {                    // one contiguous run per operand
                         const uint32_t kc0 = c * G::KPS;
                         const uint32_t np = nKc - kc0 < (uint32_t)G::KPS ? nKc - kc0 : (uint32_t)G::KPS;
                         mbar_arrive_expect_tx(&raw_full[o], np * (BM + BN) * 16);
-                        bulk_load(dst, J.tQ + ((size_t)cur.rb * nKc + kc0) * BM, np * BM * 16, &raw_full[o]);
-                        bulk_load(dst + G::RAW_A, J.tDB + ((size_t)cur.tile * nKc + kc0) * BN, np * BN * 16,
+                        bulk_load(dst, J.tQ + ((size_t)rb * nKc + kc0) * BM, np * BM * 16, &raw_full[o]);
+                        bulk_load(dst + G::RAW_A, J.tDB + ((size_t)tile * nKc + kc0) * BN, np * BN * 16,
                                   &raw_full[o]);
                     }
                     ++rs;
                 }
-                cur.step(jobs);
+            };
+            if (DYN) {
+                // claim row blocks one at a time and publish each to the other
+                // roles; the end marker once none is left (or on abort)
+                TileSeq<true> cur;
+                cur.init_dynamic(jobs, njobs, item_full, item_ring);
+                for (uint32_t it = 0;; ++it) {
+                    const uint32_t slot = it % IR;
+                    if (it >= (uint32_t)IR) wait(&item_empty[slot], ((it / IR) - 1) & 1);
+                    uint32_t item = ITEM_END;
+                    if (!*abort_flag) {
+                        item = atomicAdd(p.counter, 1u);
+                        if (item >= p.items) item = ITEM_END;
+                    }
+                    item_ring[slot] = item;
+                    mbar_arrive(&item_full[slot]);   // release: the entry is visible to the waiters
+                    if (item == ITEM_END) break;
+                    cur.set_item(item);
+                    const Job &J = jobs[cur.j];
+                    for (uint32_t tile = 0; tile < J.tiles && !*abort_flag; ++tile) issue_tile(J, cur.rb, tile);
+                }
+            } else {
+                TileSeq<false> seq;
+                seq.init_static(jobs, njobs, u_lo, n_my_tiles);
+                while (seq.next(wait, abort_flag) && !*abort_flag) issue_tile(jobs[seq.j], seq.rb, seq.tile);
             }
             // every copy issued here has landed before the block may exit
             for (uint32_t i = rs > (uint32_t)RD ? rs - RD : 0; i < rs; ++i)
@@ -737,10 +833,11 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
         const bool two_b = e + 128 < BN;
         const uint32_t a_lane = tmem + ((uint32_t)((warp & 3) * 32) << 16) + A_COL;
         uint32_t sl = 0;
-        Cursor cur;
-        cur.start(jobs, njobs, u_lo);
-        for (uint32_t t = 0; t < n_my_tiles; ++t) {
-            const uint32_t nKc = jobs[cur.j].nKc;
+        TileSeq<DYN> seq;
+        if (DYN) seq.init_dynamic(jobs, njobs, item_full, item_ring);
+        else seq.init_static(jobs, njobs, u_lo, n_my_tiles);
+        while (seq.next(wait, abort_flag)) {
+            const uint32_t nKc = jobs[seq.j].nKc;
             const uint32_t nsl = slots_per_tile<SK>(nKc);
             for (uint32_t c = 0; c < nsl; ++c, ++sl) {
                 const uint32_t ro = sl % RD, o = sl % NOP;
@@ -770,7 +867,6 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&op_full[o]);
             }
-            cur.step(jobs);
         }
     } else {
         // ------------------------------ epilogue ------------------------------
@@ -797,11 +893,13 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
         uint32_t eff_i = NO_IDX;
         RowFilter filt;
         filt.all = true; filt.c0 = filt.c1 = 0.f;
-        Cursor cur;
-        cur.start(jobs, njobs, u_lo);
+        TileSeq<DYN> seq;
+        if (DYN) seq.init_dynamic(jobs, njobs, item_full, item_ring);
+        else seq.init_static(jobs, njobs, u_lo, n_my_tiles);
         uint32_t b_pre[2] = {0u, 0u};   // counts of this thread's columns of the next tile
-        uint32_t N = jobs[cur.j].N;
-        float invL = jobs[cur.j].invL;
+        bool b_pre_ok = false;          // b_pre holds them
+        uint32_t N = jobs[0].N;
+        float invL = jobs[0].invL;
         // insert every buffered pair of this row into its heap (warp-wide loop)
         auto drain = [&]() {
             while (__any_sync(0xffffffffu, nbuf > 0)) {
@@ -818,17 +916,16 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
             }
         };
 
-        for (uint32_t t = 0; t < n_my_tiles; ++t) {
-            if (t > 0) cur.step(jobs);
-            const Job &J = jobs[cur.j];
-            const uint32_t tile = cur.tile;
+        for (uint32_t t = 0; seq.next(wait, abort_flag); ++t) {
+            const Job &J = jobs[seq.j];
+            const uint32_t tile = seq.tile;
             if (t == 0 || tile == 0) {
                 // a new row block: its row constants, empty heaps, empty
                 // published thresholds (the other group reads them after the
                 // barrier below)
                 N = J.N;
                 invL = J.invL;
-                q = cur.rb * BM + r;
+                q = seq.rb * BM + r;
                 row_ok = q < J.nQ;
                 a = row_ok ? __ldg(J.pcQ + q) : 0u;
                 const uint32_t a_cl = a < N - 1 ? a : N - 1;
@@ -849,7 +946,7 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
             // per-column values (raw b, bound term f0) of this group's columns,
             // one or two per thread; their counts were fetched during the
             // previous tile (the first tile fetches its own)
-            if (t == 0) {
+            if (!b_pre_ok) {
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
                     const uint32_t j = (uint32_t)(c_lo + e + 128 * i);
@@ -872,15 +969,26 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                 else f0 = sqrtf(Bf);
                 cv[j] = make_float2((float)b, f0);   // raw count: U' is formed from the raw a, b, c
             }
-            if (t + 1 < n_my_tiles) {   // the next tile's counts, in flight during this one
-                Cursor nx = cur;
-                nx.step(jobs);
-                const Job &J2 = jobs[nx.j];
+            // the next tile's counts, in flight during this one (when the next
+            // tile is known: the rest of a static range, or of the same row block)
+            b_pre_ok = false;
+            {
+                uint32_t nj = 0, ntile = 0;
+                if (!DYN && seq.left > 0) {
+                    Cursor nx = seq.cur;
+                    nx.step(jobs);
+                    nj = nx.j; ntile = nx.tile; b_pre_ok = true;
+                } else if (DYN && tile + 1 < J.tiles) {
+                    nj = seq.j; ntile = tile + 1; b_pre_ok = true;
+                }
+                if (b_pre_ok) {
+                    const Job &J2 = jobs[nj];
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const uint32_t j = (uint32_t)(c_lo + e + 128 * i);
-                    const uint32_t col = nx.tile * BN + j;
-                    b_pre[i] = (j < (uint32_t)c_hi && col < J2.nDB) ? __ldg(J2.pcDB + col) : 0u;
+                    for (int i = 0; i < 2; ++i) {
+                        const uint32_t j = (uint32_t)(c_lo + e + 128 * i);
+                        const uint32_t col = ntile * BN + j;
+                        b_pre[i] = (j < (uint32_t)c_hi && col < J2.nDB) ? __ldg(J2.pcDB + col) : 0u;
+                    }
                 }
             }
             named_sync(2 + grp, 128);
@@ -1030,10 +1138,14 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                 }
                 if (eff_i != NO_IDX) filt = make_filter<M>(eff_k, rc, invL, J.log2N);
             }
-            if (t + 1 < n_my_tiles && tile + 1 < J.tiles) continue;
+            if (!seq.segment_end()) continue;
             // ---- end of this row block's segment: its list for part `part`
-            const uint64_t x0 = J.unit_base + (uint64_t)cur.rb * J.tiles;   // first unit of this row block
-            const uint32_t part = blockIdx.x - block_of(p, x0, gridDim.x);
+            // (a dynamically scheduled row block is whole: part 0 of 1)
+            uint32_t part = 0;
+            if (!DYN) {
+                const uint64_t x0 = J.unit_base + (uint64_t)seq.rb * J.tiles;   // first unit of this row block
+                part = blockIdx.x - block_of(p, x0, gridDim.x);
+            }
             // sort each heap best first; with two groups the first merges both lists
             // (shared heap: one list, sorted by the first group once both are done)
             if (SHARED && NG == 2) named_sync(4, 128 * NG);
@@ -1085,6 +1197,10 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
             }
             // every heap read of this segment is done before the next one resets them
             if (NG == 2) named_sync(6, 128 * NG);
+            if (DYN) {   // this row block is done: its ring entry may be reused
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&item_empty[seq.slot()]);
+            }
         }
     }
 

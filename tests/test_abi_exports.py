@@ -2,6 +2,8 @@
 import os
 import re
 
+import pytest
+
 import oracle
 from paper_1910_04658_gb300 import binding, build
 
@@ -71,9 +73,32 @@ def test_tensor_core_plan_parts_match_the_persistent_schedule():
     for nq, ndb in ((100_000, 100_000), (4096, 1_000_000), (1000, 1000), (37, 20_000), (129, 257)):
         uses_tc, splits, launches = B.bs_topk_plan(nq, ndb, 4096, 50, B.BS_VARIANT_TC, nq == ndb)
         assert uses_tc and splits == parts(nq, ndb), (nq, ndb, splits, parts(nq, ndb))
-        # two re-layouts (Q in 128-row, DB in 240-row blocks), the ranking
+        # two re-layouts (Q in 128-row, DB in 208-row blocks), the ranking
         # kernel, and the merge when some row block is split
         assert launches == 3 + (splits > 1)
+
+
+def test_batched_plan_claims_whole_row_blocks():
+    # bs_topk_batched_plan is host-only (the addresses are never touched): the
+    # dynamic schedule never splits a row block, so there is no merge -- one
+    # re-layout launch and the ranking launch; an all-empty table launches nothing
+    from paper_1910_04658_gb300 import binding as B
+
+    def job(nq, ndb, N, base):
+        return dict(Q=base, pcQ=base + 0x100000, DB=base, pcDB=base + 0x100000, score=base + 0x200000,
+                    idx=base + 0x300000, nQ=nq, nDB=ndb, N=N, exclude_self=nq == ndb)
+
+    tab = [job(100_000, 100_000, 4096, 1 << 32), job(300, 300, 256, 2 << 32), job(5000, 20, 8192, 3 << 32)]
+    assert B.bs_topk_batched_plan(tab, 50) == (1, 2)
+    assert B.bs_topk_batched_plan([job(0, 10, 1024, 1 << 32)], 50) == (1, 0)
+    # workspace: a 256-byte counter, then each job's tiled Q (rows to 128) and DB (rows to 208)
+    ws = B.bs_topk_batched_workspace_bytes(tab, 50)
+    a256 = lambda x: (x + 255) // 256 * 256
+    want = 256 + sum(a256(-(-nq // 128) * 128 * N // 8) + a256(-(-ndb // 208) * 208 * N // 8)
+                     for nq, ndb, N in ((100_000, 100_000, 4096), (300, 300, 256), (5000, 20, 8192)))
+    assert ws == want, (ws, want)
+    with pytest.raises(B.BinSketchError):   # N = 96: not a tensor-core shape
+        B.bs_topk_batched_plan([job(10, 10, 96, 1 << 32)], 50)
 
 
 def test_header_is_plain_c_and_a_c_program_links(tmp_path):

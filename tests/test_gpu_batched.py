@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import oracle
-from tests.helpers import check_topk_row, u32
+from tests.helpers import check_topk_row, dev_u32, u32
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -84,11 +84,10 @@ def test_persistent_batch_equals_per_dataset_calls(datasets):
         s0, i0 = per.results(j)
         s1, i1 = job.results(j)
         assert torch.equal(i0, i1) and torch.equal(s0, s1), j
-    # launches: the batched sketch, the re-layout, the ranking, (a merge), and
-    # the side dataset's own calls -- far fewer than one top-k per dataset
+    # launches: the batched sketch, the re-layout, the ranking, and the side
+    # dataset's own calls -- far fewer than one top-k per dataset
     assert job.launches() < per.launches()
-    splits, n_launch = B.bs_topk_batched_plan(job.tjobs, 20)
-    assert n_launch == 2 + (splits > 1)
+    assert B.bs_topk_batched_plan(job.tjobs, 20) == (1, 2)
 
 
 def test_batched_topk_rejects_bad_tables(datasets):
@@ -105,3 +104,51 @@ def test_batched_topk_rejects_bad_tables(datasets):
     with pytest.raises(B.BinSketchError) as e:     # N = 96: not a tensor-core shape
         B.bs_topk_batched(bad, B.BS_COS, 20, ws, job.bwsb, 0)
     assert e.value.code == 7
+
+
+def test_dynamic_schedule_many_small_jobs_repeatable():
+    # 64 problems (the table maximum) of mixed shapes, self-joins and
+    # query-vs-database pairs, many more row blocks than resident blocks:
+    # whichever block claims a row block, each list equals the single-problem
+    # tensor-core call's, and a second call on the same workspace (its claim
+    # counter reset by the re-layout launch) gives the same lists again
+    from paper_1910_04658_gb300.inputs import random_sketches
+
+    rng = np.random.default_rng(21)
+    k, dev = 16, torch.device("cuda", 0)
+    jobs, refs = [], []
+    for j in range(B.BS_TOPK_BATCH_MAX):
+        N = int(rng.choice([256, 512, 1024, 4096]))
+        nq = int(rng.integers(1, 700))
+        self_join = j % 3 == 0
+        ndb = nq if self_join else int(rng.integers(1, 2500))
+        dens = float(rng.uniform(0.02, 0.4))
+        q = dev_u32(random_sketches(1000 + j, nq, N, dens))
+        db = q if self_join else dev_u32(random_sketches(5000 + j, ndb, N, dens))
+        pcq = torch.empty((nq,), dtype=torch.int32, device=dev)
+        pcdb = pcq if self_join else torch.empty((ndb,), dtype=torch.int32, device=dev)
+        B.bs_popcount_rows(q, nq, N, pcq)
+        if not self_join:
+            B.bs_popcount_rows(db, ndb, N, pcdb)
+        score = torch.empty((nq, k), dtype=torch.float32, device=dev)
+        idx = torch.empty((nq, k), dtype=torch.int32, device=dev)
+        jobs.append(dict(Q=q, pcQ=pcq, DB=db, pcDB=pcdb, score=score, idx=idx, nQ=nq, nDB=ndb, N=N,
+                         exclude_self=self_join, k=k))
+        s_ref = torch.empty_like(score)
+        i_ref = torch.empty_like(idx)
+        wsb = B.bs_topk_workspace_bytes(nq, ndb, N, k)
+        ws = torch.empty((max(wsb, 1),), dtype=torch.uint8, device=dev)
+        B.bs_topk_ex(q, pcq, nq, db, pcdb, ndb, N, B.BS_JS, k, self_join, s_ref, i_ref, ws, wsb, B.BS_VARIANT_TC)
+        refs.append((s_ref, i_ref))
+    tab = B._job_table(jobs)
+    wsb = B.bs_topk_batched_workspace_bytes(tab, k)
+    ws = torch.empty((wsb,), dtype=torch.uint8, device=dev)
+    for _ in range(2):
+        for jb in jobs:
+            jb["score"].fill_(7.0)
+            jb["idx"].fill_(-7)
+        B.bs_topk_batched(tab, B.BS_JS, k, ws, wsb, 0)
+        torch.cuda.synchronize()
+        assert B.bs_get_async_error() == 0
+        for j, (jb, (s_ref, i_ref)) in enumerate(zip(jobs, refs)):
+            assert torch.equal(jb["idx"], i_ref) and torch.equal(jb["score"], s_ref), j
