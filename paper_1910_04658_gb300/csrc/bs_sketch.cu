@@ -100,10 +100,12 @@ constexpr int kSketchWarps = 8;
 // One warp per row, rows strided over the grid.  The row's N/32-word sketch
 // lives in shared memory (kept zero between rows: the write-out clears it);
 // the next row's offsets are loaded before the current row is scattered.
-template <bool PARITY>
+// Off: the type the offsets are held in -- 32 bits when nnz < 2^32 (fewer
+// registers: the kernel runs at 32 a thread), else 64 bits.
+template <bool PARITY, typename Off>
 __global__ void __launch_bounds__(kSketchWarps * 32, 8)
     sketch_kernel(const uint64_t *__restrict__ row_ptr, const uint32_t *__restrict__ col,
-                  uint32_t n_rows, uint64_t nnz, uint32_t d, uint32_t N, uint64_t mult,
+                  uint32_t n_rows, Off nnz, uint32_t d, uint32_t N, uint64_t mult,
                   uint64_t add, uint32_t *__restrict__ sketch, uint32_t *__restrict__ popcnt,
                   unsigned int *err) {
     extern __shared__ __align__(16) uint32_t smem_words[];
@@ -118,26 +120,32 @@ __global__ void __launch_bounds__(kSketchWarps * 32, 8)
     __syncwarp();
 
     uint32_t r = blockIdx.x * kSketchWarps + warp;
-    uint64_t b = 0, e = 0;
+    // offsets past the index array (or not representable in Off) fail the check below
+    auto off = [nnz](uint64_t x) -> Off { return x > (uint64_t)nnz ? nnz + 1 : (Off)x; };
+    Off b = 0, e = 0;
     if (r < n_rows) {
-        b = __ldg(row_ptr + r);
-        e = __ldg(row_ptr + r + 1);
+        b = off(__ldg(row_ptr + r));
+        e = off(__ldg(row_ptr + r + 1));
     }
     for (; r < n_rows; r += nwarps) {
         const uint32_t rn = r + nwarps;
-        uint64_t nb = 0, ne = 0;
+        Off nb = 0, ne = 0;
         if (rn < n_rows) {   // next row's offsets, in flight while this row is done
-            nb = __ldg(row_ptr + rn);
-            ne = __ldg(row_ptr + rn + 1);
+            nb = off(__ldg(row_ptr + rn));
+            ne = off(__ldg(row_ptr + rn + 1));
         }
         const bool ok = (b <= e) && (e <= nnz);
         bool bad = false;
         if (ok) {
-            // rows are done in pieces of at most 2^30 indices (one piece in practice)
-            for (uint64_t q = b; q < e; q += (1ull << 30)) {
-                const uint64_t rest = e - q;
-                const uint32_t len = rest > (1ull << 30) ? (1u << 30) : (uint32_t)rest;
-                scatter_row<PARITY>(s, col + q, len, d, h, N, lane, bad);
+            if (sizeof(Off) == 4) {
+                scatter_row<PARITY>(s, col + b, (uint32_t)(e - b), d, h, N, lane, bad);
+            } else {
+                // rows are done in pieces of at most 2^30 indices (one piece in practice)
+                for (uint64_t q = b; q < e; q += (1ull << 30)) {
+                    const uint64_t rest = e - q;
+                    const uint32_t len = rest > (1ull << 30) ? (1u << 30) : (uint32_t)rest;
+                    scatter_row<PARITY>(s, col + q, len, d, h, N, lane, bad);
+                }
             }
         }
         bad = __any_sync(0xffffffffu, bad);
@@ -208,13 +216,20 @@ static bs_status launch_sketch(const uint64_t *row_ptr, const uint32_t *col, uin
     hash_params(seed, &mult, &add);
     cudaStream_t st = (cudaStream_t)stream;
     const size_t smem = (size_t)kSketchWarps * (N / 32) * sizeof(uint32_t);
-    auto kern = sketch_kernel<PARITY>;
-    if (ensure_smem((const void *)kern, smem) != cudaSuccess) return BS_ERR_CUDA;
     const uint32_t want = (n_rows + kSketchWarps - 1) / kSketchWarps;
     const uint32_t cap = (uint32_t)sm_count() * 32u;
     const uint32_t grid = want < cap ? want : cap;
-    kern<<<grid, kSketchWarps * 32, smem, st>>>(row_ptr, col, n_rows, nnz, d, N, mult, add, sketch,
-                                                popcnt, err);
+    if (nnz < 0xFFFFFFFFull) {
+        auto kern = sketch_kernel<PARITY, uint32_t>;
+        if (ensure_smem((const void *)kern, smem) != cudaSuccess) return BS_ERR_CUDA;
+        kern<<<grid, kSketchWarps * 32, smem, st>>>(row_ptr, col, n_rows, (uint32_t)nnz, d, N, mult, add,
+                                                    sketch, popcnt, err);
+    } else {
+        auto kern = sketch_kernel<PARITY, uint64_t>;
+        if (ensure_smem((const void *)kern, smem) != cudaSuccess) return BS_ERR_CUDA;
+        kern<<<grid, kSketchWarps * 32, smem, st>>>(row_ptr, col, n_rows, nnz, d, N, mult, add, sketch,
+                                                    popcnt, err);
+    }
     return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
 }
 
