@@ -109,6 +109,8 @@ __host__ __device__ __forceinline__ uint32_t slots_per_tile(uint32_t nKc) {
     return SK == 128 ? (nKc + 1) / 2 : nKc;
 }
 
+constexpr int GSPLIT = 96;                 // first column of the second epilogue group
+static_assert(GSPLIT % 32 == 0 && GSPLIT <= 256 && BN - GSPLIT <= 256, "two columns a thread per group");
 constexpr int CB = 8;                      // admitted pairs a row buffers within a tile
 constexpr uint32_t NO_IDX = 0xFFFFFFFFu;
 // Admit when U' >= bound * (1 - 2^-13).  U' is an exact integer and the bound
@@ -875,8 +877,10 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
         const int quarter = warp & 3;              // TMEM lanes this warp may access
         const int r = quarter * 32 + lane;         // row within the block
         // tile columns of this group
-        const int c_lo = NG == 1 ? 0 : grp * 128;
-        const int c_hi = (NG == 1 || grp == 1) ? BN : 128;
+        // (two groups: 96 and 112 of the 208 columns -- the most even split
+        // whose 32-column TMEM loads all start at a multiple of 32)
+        const int c_lo = NG == 1 ? 0 : grp * GSPLIT;
+        const int c_hi = (NG == 1 || grp == 1) ? BN : GSPLIT;
         // row constants of the current row block (set at each segment start)
         uint32_t q = 0, a = 0;
         bool row_ok = false;
