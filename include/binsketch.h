@@ -180,7 +180,9 @@ bs_status bs_estimate_pairs_ex(const uint32_t *A, const uint32_t *pcA, uint32_t 
  * database is divided between blocks (the CUDA-core kernel splits the
  * database; the tensor-core kernel's persistent blocks cut some row blocks
  * in two), and for the tensor-core kernel k-chunk-tiled copies of Q (rows
- * rounded up to 128) and DB (rows rounded up to 208), N/8 bytes per row.
+ * rounded up to 128) and DB (rows rounded up to 208), N/8 bytes per row --
+ * or, for the configurations that read it (c = 10, 11 below), the FP4 copy
+ * of DB, N/2 bytes per row.
  */
 size_t bs_topk_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k);
 
@@ -241,11 +243,19 @@ bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
  *   c = 8: 2 slots x 256 bits, 1 group,  ring 2
  *   c = 9: 1 slot  x 256 bits, 1 group,  ring 2 (the smallest: every k up
  *          to BS_TOPK_K_MAX fits)
- * The default is the first that fits in the order 0, 1, ..., 9.
+ *   c = 10: the database operand is not widened in the kernel: the call
+ *          writes an FP4 copy of DB (N/2 bytes a row, in the workspace) and
+ *          TMA moves each 256-bit slot of a tile from it into shared memory,
+ *          3 database slots, 2 query slots, 2 groups
+ *   c = 11: as c = 10 with 4 database slots and the shared heap
+ * The default, for bs_topk / bs_topk_ex / bs_topk_shard / bs_topk_noalloc,
+ * is the first of 10, 11 that fits k, else the first of 0, 1, ..., 9 that
+ * fits; calls with a database kept tiled (bs_topk_pretiled) and the batched
+ * form use 0..9 only (c = 10, 11 there return BS_ERR_UNSUPPORTED).
  * Environment: for calls that pass BS_VARIANT_AUTO (bs_topk among them) the
  * variable BS_VARIANT, read once, overrides the choice: "popc" forces the
- * CUDA-core kernel, "tc<c>" selects configuration c wherever the tensor-core
- * kernel applies and c fits k.
+ * CUDA-core kernel, "tc<c>" (c = 0..11) selects configuration c wherever the
+ * tensor-core kernel applies and c fits k.
  * A configuration whose shared memory does not fit k returns
  * BS_ERR_UNSUPPORTED.  bs_topk_workspace_bytes() covers every variant.
  *

@@ -304,13 +304,20 @@ uint32_t tc_splits(uint32_t nQ, uint32_t nDB);
 // bytes of a k-chunk-tiled copy of an n-row sketch matrix in R-row blocks
 // (R = 128 for queries, 208 for a database)
 size_t tc_tiled_bytes(uint32_t n, uint32_t N, uint32_t R);
+// bytes of the FP4 copy of an n-row database (N / 2 bytes a row) that the
+// TMA configurations read
+size_t tc_fp4_bytes(uint32_t n, uint32_t N);
+// tensor-core block configurations: BS_VARIANT_TC_CFG(c), 0 <= c < kTcConfigCount;
+// c >= kTcFirstTmaCfg read the database operand from the FP4 copy by TMA
+constexpr int kTcConfigCount = 12, kTcFirstTmaCfg = 10;
 // wait budget of the tensor-core kernel's bounded waits (cycles), and the
 // shortened budget of a fault-injected call
 constexpr long long kTcWaitLimit = kWaitLimitCycles;
 constexpr long long kTcInjectWaitLimit = 2000000ll;
 // tiled: scratch for the tiled copies, tc_tiled_bytes(nQ, N, 128) rounded up
-// to 256 bytes, then tc_tiled_bytes(nDB, N, 208) (the second part unused when
-// db_tiled, a database kept tiled by bs_tile_sketches, is given)
+// to 256 bytes, then the larger of tc_tiled_bytes(nDB, N, 208) and
+// tc_fp4_bytes(nDB, N) (the second part unused when db_tiled, a database kept
+// tiled by bs_tile_sketches, is given)
 // inject: test-only fault injection (0 = none, 1 = the MMA issuer never
 // announces its first accumulator; waits give up after kTcInjectWaitLimit)
 bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
@@ -332,9 +339,10 @@ bs_status tc_batched_plan(const bs_topk_job *jobs, uint32_t n, uint32_t k, uint3
                           uint32_t *jobs_run);
 bs_status topk_tc_batched(const bs_topk_job *jobs, uint32_t n, int measure, uint32_t k, void *workspace,
                           size_t workspace_bytes, int cfg, unsigned int *err, cudaStream_t stream);
-// tensor-core block configuration chosen for k when none is requested; -1 if
-// no configuration fits
-int tc_default_cfg(uint32_t k);
+// tensor-core block configuration chosen for k when none is requested
+// (allow_tma: the call may build the FP4 database copy); -1 if none fits
+int tc_default_cfg(uint32_t k, bool allow_tma);
+bool tc_cfg_tma(int cfg);
 bool tc_cfg_fits(int cfg, uint32_t k);
 bool tc_shape_ok(uint32_t N, uint32_t k);
 // row-major sketches [n][N/32] -> k-chunk tiles of R-row blocks (N % 128 == 0)

@@ -583,7 +583,12 @@ static int env_variant() {
         const char *e = getenv("BS_VARIANT");
         if (!e) return;
         if (!strcmp(e, "popc")) v = -1;
-        else if (e[0] == 't' && e[1] == 'c' && e[2] >= '0' && e[2] <= '9' && e[3] == 0) v = e[2] - '0';
+        else if (e[0] == 't' && e[1] == 'c' && e[2] >= '0' && e[2] <= '9') {
+            int c = e[2] - '0';
+            if (e[3] >= '0' && e[3] <= '9' && e[4] == 0) c = 10 * c + (e[3] - '0');
+            else if (e[3] != 0) return;
+            if (c < kTcConfigCount) v = c;
+        }
     });
     return v;
 }
@@ -629,8 +634,8 @@ bs_status bs_estimate_pairs(const uint32_t *A, const uint32_t *pcA, uint32_t nA,
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static size_t tc_workspace(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, uint32_t splits) {
-    return align256(ws_bytes(splits, nQ, k)) + align256(tc_tiled_bytes(nQ, N, kTcQueryRows)) +
-           align256(tc_tiled_bytes(nDB, N, kTcTileRows));
+    const size_t db = std::max(tc_tiled_bytes(nDB, N, kTcTileRows), tc_fp4_bytes(nDB, N));
+    return align256(ws_bytes(splits, nQ, k)) + align256(tc_tiled_bytes(nQ, N, kTcQueryRows)) + align256(db);
 }
 
 size_t bs_topk_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k) {
@@ -656,7 +661,7 @@ static bs_status topk_impl(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, 
     int tc_cfg = (int)((variant >> 4) & 15u) - 1;   // -1: default configuration
     if (variant >> 8) return BS_ERR_INVALID_ARG;
     variant &= 15u;
-    if (m < 0 || variant > BS_VARIANT_TC || tc_cfg > 9) return BS_ERR_INVALID_ARG;
+    if (m < 0 || variant > BS_VARIANT_TC || tc_cfg >= kTcConfigCount) return BS_ERR_INVALID_ARG;
     if (variant == BS_VARIANT_AUTO && tc_cfg < 0) {
         const int ev = env_variant();
         if (ev == -1) variant = BS_VARIANT_POPC;
@@ -844,7 +849,7 @@ bs_status bs_topk_batched(const bs_topk_job *jobs, uint32_t n_jobs, uint32_t by,
     if (k == 0 || k > BS_TOPK_K_MAX) return BS_ERR_INVALID_ARG;
     const int m = measure_code(by);
     const int cfg = (int)((variant >> 4) & 15u) - 1;
-    if (m < 0 || (variant >> 8) || cfg > 9) return BS_ERR_INVALID_ARG;
+    if (m < 0 || (variant >> 8) || cfg >= kTcConfigCount) return BS_ERR_INVALID_ARG;
     if ((variant & 15u) != BS_VARIANT_AUTO && (variant & 15u) != BS_VARIANT_TC) return BS_ERR_INVALID_ARG;
     for (uint32_t i = 0; i < n_jobs; ++i)
         if (!valid_N(jobs[i].N)) return BS_ERR_INVALID_ARG;

@@ -185,6 +185,41 @@ static void fill_job(Job &J, const uint32_t *pcQ, const uint32_t *pcDB, uint32_t
     J.log2N = (float)log2((double)N);
 }
 
+// The FP4 copy of a packed sketch matrix that the TMA configurations read as
+// their database operand: 32-bit word w becomes the 16 bytes ((w << 1) & M,
+// w & M, (w >> 1) & M, (w >> 2) & M), M = 0x22222222 (the widening the
+// kernel applies to the query operand), rows stay contiguous (N / 2 bytes).
+// One 16-byte input chunk per thread, 64 bytes out.
+__global__ void __launch_bounds__(256) widen_fp4_kernel(const uint4 *__restrict__ src, size_t n_chunks,
+                                                         uint4 *__restrict__ dst) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_chunks; i += stride) {
+        const uint4 v = src[i];
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            dst[4 * i + t] = make_uint4((w[t] << 1) & 0x22222222u, w[t] & 0x22222222u, (w[t] >> 1) & 0x22222222u,
+                                        (w[t] >> 2) & 0x22222222u);
+    }
+}
+
+// 2-D tensor map over the FP4 copy [rows][N / 2 bytes]: boxes of one 256-bit
+// operand slot (128 bytes) x BN rows with the 128-byte swizzle, so a box lands
+// in the layout the MMA's database descriptors read; rows past the end and
+// the second half of a last 128-bit slot arrive as zeros.  N % 128 == 0 makes
+// the row pitch a multiple of 64 bytes.
+static bool make_map_fp4(CUtensorMap *m, const void *ptr, uint32_t rows, uint32_t N) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc || rows == 0) return false;
+    cuuint64_t dims[2] = {N / 2, rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(N / 2)};
+    cuuint32_t box[2] = {128, BN};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace tc
 
 // ---------------------------------------------------------------------------
@@ -193,8 +228,8 @@ static void fill_job(Job &J, const uint32_t *pcQ, const uint32_t *pcDB, uint32_t
 
 static size_t tc_cfg_smem(int cfg, uint32_t k) {
     switch (cfg) {
-#define X(c, nop, ng, sk, rd, sh) \
-    case c: return tc::smem_bytes<nop, ng, sk, rd, sh>(k);
+#define X(c, nop, ng, sk, rd, sh, nb) \
+    case c: return tc::smem_bytes<nop, ng, sk, rd, sh, nb>(k);
         BS_TC_CONFIGS(X)
 #undef X
     }
@@ -203,16 +238,24 @@ static size_t tc_cfg_smem(int cfg, uint32_t k) {
 
 bool tc_cfg_fits(int cfg, uint32_t k) { return tc_cfg_smem(cfg, k) <= tc::kSmemLimit; }
 
-// default: the first configuration in table order that fits -- deeper
+static_assert(tc::kTcConfigs == kTcConfigCount && tc::kTcFirstTma == kTcFirstTmaCfg, "configuration table");
+bool tc_cfg_tma(int cfg) { return cfg >= tc::kTcFirstTma; }
+
+// default: where the call may build the FP4 database copy (one problem, the
+// database not kept tiled by the caller), the first TMA configuration that
+// fits; otherwise the first configuration in table order that fits -- deeper
 // operand rings and two epilogue groups first
-int tc_default_cfg(uint32_t k) {
-    for (int c = 0; c < tc::kTcConfigs; ++c)
+int tc_default_cfg(uint32_t k, bool allow_tma) {
+    if (allow_tma)
+        for (int c = tc::kTcFirstTma; c < tc::kTcConfigs; ++c)
+            if (tc_cfg_fits(c, k)) return c;
+    for (int c = 0; c < tc::kTcFirstTma; ++c)
         if (tc_cfg_fits(c, k)) return c;
     return -1;
 }
 
 bool tc_shape_ok(uint32_t N, uint32_t k) {
-    return (N % 128) == 0 && N >= 256 && N <= 8192 && k >= 1 && tc_cfg_fits(tc::kTcConfigs - 1, k);
+    return (N % 128) == 0 && N >= 256 && N <= 8192 && k >= 1 && tc_cfg_fits(tc::kTcFirstTma - 1, k);
 }
 
 bool tc_supported(const uint32_t *Q, const uint32_t *DB, uint32_t N, uint32_t k) {
@@ -236,6 +279,9 @@ uint32_t tc_splits(uint32_t nQ, uint32_t nDB) {
 // Bytes of a k-chunk-tiled copy of n rows in R-row blocks (R = tc::BM for
 // queries, tc::BN for a database).
 size_t tc_tiled_bytes(uint32_t n, uint32_t N, uint32_t R) { return (size_t)((n + R - 1) / R) * R * (N / 8); }
+
+// Bytes of the FP4 copy of n rows (the TMA configurations' database operand).
+size_t tc_fp4_bytes(uint32_t n, uint32_t N) { return (size_t)n * (N / 2); }
 
 bs_status tile_sketches(const uint32_t *sk, uint32_t n, uint32_t N, uint32_t R, void *tiled, cudaStream_t stream) {
     if (n == 0) return BS_OK;
@@ -262,21 +308,33 @@ bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uin
                   int exclude_self, uint32_t self_off, float *score, uint32_t *idx, float *ws_key,
                   uint32_t *ws_idx, uint32_t splits, void *tiled, const void *db_tiled, int cfg_req,
                   uint32_t inject, unsigned int *err, cudaStream_t stream) {
-    const int cfg = cfg_req >= 0 ? cfg_req : tc_default_cfg(k);
+    const int cfg = cfg_req >= 0 ? cfg_req : tc_default_cfg(k, db_tiled == nullptr);
     if (cfg < 0 || !tc_cfg_fits(cfg, k)) return BS_ERR_UNSUPPORTED;
+    const bool fp4_db = tc_cfg_tma(cfg);
+    if (fp4_db && db_tiled) return BS_ERR_UNSUPPORTED;   // a kept tiled database has no FP4 copy
+    static thread_local tc::Args<1> p;   // ~2 KB of launch arguments, rebuilt per call
+    memset(&p, 0, sizeof(p));
     // k-chunk-tiled copies: Q in 128-row blocks, DB in 208-row blocks (none for
-    // DB when the caller keeps it tiled)
+    // DB when the caller keeps it tiled, or the FP4 copy for the TMA configurations)
     uint4 *tQ = reinterpret_cast<uint4 *>(tiled);
     if (tile_sketches(Q, nQ, N, tc::BM, tQ, stream) != BS_OK) return BS_ERR_CUDA;
     const uint4 *tDB = reinterpret_cast<const uint4 *>(db_tiled);
-    if (!db_tiled) {
+    if (fp4_db) {
+        uint4 *w = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(tiled) +
+                                             ((tc_tiled_bytes(nQ, N, tc::BM) + 255) & ~(size_t)255));
+        const size_t chunks = (size_t)nDB * (N / 128);
+        const uint32_t blocks = (uint32_t)std::min<size_t>((chunks + 255) / 256, (size_t)sm_count() * 16);
+        if (chunks > 0) {
+            tc::widen_fp4_kernel<<<blocks, 256, 0, stream>>>(reinterpret_cast<const uint4 *>(DB), chunks, w);
+            if (cudaGetLastError() != cudaSuccess) return BS_ERR_CUDA;
+        }
+        if (!tc::make_map_fp4(&p.maps[1], w, nDB, N)) return BS_ERR_CUDA;
+    } else if (!db_tiled) {
         uint4 *t = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(tiled) +
                                              ((tc_tiled_bytes(nQ, N, tc::BM) + 255) & ~(size_t)255));
         if (tile_sketches(DB, nDB, N, tc::BN, t, stream) != BS_OK) return BS_ERR_CUDA;
         tDB = t;
     }
-    static thread_local tc::Args<1> p;   // ~2 KB of launch arguments, rebuilt per call
-    memset(&p, 0, sizeof(p));
     tc::Job &J = p.job[0];
     tc::fill_job(J, pcQ, pcDB, nQ, nDB, N);
     J.tQ = tQ; J.tDB = tDB;
@@ -400,8 +458,8 @@ bs_status topk_tc_batched(const bs_topk_job *jobs, uint32_t n, int measure, uint
         if ((reinterpret_cast<uintptr_t>(jb.Q) & 15u) || (reinterpret_cast<uintptr_t>(jb.DB) & 15u))
             return BS_ERR_UNSUPPORTED;
     }
-    const int cfg = cfg_req >= 0 ? cfg_req : tc_default_cfg(k);
-    if (cfg < 0 || !tc_cfg_fits(cfg, k)) return BS_ERR_UNSUPPORTED;
+    const int cfg = cfg_req >= 0 ? cfg_req : tc_default_cfg(k, false);
+    if (cfg < 0 || !tc_cfg_fits(cfg, k) || tc_cfg_tma(cfg)) return BS_ERR_UNSUPPORTED;
     static thread_local BatchPlan bp;
     const bs_status ps = plan_batch(jobs, n, k, bp);
     if (ps != BS_OK) return ps;

@@ -124,18 +124,20 @@ constexpr float LOG2_FILTER_SLACK = -1.76126e-4f;   // log2(FILTER_SLACK), folde
 // Shared-memory layout for NOP operand slots and RD raw slots of SK bytes
 // per row and NG epilogue groups (offsets from the 1024-aligned base); the
 // heaps follow.
-template <int NOP, int NG, int SK, int RD>
+template <int NOP, int NG, int SK, int RD, int NB = 0>
 struct Smem {
     static_assert(NOP * Geo<SK>::TCOLS <= (int)(SF_COL - A_COL), "query operand slots exceed their TMEM columns");
+    // NB > 0: NB database slots filled by TMA from the FP4 copy, raw slots hold
+    // the query operand only; NB = 0: NOP database slots the widening warps fill
     static constexpr int op = 0;
-    static constexpr int raw = op + NOP * Geo<SK>::BYTES;
-    static constexpr int col = raw + RD * Geo<SK>::RAW_SLOT;    // [2 tiles][3][BNP] floats
+    static constexpr int raw = op + (NB > 0 ? NB : NOP) * Geo<SK>::BYTES;
+    static constexpr int col = raw + RD * (NB > 0 ? Geo<SK>::RAW_A : Geo<SK>::RAW_SLOT);   // [2 tiles][3][BNP] floats
     static constexpr int bars = col + 2 * 3 * BNP * 4;
     static constexpr int thr = bars + 512;                      // [NG][BM] key, idx, size
     static constexpr int lock = thr + NG * BM * 12;             // [BM] shared-heap row locks
     static constexpr int cbuf = lock + BM * 4;                  // [NG][CB][BM] admitted pairs
     static constexpr int heap = cbuf + NG * CB * BM * 4;
-    static_assert((2 * NOP + 2 * RD + 5 + 2 * IR) * 8 + 8 + 4 * IR <= 512, "barrier area");
+    static_assert((2 * NOP + 2 * RD + 2 * NB + 5 + 2 * IR) * 8 + 8 + 4 * IR <= 512, "barrier area");
 };
 
 // One problem of the job table: nQ query rows against nDB database rows.
@@ -641,11 +643,16 @@ __device__ __forceinline__ uint32_t block_of(const Args<NJ> &p, uint64_t x, uint
     return lo;
 }
 
-template <int MODE, int M, int NOP, int NG, int SK, int RD, bool SHARED, int NJ>
+template <int MODE, int M, int NOP, int NG, int SK, int RD, bool SHARED, int NJ, int NB = 0>
 __global__ void __launch_bounds__(threads_for(NG), 1)
     pair_tc_kernel(const __grid_constant__ Args<NJ> p) {
-    using Smem = tc::Smem<NOP, NG, SK, RD>;
+    using Smem = tc::Smem<NOP, NG, SK, RD, NB>;
     using G = Geo<SK>;
+    // BT: the database operand arrives already widened, by TMA from an FP4
+    // copy in global memory (tensor map p.maps[1], 128-byte swizzle), into NB
+    // shared-memory slots; the widening warps write only the query operand
+    constexpr bool BT = NB > 0;
+    static_assert(!BT || (MODE == MODE_TOPK && NJ == 1 && SK == 128), "TMA database operand: one top-k problem");
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -658,7 +665,8 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
     uint64_t *acc_full = raw_empty + RD, *acc_empty = acc_full + 2;
     uint64_t *drain_bar = acc_empty + 2;
     uint64_t *item_full = drain_bar + 1, *item_empty = item_full + IR;   // dynamic schedule
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(item_empty + IR);
+    uint64_t *b_full = item_empty + IR, *b_empty = b_full + NB;           // TMA database slots
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(b_empty + NB);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     volatile uint32_t *item_ring = reinterpret_cast<volatile uint32_t *>(tmem_slot + 2);   // [IR]
     // a batch of top-k problems claims whole row blocks at run time; one
@@ -702,6 +710,10 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
         for (int i = 0; i < IR; ++i) {
             mbar_init(&item_full[i], 1);
             mbar_init(&item_empty[i], 4 * NG);
+        }
+        for (int i = 0; i < NB; ++i) {
+            mbar_init(&b_full[i], 1);
+            mbar_init(&b_empty[i], 1);
         }
         *abort_flag = 0;
         fence_mbar_init();
@@ -750,17 +762,20 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                 const uint32_t d_tmem = tmem + ab * BN;
                 for (uint32_t c = 0; c < nsl; ++c, ++sl) {
                     const uint32_t o = sl % NOP;
+                    const uint32_t ob = BT ? sl % (NB > 0 ? NB : 1) : o;   // database slot
                     wait(&op_full[o], (sl / NOP) & 1);
+                    if (BT) wait(&b_full[ob], (sl / (NB > 0 ? NB : 1)) & 1);
                     tc_fence_after();
                     if (!*abort_flag) {
                         const uint32_t a_tmem = tmem + A_COL + o * G::TCOLS;
-                        const uint32_t b_addr = smem_u32(op + o * G::BYTES);
+                        const uint32_t b_addr = smem_u32(op + ob * G::BYTES);
 #pragma unroll
                         for (int kk = 0; kk < G::MMAS; ++kk)
                             mma_fp4(d_tmem, a_tmem + 8 * kk, sw_desc<SK>(b_addr + kk * 32), IDESC, sfa, sfb,
                                     (c | (uint32_t)kk) != 0);
                     }
                     mma_commit(&op_empty[o]);
+                    if (BT) mma_commit(&b_empty[ob]);
                 }
                 // fault injection (tests only): the first accumulator is never
                 // announced, as if this role had died
@@ -774,6 +789,8 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
         // ----------------------------- TMA producer -----------------------------
         if (lane == 0) {
             uint32_t rs = 0;   // raw slots issued
+            uint32_t bs = 0;   // TMA database slots issued
+            constexpr int NBS = NB > 0 ? NB : 1;
             // the raw slots of one tile
             auto issue_tile = [&](const Job &J, uint32_t rb, uint32_t tile) {
                 const uint32_t nKc = J.nKc;
@@ -782,7 +799,21 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                     const uint32_t o = rs % RD;
                     if (rs >= RD) wait(&raw_empty[o], ((rs / RD) - 1) & 1);
                     if (*abort_flag) return;
-                    uint8_t *dst = raw + o * G::RAW_SLOT;
+                    uint8_t *dst = raw + o * (BT ? G::RAW_A : G::RAW_SLOT);
+                    if (BT) {   // the query operand's packed bits; the widened database tile by TMA
+                        const uint32_t kc0 = c * G::KPS;
+                        const uint32_t np = nKc - kc0 < (uint32_t)G::KPS ? nKc - kc0 : (uint32_t)G::KPS;
+                        mbar_arrive_expect_tx(&raw_full[o], np * BM * 16);
+                        bulk_load(dst, J.tQ + ((size_t)rb * nKc + kc0) * BM, np * BM * 16, &raw_full[o]);
+                        ++rs;
+                        const uint32_t ob = bs % NBS;
+                        if (bs >= (uint32_t)NBS) wait(&b_empty[ob], ((bs / NBS) - 1) & 1);
+                        if (*abort_flag) return;
+                        mbar_arrive_expect_tx(&b_full[ob], G::BYTES);
+                        tma_load_2d(op + ob * G::BYTES, &p.maps[1], &b_full[ob], (int)(c * SK), (int)(tile * BN));
+                        ++bs;
+                        continue;
+                    }
                     if (MODE == MODE_STORE) {   // strided rows through the tensor maps
                         mbar_arrive_expect_tx(&raw_full[o], G::RAW_A + G::RAW_B);
                         tma_load_2d(dst, &p.maps[0], &raw_full[o], (int)(G::WPS * c), (int)(rb * BM));
@@ -826,6 +857,8 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
             // every copy issued here has landed before the block may exit
             for (uint32_t i = rs > (uint32_t)RD ? rs - RD : 0; i < rs; ++i)
                 if (!mbar_wait(&raw_full[i % RD], (i / RD) & 1, p.wait_limit)) raise_error(p.err, BS_ERR_TIMEOUT);
+            for (uint32_t i = bs > (uint32_t)NBS ? bs - NBS : 0; i < bs; ++i)
+                if (!mbar_wait(&b_full[i % NBS], (i / NBS) & 1, p.wait_limit)) raise_error(p.err, BS_ERR_TIMEOUT);
         }
     } else if (warp < 6) {
         // ------------------------------ widening ------------------------------
@@ -844,7 +877,7 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
             for (uint32_t c = 0; c < nsl; ++c, ++sl) {
                 const uint32_t ro = sl % RD, o = sl % NOP;
                 wait(&raw_full[ro], (sl / RD) & 1);
-                const uint8_t *src = raw + ro * G::RAW_SLOT;
+                const uint8_t *src = raw + ro * (BT ? G::RAW_A : G::RAW_SLOT);
                 uint32_t xa[G::WPS], xb0[G::WPS], xb1[G::WPS];
                 if (MODE == MODE_STORE) {
                     raw_row<SK>(src, 16, G::RAW_ROW, e, G::KPS, xa);
@@ -853,18 +886,18 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                 } else {
                     const int valid = (int)(nKc - c * G::KPS);
                     raw_row<SK>(src, BM * 16, 16, e, valid, xa);
-                    raw_row<SK>(src + G::RAW_A, BN * 16, 16, e, valid, xb0);
-                    if (two_b) raw_row<SK>(src + G::RAW_A, BN * 16, 16, e + 128, valid, xb1);
+                    if (!BT) raw_row<SK>(src + G::RAW_A, BN * 16, 16, e, valid, xb0);
+                    if (!BT && two_b) raw_row<SK>(src + G::RAW_A, BN * 16, 16, e + 128, valid, xb1);
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&raw_empty[ro]);   // the raw slot may be refilled
                 if (sl >= (uint32_t)NOP) wait(&op_empty[o], ((sl / NOP) - 1) & 1);
                 uint8_t *oB = op + o * G::BYTES;
                 widen_tmem<SK>(a_lane + o * G::TCOLS, xa);
-                widen_store<SK>(oB, e, xb0);
-                if (two_b) widen_store<SK>(oB, e + 128, xb1);
+                if (!BT) widen_store<SK>(oB, e, xb0);
+                if (!BT && two_b) widen_store<SK>(oB, e + 128, xb1);
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                fence_async_smem();
+                if (!BT) fence_async_smem();   // the generic-proxy stores, before the MMA reads them
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&op_full[o]);
@@ -1223,23 +1256,26 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
 // The last, a single operand slot, keeps k up to BS_TOPK_K_MAX on the tensor
 // cores at the cost of overlap between widening and MMA.
 // ---------------------------------------------------------------------------
-#define BS_TC_CONFIGS(X)          \
-    X(0, 2, 2, 128, 4, false)     \
-    X(1, 2, 2, 128, 4, true)      \
-    X(2, 4, 2, 64, 8, false)      \
-    X(3, 4, 2, 64, 8, true)       \
-    X(4, 2, 1, 128, 4, false)     \
-    X(5, 2, 2, 128, 6, false)     \
-    X(6, 2, 2, 128, 2, false)     \
-    X(7, 2, 2, 128, 6, true)      \
-    X(8, 2, 1, 128, 2, false)     \
-    X(9, 1, 1, 128, 2, false)
-constexpr int kTcConfigs = 10;
+#define BS_TC_CONFIGS(X)             \
+    X(0, 2, 2, 128, 4, false, 0)     \
+    X(1, 2, 2, 128, 4, true, 0)      \
+    X(2, 4, 2, 64, 8, false, 0)      \
+    X(3, 4, 2, 64, 8, true, 0)       \
+    X(4, 2, 1, 128, 4, false, 0)     \
+    X(5, 2, 2, 128, 6, false, 0)     \
+    X(6, 2, 2, 128, 2, false, 0)     \
+    X(7, 2, 2, 128, 6, true, 0)      \
+    X(8, 2, 1, 128, 2, false, 0)     \
+    X(9, 1, 1, 128, 2, false, 0)     \
+    X(10, 2, 2, 128, 4, false, 3)    \
+    X(11, 2, 2, 128, 4, true, 4)
+constexpr int kTcConfigs = 12;
+constexpr int kTcFirstTma = 10;         // configurations from here on read the FP4 database copy
 constexpr size_t kSmemLimit = 232448;   // 227 KB per block
 
-template <int NOP, int NG, int SK, int RD, bool SH>
+template <int NOP, int NG, int SK, int RD, bool SH, int NB = 0>
 __host__ __device__ constexpr size_t smem_bytes(uint32_t k) {
-    return 1024 + Smem<NOP, NG, SK, RD>::heap + (size_t)(SH ? 1 : NG) * k * BM * 8;
+    return 1024 + Smem<NOP, NG, SK, RD, NB>::heap + (size_t)(SH ? 1 : NG) * k * BM * 8;
 }
 
 // Launch of one configuration for one measure (defined in the per-measure

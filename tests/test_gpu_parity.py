@@ -257,7 +257,7 @@ def test_topk_tc_dense_and_saturated(N, by, m):
             check_topk_row(s[q], ix[q], oest[m, q], 30, m, exclude_q=q)
 
 
-@pytest.mark.parametrize("cfg", range(10))
+@pytest.mark.parametrize("cfg", range(B.BS_TC_CONFIGS))
 @pytest.mark.parametrize("N,by,k", [(1024, "js", 50), (4096, "ham", 20), (256, "cos", 100), (2048, "ip", 1)])
 def test_topk_tc_block_configurations_agree(cfg, N, by, k):
     # every operand-slot width / ring depth / epilogue split gives the same
@@ -276,6 +276,30 @@ def test_topk_tc_block_configurations_agree(cfg, N, by, k):
     except B.BinSketchError as e:
         assert e.code == 7     # this configuration's heaps do not fit k
         return
+    assert B.bs_get_async_error() == 0
+    assert torch.equal(i, ref_i) and torch.equal(s, ref_s)
+
+
+@pytest.mark.parametrize("cfg", range(B.BS_TC_FIRST_TMA, B.BS_TC_CONFIGS))
+@pytest.mark.parametrize("N,by", [(384, "js"), (640, "ip"), (8192, "cos")])
+def test_topk_tma_database_operand_ragged(cfg, N, by):
+    # the configurations that read the FP4 database copy by TMA: a database
+    # whose rows end inside a 208-row tile (rows past the end arrive as zeros)
+    # and N with an odd number of 128-bit chunks (the last 256-bit slot is
+    # half outside the row); queries against another matrix, no self pair --
+    # bit for bit the CUDA-core kernel's lists
+    k = 20
+    qc = inputs.random_csr(31, 300, 300_000, 1, 400)
+    dc = inputs.random_csr(32, 1000, 300_000, 1, 400)
+    qs, qp = _gpu_sketch(qc, N, 4)
+    ds, dp = _gpu_sketch(dc, N, 4)
+    ref_s, ref_i = api.topk(qs, qp, ds, dp, N, k, by=by, variant="popc")
+    s = torch.empty((qc.n, k), dtype=torch.float32, device="cuda")
+    i = torch.empty((qc.n, k), dtype=torch.int32, device="cuda")
+    wsb = B.bs_topk_workspace_bytes(qc.n, dc.n, N, k)
+    ws = torch.empty((wsb,), dtype=torch.uint8, device="cuda")
+    B.bs_topk_ex(qs, qp, qc.n, ds, dp, dc.n, N, B.MEASURE_BITS[by], k, 0, s, i, ws, wsb,
+                 B.BS_VARIANT_TC | B.BS_VARIANT_TC_CFG(cfg))
     assert B.bs_get_async_error() == 0
     assert torch.equal(i, ref_i) and torch.equal(s, ref_s)
 
