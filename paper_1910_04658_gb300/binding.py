@@ -20,15 +20,15 @@ LIB_PATH = os.path.join(PKG, "_build", "libbinsketch.so")
 
 BS_IP, BS_HAM, BS_JS, BS_COS = 1, 2, 4, 8
 BS_VARIANT_AUTO, BS_VARIANT_POPC, BS_VARIANT_TC = 0, 1, 2
-VARIANTS = {"auto": 0, "popc": 1, "tc": 2}   # plus "tc0" .. "tc11" below
+VARIANTS = {"auto": 0, "popc": 1, "tc": 2}   # plus "tc0" .. "tc14" below
 
 
-BS_TC_CONFIGS = 12
+BS_TC_CONFIGS = 15
 BS_TC_FIRST_TMA = 10   # configurations from here on read an FP4 copy of the database by TMA
 
 
 def BS_VARIANT_TC_CFG(c: int) -> int:
-    """Bits selecting tensor-core block configuration c (0..11) in bs_topk_ex's variant."""
+    """Bits selecting tensor-core block configuration c (0..14) in bs_topk_ex's variant."""
     return (c + 1) << 4
 
 

@@ -309,15 +309,16 @@ size_t tc_tiled_bytes(uint32_t n, uint32_t N, uint32_t R);
 size_t tc_fp4_bytes(uint32_t n, uint32_t N);
 // tensor-core block configurations: BS_VARIANT_TC_CFG(c), 0 <= c < kTcConfigCount;
 // c >= kTcFirstTmaCfg read the database operand from the FP4 copy by TMA
-constexpr int kTcConfigCount = 12, kTcFirstTmaCfg = 10;
+// (those with no widening warps the query operand too, from an FP4 copy of Q)
+constexpr int kTcConfigCount = 15, kTcFirstTmaCfg = 10;
 // wait budget of the tensor-core kernel's bounded waits (cycles), and the
 // shortened budget of a fault-injected call
 constexpr long long kTcWaitLimit = kWaitLimitCycles;
 constexpr long long kTcInjectWaitLimit = 2000000ll;
-// tiled: scratch for the tiled copies, tc_tiled_bytes(nQ, N, 128) rounded up
-// to 256 bytes, then the larger of tc_tiled_bytes(nDB, N, 208) and
-// tc_fp4_bytes(nDB, N) (the second part unused when db_tiled, a database kept
-// tiled by bs_tile_sketches, is given)
+// tiled: scratch for the operand copies, the larger of tc_tiled_bytes(nQ, N,
+// 128) and tc_fp4_bytes(nQ, N) rounded up to 256 bytes, then the larger of
+// tc_tiled_bytes(nDB, N, 208) and tc_fp4_bytes(nDB, N) (the second part
+// unused when db_tiled, a database kept tiled by bs_tile_sketches, is given)
 // inject: test-only fault injection (0 = none, 1 = the MMA issuer never
 // announces its first accumulator; waits give up after kTcInjectWaitLimit)
 bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,

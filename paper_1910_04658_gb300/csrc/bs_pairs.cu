@@ -634,8 +634,9 @@ bs_status bs_estimate_pairs(const uint32_t *A, const uint32_t *pcA, uint32_t nA,
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static size_t tc_workspace(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, uint32_t splits) {
+    const size_t q = std::max(tc_tiled_bytes(nQ, N, kTcQueryRows), tc_fp4_bytes(nQ, N));
     const size_t db = std::max(tc_tiled_bytes(nDB, N, kTcTileRows), tc_fp4_bytes(nDB, N));
-    return align256(ws_bytes(splits, nQ, k)) + align256(tc_tiled_bytes(nQ, N, kTcQueryRows)) + align256(db);
+    return align256(ws_bytes(splits, nQ, k)) + align256(q) + align256(db);
 }
 
 size_t bs_topk_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k) {

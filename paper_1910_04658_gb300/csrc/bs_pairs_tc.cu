@@ -204,16 +204,17 @@ __global__ void __launch_bounds__(256) widen_fp4_kernel(const uint4 *__restrict_
 }
 
 // 2-D tensor map over the FP4 copy [rows][N / 2 bytes]: boxes of one 256-bit
-// operand slot (128 bytes) x BN rows with the 128-byte swizzle, so a box lands
+// operand slot (128 bytes) x box_rows rows (BN for a database tile, BM for a
+// query block) with the 128-byte swizzle, so a box lands
 // in the layout the MMA's database descriptors read; rows past the end and
 // the second half of a last 128-bit slot arrive as zeros.  N % 128 == 0 makes
 // the row pitch a multiple of 64 bytes.
-static bool make_map_fp4(CUtensorMap *m, const void *ptr, uint32_t rows, uint32_t N) {
+static bool make_map_fp4(CUtensorMap *m, const void *ptr, uint32_t rows, uint32_t N, uint32_t box_rows) {
     EncodeTiledFn enc = encode_tiled();
     if (!enc || rows == 0) return false;
     cuuint64_t dims[2] = {N / 2, rows};
     cuuint64_t strides[1] = {(cuuint64_t)(N / 2)};
-    cuuint32_t box[2] = {128, BN};
+    cuuint32_t box[2] = {128, box_rows};
     cuuint32_t estr[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(ptr), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -241,13 +242,28 @@ bool tc_cfg_fits(int cfg, uint32_t k) { return tc_cfg_smem(cfg, k) <= tc::kSmemL
 static_assert(tc::kTcConfigs == kTcConfigCount && tc::kTcFirstTma == kTcFirstTmaCfg, "configuration table");
 bool tc_cfg_tma(int cfg) { return cfg >= tc::kTcFirstTma; }
 
+// configurations with no widening warps: the query operand by TMA as well
+static bool tc_cfg_query_tma(int cfg) {
+    switch (cfg) {
+#define X(c, nop, ng, sk, rd, sh, nb) \
+    case c: return nop == 0;
+        BS_TC_CONFIGS(X)
+#undef X
+    }
+    return false;
+}
+
 // default: where the call may build the FP4 database copy (one problem, the
 // database not kept tiled by the caller), the first TMA configuration that
 // fits; otherwise the first configuration in table order that fits -- deeper
 // operand rings and two epilogue groups first
 int tc_default_cfg(uint32_t k, bool allow_tma) {
+    // measured order on the 100,000-row all-pairs top-50: both operands by
+    // TMA with three epilogue groups first
+    static const int tma_order[] = {12, 13, 14, 10, 11};
+    static_assert(sizeof(tma_order) / sizeof(tma_order[0]) == tc::kTcConfigs - tc::kTcFirstTma, "TMA order");
     if (allow_tma)
-        for (int c = tc::kTcFirstTma; c < tc::kTcConfigs; ++c)
+        for (int c : tma_order)
             if (tc_cfg_fits(c, k)) return c;
     for (int c = 0; c < tc::kTcFirstTma; ++c)
         if (tc_cfg_fits(c, k)) return c;
@@ -311,29 +327,39 @@ bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uin
     const int cfg = cfg_req >= 0 ? cfg_req : tc_default_cfg(k, db_tiled == nullptr);
     if (cfg < 0 || !tc_cfg_fits(cfg, k)) return BS_ERR_UNSUPPORTED;
     const bool fp4_db = tc_cfg_tma(cfg);
+    const bool fp4_q = tc_cfg_query_tma(cfg);
     if (fp4_db && db_tiled) return BS_ERR_UNSUPPORTED;   // a kept tiled database has no FP4 copy
     static thread_local tc::Args<1> p;   // ~2 KB of launch arguments, rebuilt per call
     memset(&p, 0, sizeof(p));
     // k-chunk-tiled copies: Q in 128-row blocks, DB in 208-row blocks (none for
     // DB when the caller keeps it tiled, or the FP4 copy for the TMA configurations)
+    auto widen = [&](const uint32_t *src, uint32_t rows, uint4 *dst) {
+        const size_t chunks = (size_t)rows * (N / 128);
+        const uint32_t blocks = (uint32_t)std::min<size_t>((chunks + 255) / 256, (size_t)sm_count() * 16);
+        if (chunks == 0) return true;
+        tc::widen_fp4_kernel<<<blocks, 256, 0, stream>>>(reinterpret_cast<const uint4 *>(src), chunks, dst);
+        return cudaGetLastError() == cudaSuccess;
+    };
     uint4 *tQ = reinterpret_cast<uint4 *>(tiled);
-    if (tile_sketches(Q, nQ, N, tc::BM, tQ, stream) != BS_OK) return BS_ERR_CUDA;
+    const size_t q_bytes = std::max(tc_tiled_bytes(nQ, N, tc::BM), tc_fp4_bytes(nQ, N));
+    uint4 *db_area = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(tiled) + ((q_bytes + 255) & ~(size_t)255));
+    // the query operand: its FP4 copy (all-pairs: the database's copy serves both)
+    // or its k-chunk tiles
+    const bool same = Q == DB && nQ == nDB;
+    if (fp4_q) {
+        if (!same && !widen(Q, nQ, tQ)) return BS_ERR_CUDA;
+    } else if (tile_sketches(Q, nQ, N, tc::BM, tQ, stream) != BS_OK) {
+        return BS_ERR_CUDA;
+    }
     const uint4 *tDB = reinterpret_cast<const uint4 *>(db_tiled);
     if (fp4_db) {
-        uint4 *w = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(tiled) +
-                                             ((tc_tiled_bytes(nQ, N, tc::BM) + 255) & ~(size_t)255));
-        const size_t chunks = (size_t)nDB * (N / 128);
-        const uint32_t blocks = (uint32_t)std::min<size_t>((chunks + 255) / 256, (size_t)sm_count() * 16);
-        if (chunks > 0) {
-            tc::widen_fp4_kernel<<<blocks, 256, 0, stream>>>(reinterpret_cast<const uint4 *>(DB), chunks, w);
-            if (cudaGetLastError() != cudaSuccess) return BS_ERR_CUDA;
-        }
-        if (!tc::make_map_fp4(&p.maps[1], w, nDB, N)) return BS_ERR_CUDA;
+        if (!widen(DB, nDB, db_area)) return BS_ERR_CUDA;
+        if (!tc::make_map_fp4(&p.maps[1], db_area, nDB, N, tc::BN)) return BS_ERR_CUDA;
+        if (fp4_q && !tc::make_map_fp4(&p.maps[0], same ? (const void *)db_area : (const void *)tQ, nQ, N, tc::BM))
+            return BS_ERR_CUDA;
     } else if (!db_tiled) {
-        uint4 *t = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(tiled) +
-                                             ((tc_tiled_bytes(nQ, N, tc::BM) + 255) & ~(size_t)255));
-        if (tile_sketches(DB, nDB, N, tc::BN, t, stream) != BS_OK) return BS_ERR_CUDA;
-        tDB = t;
+        if (tile_sketches(DB, nDB, N, tc::BN, db_area, stream) != BS_OK) return BS_ERR_CUDA;
+        tDB = db_area;
     }
     tc::Job &J = p.job[0];
     tc::fill_job(J, pcQ, pcDB, nQ, nDB, N);

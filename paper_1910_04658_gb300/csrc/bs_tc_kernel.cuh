@@ -75,8 +75,10 @@ constexpr int IR = 8;                      // dynamic schedule: row blocks publi
 constexpr uint32_t ITEM_END = 0xFFFFFFFFu; // no row block left
 enum { INJECT_NONE = 0, INJECT_STALL = 1 };
 
-// threads per block with NG epilogue groups
-__host__ __device__ constexpr int threads_for(int NG) { return 32 * (6 + 4 * NG); }
+// threads per block with NG epilogue groups: MMA warp, producer warp, 4
+// widening warps (none when both operands arrive by TMA), the epilogue groups
+__host__ __device__ constexpr int epi_warp0(bool widen) { return widen ? 6 : 2; }
+__host__ __device__ constexpr int threads_for(int NG, bool widen = true) { return 32 * (epi_warp0(widen) + 4 * NG); }
 
 // Operand slot geometry for SK bytes of K per row: one FP4 byte holds two
 // sketch bits, so a slot covers 2 SK bits -- SK = 128: 256 bits (two 128-bit
@@ -124,19 +126,24 @@ constexpr float LOG2_FILTER_SLACK = -1.76126e-4f;   // log2(FILTER_SLACK), folde
 // Shared-memory layout for NOP operand slots and RD raw slots of SK bytes
 // per row and NG epilogue groups (offsets from the 1024-aligned base); the
 // heaps follow.
-template <int NOP, int NG, int SK, int RD, int NB = 0>
+template <int NOP, int NG, int SK, int RD, int NB = 0, bool SH = false>
 struct Smem {
     static_assert(NOP * Geo<SK>::TCOLS <= (int)(SF_COL - A_COL), "query operand slots exceed their TMEM columns");
+    // NOP = 0: NB stages of both operands, filled by TMA from the FP4 copies
+    // (query block BM x SK bytes, then database tile BN x SK bytes);
     // NB > 0: NB database slots filled by TMA from the FP4 copy, raw slots hold
     // the query operand only; NB = 0: NOP database slots the widening warps fill
+    static constexpr int ABYTES = BM * SK;
+    static constexpr int STAGE = ABYTES + Geo<SK>::BYTES;
+    static_assert(ABYTES % 1024 == 0 && STAGE % 1024 == 0, "stage alignment");
     static constexpr int op = 0;
-    static constexpr int raw = op + (NB > 0 ? NB : NOP) * Geo<SK>::BYTES;
+    static constexpr int raw = op + (NOP == 0 ? NB * STAGE : (NB > 0 ? NB : NOP) * Geo<SK>::BYTES);
     static constexpr int col = raw + RD * (NB > 0 ? Geo<SK>::RAW_A : Geo<SK>::RAW_SLOT);   // [2 tiles][3][BNP] floats
     static constexpr int bars = col + 2 * 3 * BNP * 4;
     static constexpr int thr = bars + 512;                      // [NG][BM] key, idx, size
     static constexpr int lock = thr + NG * BM * 12;             // [BM] shared-heap row locks
-    static constexpr int cbuf = lock + BM * 4;                  // [NG][CB][BM] admitted pairs
-    static constexpr int heap = cbuf + NG * CB * BM * 4;
+    static constexpr int cbuf = lock + BM * 4;                  // [NG][CB][BM] admitted pairs (per-group heaps)
+    static constexpr int heap = cbuf + (SH ? 0 : NG * CB * BM * 4);
     static_assert((2 * NOP + 2 * RD + 2 * NB + 5 + 2 * IR) * 8 + 8 + 4 * IR <= 512, "barrier area");
 };
 
@@ -199,6 +206,16 @@ __device__ __forceinline__ void mma_fp4(uint32_t d_tmem, uint32_t a_tmem, uint64
         "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], [%1], %2, %3, [%5], [%6], p;\n\t}\n" ::"r"(
             d_tmem),
         "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate), "r"(sfa), "r"(sfb)
+        : "memory");
+}
+// the same with the query operand in shared memory too (descriptor adesc)
+__device__ __forceinline__ void mma_fp4_ss(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t sfa, uint32_t sfb, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%5], [%6], p;\n\t}\n" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "r"(sfa), "r"(sfb)
         : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
@@ -644,15 +661,23 @@ __device__ __forceinline__ uint32_t block_of(const Args<NJ> &p, uint64_t x, uint
 }
 
 template <int MODE, int M, int NOP, int NG, int SK, int RD, bool SHARED, int NJ, int NB = 0>
-__global__ void __launch_bounds__(threads_for(NG), 1)
+__global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
     pair_tc_kernel(const __grid_constant__ Args<NJ> p) {
-    using Smem = tc::Smem<NOP, NG, SK, RD, NB>;
+    using Smem = tc::Smem<NOP, NG, SK, RD, NB, SHARED>;
     using G = Geo<SK>;
     // BT: the database operand arrives already widened, by TMA from an FP4
     // copy in global memory (tensor map p.maps[1], 128-byte swizzle), into NB
-    // shared-memory slots; the widening warps write only the query operand
+    // shared-memory slots; the widening warps write only the query operand.
+    // AT (NOP = 0): the query operand too (tensor map p.maps[0], 128-row
+    // boxes): NB stages of both operands, no widening warps, the MMA reads
+    // both from shared memory
     constexpr bool BT = NB > 0;
+    constexpr bool AT = NOP == 0;
+    constexpr int EPI0 = epi_warp0(!AT);   // first epilogue warp
     static_assert(!BT || (MODE == MODE_TOPK && NJ == 1 && SK == 128), "TMA database operand: one top-k problem");
+    static_assert(!AT || (BT && RD == 0), "TMA query operand: stages of both operands");
+    static_assert(NG <= 2 || SHARED, "three epilogue groups share one heap per row");
+    constexpr uint32_t NOPS = NOP > 0 ? NOP : 1, RDS = RD > 0 ? RD : 1, NBS = NB > 0 ? NB : 1;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -733,7 +758,7 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     // unit block scales (all 128 lanes of columns SF_COL ..) before any MMA
-    if (warp >= 6 && warp < 10) tmem_fill32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + SF_COL, UNIT_SCALES);
+    if (warp >= EPI0 && warp < EPI0 + 4) tmem_fill32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + SF_COL, UNIT_SCALES);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -761,20 +786,29 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + ab * BN;
                 for (uint32_t c = 0; c < nsl; ++c, ++sl) {
-                    const uint32_t o = sl % NOP;
-                    const uint32_t ob = BT ? sl % (NB > 0 ? NB : 1) : o;   // database slot
-                    wait(&op_full[o], (sl / NOP) & 1);
-                    if (BT) wait(&b_full[ob], (sl / (NB > 0 ? NB : 1)) & 1);
+                    const uint32_t o = sl % NOPS;
+                    const uint32_t ob = BT ? sl % NBS : o;   // database slot (AT: stage)
+                    if (!AT) wait(&op_full[o], (sl / NOPS) & 1);
+                    if (BT) wait(&b_full[ob], (sl / NBS) & 1);
                     tc_fence_after();
                     if (!*abort_flag) {
-                        const uint32_t a_tmem = tmem + A_COL + o * G::TCOLS;
-                        const uint32_t b_addr = smem_u32(op + ob * G::BYTES);
+                        if (AT) {
+                            const uint32_t a_addr = smem_u32(op + ob * Smem::STAGE);
+                            const uint32_t b_addr = a_addr + Smem::ABYTES;
 #pragma unroll
-                        for (int kk = 0; kk < G::MMAS; ++kk)
-                            mma_fp4(d_tmem, a_tmem + 8 * kk, sw_desc<SK>(b_addr + kk * 32), IDESC, sfa, sfb,
-                                    (c | (uint32_t)kk) != 0);
+                            for (int kk = 0; kk < G::MMAS; ++kk)
+                                mma_fp4_ss(d_tmem, sw_desc<SK>(a_addr + kk * 32), sw_desc<SK>(b_addr + kk * 32),
+                                           IDESC, sfa, sfb, (c | (uint32_t)kk) != 0);
+                        } else {
+                            const uint32_t a_tmem = tmem + A_COL + o * G::TCOLS;
+                            const uint32_t b_addr = smem_u32(op + ob * G::BYTES);
+#pragma unroll
+                            for (int kk = 0; kk < G::MMAS; ++kk)
+                                mma_fp4(d_tmem, a_tmem + 8 * kk, sw_desc<SK>(b_addr + kk * 32), IDESC, sfa, sfb,
+                                        (c | (uint32_t)kk) != 0);
+                        }
                     }
-                    mma_commit(&op_empty[o]);
+                    if (!AT) mma_commit(&op_empty[o]);
                     if (BT) mma_commit(&b_empty[ob]);
                 }
                 // fault injection (tests only): the first accumulator is never
@@ -789,15 +823,25 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
         // ----------------------------- TMA producer -----------------------------
         if (lane == 0) {
             uint32_t rs = 0;   // raw slots issued
-            uint32_t bs = 0;   // TMA database slots issued
-            constexpr int NBS = NB > 0 ? NB : 1;
+            uint32_t bs = 0;   // TMA database slots (AT: stages) issued
             // the raw slots of one tile
             auto issue_tile = [&](const Job &J, uint32_t rb, uint32_t tile) {
                 const uint32_t nKc = J.nKc;
                 const uint32_t nsl = slots_per_tile<SK>(nKc);
                 for (uint32_t c = 0; c < nsl; ++c) {
-                    const uint32_t o = rs % RD;
-                    if (rs >= RD) wait(&raw_empty[o], ((rs / RD) - 1) & 1);
+                    if (AT) {   // one stage: the query block's and the database tile's slot, both by TMA
+                        const uint32_t ob = bs % NBS;
+                        if (bs >= (uint32_t)NBS) wait(&b_empty[ob], ((bs / NBS) - 1) & 1);
+                        if (*abort_flag) return;
+                        uint8_t *dst = op + ob * Smem::STAGE;
+                        mbar_arrive_expect_tx(&b_full[ob], Smem::STAGE);
+                        tma_load_2d(dst, &p.maps[0], &b_full[ob], (int)(c * SK), (int)(rb * BM));
+                        tma_load_2d(dst + Smem::ABYTES, &p.maps[1], &b_full[ob], (int)(c * SK), (int)(tile * BN));
+                        ++bs;
+                        continue;
+                    }
+                    const uint32_t o = rs % RDS;
+                    if (rs >= RDS) wait(&raw_empty[o], ((rs / RDS) - 1) & 1);
                     if (*abort_flag) return;
                     uint8_t *dst = raw + o * (BT ? G::RAW_A : G::RAW_SLOT);
                     if (BT) {   // the query operand's packed bits; the widened database tile by TMA
@@ -855,12 +899,12 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                 while (seq.next(wait, abort_flag) && !*abort_flag) issue_tile(jobs[seq.j], seq.rb, seq.tile);
             }
             // every copy issued here has landed before the block may exit
-            for (uint32_t i = rs > (uint32_t)RD ? rs - RD : 0; i < rs; ++i)
-                if (!mbar_wait(&raw_full[i % RD], (i / RD) & 1, p.wait_limit)) raise_error(p.err, BS_ERR_TIMEOUT);
+            for (uint32_t i = rs > RDS ? rs - RDS : 0; i < rs; ++i)
+                if (!mbar_wait(&raw_full[i % RDS], (i / RDS) & 1, p.wait_limit)) raise_error(p.err, BS_ERR_TIMEOUT);
             for (uint32_t i = bs > (uint32_t)NBS ? bs - NBS : 0; i < bs; ++i)
                 if (!mbar_wait(&b_full[i % NBS], (i / NBS) & 1, p.wait_limit)) raise_error(p.err, BS_ERR_TIMEOUT);
         }
-    } else if (warp < 6) {
+    } else if (!AT && warp < 6) {
         // ------------------------------ widening ------------------------------
         // thread e owns query row e -- the row of its warp's TMEM lane quarter --
         // and database rows e and e + 128 of a slot
@@ -875,8 +919,8 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
             const uint32_t nKc = jobs[seq.j].nKc;
             const uint32_t nsl = slots_per_tile<SK>(nKc);
             for (uint32_t c = 0; c < nsl; ++c, ++sl) {
-                const uint32_t ro = sl % RD, o = sl % NOP;
-                wait(&raw_full[ro], (sl / RD) & 1);
+                const uint32_t ro = sl % RDS, o = sl % NOPS;
+                wait(&raw_full[ro], (sl / RDS) & 1);
                 const uint8_t *src = raw + ro * (BT ? G::RAW_A : G::RAW_SLOT);
                 uint32_t xa[G::WPS], xb0[G::WPS], xb1[G::WPS];
                 if (MODE == MODE_STORE) {
@@ -891,7 +935,7 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&raw_empty[ro]);   // the raw slot may be refilled
-                if (sl >= (uint32_t)NOP) wait(&op_empty[o], ((sl / NOP) - 1) & 1);
+                if (sl >= NOPS) wait(&op_empty[o], ((sl / NOPS) - 1) & 1);
                 uint8_t *oB = op + o * G::BYTES;
                 widen_tmem<SK>(a_lane + o * G::TCOLS, xa);
                 if (!BT) widen_store<SK>(oB, e, xb0);
@@ -905,15 +949,16 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
         }
     } else {
         // ------------------------------ epilogue ------------------------------
-        const int grp = (warp - 6) >> 2;           // epilogue group
-        const int e = tid - 192 - 128 * grp;       // 0..127 within the group
+        const int grp = (warp - EPI0) >> 2;        // epilogue group
+        const int e = tid - 32 * EPI0 - 128 * grp; // 0..127 within the group
         const int quarter = warp & 3;              // TMEM lanes this warp may access
         const int r = quarter * 32 + lane;         // row within the block
         // tile columns of this group
-        // (two groups: 96 and 112 of the 208 columns -- the most even split
-        // whose 32-column TMEM loads all start at a multiple of 32)
-        const int c_lo = NG == 1 ? 0 : grp * GSPLIT;
-        const int c_hi = (NG == 1 || grp == 1) ? BN : GSPLIT;
+        // (two groups: 96 and 112 of the 208 columns, three: 64, 64 and 80 --
+        // the most even splits whose 32-column TMEM loads all start at a
+        // multiple of 32)
+        const int c_lo = NG == 1 ? 0 : (NG == 2 ? grp * GSPLIT : grp * 64);
+        const int c_hi = NG == 1 ? BN : (NG == 2 ? (grp == 1 ? BN : GSPLIT) : (grp == NG - 1 ? BN : (grp + 1) * 64));
         // row constants of the current row block (set at each segment start)
         uint32_t q = 0, a = 0;
         bool row_ok = false;
@@ -977,7 +1022,7 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                     thr_idx[(SHARED ? 0 : grp) * BM + r] = NO_IDX;
                     heap_size[(SHARED ? 0 : grp) * BM + r] = 0;
                 }
-                if (MODE == MODE_TOPK && NG == 2) named_sync(5, 128 * NG);
+                if (MODE == MODE_TOPK && NG >= 2) named_sync(9, 128 * NG);
             }
             float2 *cv = reinterpret_cast<float2 *>(colv + (t & 1) * 3 * BNP);
             // per-column values (raw b, bound term f0) of this group's columns,
@@ -1185,14 +1230,14 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
             }
             // sort each heap best first; with two groups the first merges both lists
             // (shared heap: one list, sorted by the first group once both are done)
-            if (SHARED && NG == 2) named_sync(4, 128 * NG);
+            if (SHARED && NG >= 2) named_sync(8, 128 * NG);
             if (SHARED) st.size = heap_size[r];
             Heap h;
             h.ent = hent; h.t = r; h.size = st.size; h.cap = (int)p.k;
             if (row_ok && (!SHARED || grp == 0)) h.sort_best_first();
             if (!SHARED && NG == 2) {
                 heap_size[grp * BM + r] = st.size;
-                named_sync(4, 128 * NG);
+                named_sync(8, 128 * NG);
             }
             if (grp == 0 && row_ok) {
                 const uint2 *e1 = reinterpret_cast<const uint2 *>(base + Smem::heap) + (size_t)p.k * BM;
@@ -1233,7 +1278,7 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
                 }
             }
             // every heap read of this segment is done before the next one resets them
-            if (NG == 2) named_sync(6, 128 * NG);
+            if (NG >= 2) named_sync(10, 128 * NG);
             if (DYN) {   // this row block is done: its ring entry may be reused
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&item_empty[seq.slot()]);
@@ -1268,14 +1313,17 @@ __global__ void __launch_bounds__(threads_for(NG), 1)
     X(8, 2, 1, 128, 2, false, 0)     \
     X(9, 1, 1, 128, 2, false, 0)     \
     X(10, 2, 2, 128, 4, false, 3)    \
-    X(11, 2, 2, 128, 4, true, 4)
-constexpr int kTcConfigs = 12;
+    X(11, 2, 2, 128, 4, true, 4)     \
+    X(12, 0, 3, 128, 0, true, 3)     \
+    X(13, 0, 3, 128, 0, true, 2)     \
+    X(14, 0, 2, 128, 0, true, 3)
+constexpr int kTcConfigs = 15;
 constexpr int kTcFirstTma = 10;         // configurations from here on read the FP4 database copy
 constexpr size_t kSmemLimit = 232448;   // 227 KB per block
 
 template <int NOP, int NG, int SK, int RD, bool SH, int NB = 0>
 __host__ __device__ constexpr size_t smem_bytes(uint32_t k) {
-    return 1024 + Smem<NOP, NG, SK, RD, NB>::heap + (size_t)(SH ? 1 : NG) * k * BM * 8;
+    return 1024 + Smem<NOP, NG, SK, RD, NB, SH>::heap + (size_t)(SH ? 1 : NG) * k * BM * 8;
 }
 
 // Launch of one configuration for one measure (defined in the per-measure

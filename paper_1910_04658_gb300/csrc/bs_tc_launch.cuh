@@ -26,7 +26,7 @@ cudaError_t launch_topk(int cfg, const Args<NJ> &p, uint32_t grid, cudaStream_t 
     case c:                                                                                            \
         if constexpr (nb == 0 || NJ == 1)                                                              \
             go(pair_tc_kernel<MODE_TOPK, M, nop, ng, sk, rd, sh, NJ, nb>,                              \
-               smem_bytes<nop, ng, sk, rd, sh, nb>(p.k) + jobs_smem, threads_for(ng));                 \
+               smem_bytes<nop, ng, sk, rd, sh, nb>(p.k) + jobs_smem, threads_for(ng, nop > 0));        \
         break;
         BS_TC_CONFIGS(X)
 #undef X

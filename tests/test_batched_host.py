@@ -15,6 +15,6 @@ def test_autotuner_cache_roundtrip(tmp_path):
     assert json.load(open(p)) == {key: 34}
     assert Autotuner(cache_path=str(p)).table == {key: 34}
     cands = Autotuner.candidates()
-    assert [n for n, _ in cands] == ["popc"] + [f"tc{c}" for c in range(12)]
+    assert [n for n, _ in cands] == ["popc"] + [f"tc{c}" for c in range(15)]
     # variant codes: POPC, then TC with configuration bits (c + 1) << 4
-    assert cands[0][1] == 1 and [v for _, v in cands[1:]] == [2 | ((c + 1) << 4) for c in range(12)]
+    assert cands[0][1] == 1 and [v for _, v in cands[1:]] == [2 | ((c + 1) << 4) for c in range(15)]
