@@ -315,17 +315,34 @@ constexpr int kTcConfigCount = 15, kTcFirstTmaCfg = 10;
 // shortened budget of a fault-injected call
 constexpr long long kTcWaitLimit = kWaitLimitCycles;
 constexpr long long kTcInjectWaitLimit = 2000000ll;
-// tiled: scratch for the operand copies, the larger of tc_tiled_bytes(nQ, N,
-// 128) and tc_fp4_bytes(nQ, N) rounded up to 256 bytes, then the larger of
-// tc_tiled_bytes(nDB, N, 208) and tc_fp4_bytes(nDB, N) (the second part
-// unused when db_tiled, a database kept tiled by bs_tile_sketches, is given)
+// The launches of one tensor-core top-k call (host only): the block
+// configuration, which operands go through FP4 copies, the first launch's
+// rounds of whole row blocks (rows [0, q_split)), the partial lists per row of
+// the launch over the remaining rows, the kernels launched and the partial-
+// list bytes the call needs.
+struct TcCallPlan {
+    int cfg = -1;
+    bool fp4_q = false, fp4_db = false;
+    uint32_t rounds = 0, q_split = 0, splits = 1, launches = 0;
+    size_t lists_bytes = 0;
+};
+bs_status tc_call_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, int cfg, bool same, bool pretiled,
+                       TcCallPlan &pl);
+// partial-list bytes that cover the plan of every configuration
+size_t tc_lists_bytes(uint32_t nQ, uint32_t nDB, uint32_t k);
+// lists: lists_bytes of scratch for the partial lists (tc_lists_bytes covers
+// every configuration); tiled: scratch for the operand copies, the larger of
+// tc_tiled_bytes(nQ, N, 128) and tc_fp4_bytes(nQ, N) rounded up to 256 bytes,
+// then the larger of tc_tiled_bytes(nDB, N, 208) and tc_fp4_bytes(nDB, N)
+// (the second part unused when db_tiled, a database kept tiled by
+// bs_tile_sketches, is given); the call merges its partial lists itself.
 // inject: test-only fault injection (0 = none, 1 = the MMA issuer never
 // announces its first accumulator; waits give up after kTcInjectWaitLimit)
 bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
                   const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
-                  int exclude_self, uint32_t self_off, float *score, uint32_t *idx, float *ws_key,
-                  uint32_t *ws_idx, uint32_t splits, void *tiled, const void *db_tiled, int cfg,
-                  uint32_t inject, unsigned int *err, cudaStream_t stream);
+                  int exclude_self, uint32_t self_off, float *score, uint32_t *idx, void *lists,
+                  size_t lists_bytes, void *tiled, const void *db_tiled, int cfg, uint32_t inject,
+                  unsigned int *err, cudaStream_t stream);
 // full count / estimate matrices on the tensor cores (N % 128 == 0, 256 <= N
 // <= 8192, 16-byte aligned A and B), reading the row-major sketches directly
 bool tc_store_supported(const uint32_t *A, const uint32_t *B, uint32_t N);

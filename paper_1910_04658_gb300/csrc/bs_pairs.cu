@@ -633,17 +633,18 @@ bs_status bs_estimate_pairs(const uint32_t *A, const uint32_t *pcA, uint32_t nA,
 // both operands; each part starts on a 256-byte boundary.
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static size_t tc_workspace(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, uint32_t splits) {
+// tensor-core call: [partial lists, every configuration's plan][Q copy][DB copy]
+static size_t tc_workspace(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k) {
     const size_t q = std::max(tc_tiled_bytes(nQ, N, kTcQueryRows), tc_fp4_bytes(nQ, N));
     const size_t db = std::max(tc_tiled_bytes(nDB, N, kTcTileRows), tc_fp4_bytes(nDB, N));
-    return align256(ws_bytes(splits, nQ, k)) + align256(q) + align256(db);
+    return align256(tc_lists_bytes(nQ, nDB, k)) + align256(q) + align256(db);
 }
 
 size_t bs_topk_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k) {
     if (nQ == 0 || nDB == 0 || k == 0) return 0;
     size_t need = ws_bytes(popc_splits(nQ, nDB), nQ, k);
     if (valid_N(N) && tc_shape_ok(N, k)) {
-        const size_t t = tc_workspace(nQ, nDB, N, k, tc_splits(nQ, nDB));
+        const size_t t = tc_workspace(nQ, nDB, N, k);
         if (t > need) need = t;
     }
     return need;
@@ -682,25 +683,27 @@ static bs_status topk_impl(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, 
         use_tc = nDB > 0 && tc_supported(Q, DB, N, k);
     }
     if (inject && !use_tc) return BS_ERR_UNSUPPORTED;   // the injector lives in the tensor-core kernel
-    const uint32_t splits = use_tc ? tc_splits(nQ, nDB) : popc_splits(nQ, nDB);
-    const size_t need = use_tc ? tc_workspace(nQ, nDB, N, k, splits) : ws_bytes(splits, nQ, k);
-    float *ws_key = nullptr;
-    uint32_t *ws_idx = nullptr;
-    void *tiled = nullptr;
-    if (need > 0) {
+    if (use_tc) {   // the tensor-core call plans, launches and merges by itself
+        const size_t lists = tc_lists_bytes(nQ, nDB, k);
+        const size_t need = tc_workspace(nQ, nDB, N, k);
         if (!workspace || workspace_bytes < need) return BS_ERR_NO_MEMORY;
         if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return BS_ERR_INVALID_ARG;
         uint8_t *w = reinterpret_cast<uint8_t *>(workspace);
-        if (splits > 1) {
-            ws_key = reinterpret_cast<float *>(w);
-            ws_idx = reinterpret_cast<uint32_t *>(ws_key + (size_t)splits * nQ * k);
-        }
-        tiled = w + align256(ws_bytes(splits, nQ, k));
+        return topk_tc(Q, pcQ, nQ, DB, pcDB, nDB, N, m, k, exclude_self, self_off, score, idx, w, lists,
+                       w + align256(lists), nullptr, tc_cfg, inject, err, st);
     }
-    bs_status s1 = use_tc ? topk_tc(Q, pcQ, nQ, DB, pcDB, nDB, N, m, k, exclude_self, self_off, score,
-                                    idx, ws_key, ws_idx, splits, tiled, nullptr, tc_cfg, inject, err, st)
-                          : topk_popc(Q, pcQ, nQ, DB, pcDB, nDB, N, m, k, exclude_self, self_off,
-                                      score, idx, ws_key, ws_idx, splits, err, st);
+    const uint32_t splits = popc_splits(nQ, nDB);
+    const size_t need = ws_bytes(splits, nQ, k);
+    float *ws_key = nullptr;
+    uint32_t *ws_idx = nullptr;
+    if (need > 0) {
+        if (!workspace || workspace_bytes < need) return BS_ERR_NO_MEMORY;
+        if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return BS_ERR_INVALID_ARG;
+        ws_key = reinterpret_cast<float *>(workspace);
+        ws_idx = reinterpret_cast<uint32_t *>(ws_key + (size_t)splits * nQ * k);
+    }
+    bs_status s1 = topk_popc(Q, pcQ, nQ, DB, pcDB, nDB, N, m, k, exclude_self, self_off, score, idx,
+                             ws_key, ws_idx, splits, err, st);
     if (s1 != BS_OK || splits <= 1) return s1;
     return launch_merge(m, ws_key, ws_idx, nQ, k, splits, score, idx, st);
 }
@@ -755,12 +758,19 @@ bs_status bs_topk_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, uint32
     } else if (variant == BS_VARIANT_AUTO) {
         tc = nDB > 0 && tc_shape_ok(N, k);
     }
-    const uint32_t s = (nQ == 0) ? 0 : (tc ? tc_splits(nQ, nDB) : popc_splits(nQ, nDB));
-    uint32_t l = 0;
-    // the tensor-core path re-lays out Q (128-row blocks) and DB (208-row
-    // blocks) separately, even when they are the same matrix
-    (void)same_matrix;
-    if (nQ > 0) l = 1 + (s > 1 ? 1 : 0) + (tc ? 2 : 0);
+    uint32_t s = 0, l = 0;
+    if (nQ > 0 && tc) {   // the call plan of the default tensor-core configuration
+        TcCallPlan pl;
+        const int ev = variant == BS_VARIANT_AUTO ? env_variant() : -2;
+        const bs_status ps = tc_call_plan(nQ, nDB, N, k, ev >= 0 && tc_cfg_fits(ev, k) ? ev : -1,
+                                          same_matrix != 0, false, pl);
+        if (ps != BS_OK) return ps;
+        s = pl.splits;
+        l = pl.launches;
+    } else if (nQ > 0) {
+        s = popc_splits(nQ, nDB);
+        l = 1 + (s > 1 ? 1 : 0);
+    }
     if (uses_tc) *uses_tc = tc ? 1 : 0;
     if (splits) *splits = s;
     if (launches) *launches = l;
@@ -785,7 +795,7 @@ bs_status bs_tile_sketches(const uint32_t *sketch, uint32_t n_rows, uint32_t N, 
 
 size_t bs_topk_pretiled_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k) {
     if (nQ == 0 || nDB == 0 || !valid_N(N) || !tc_shape_ok(N, k)) return 0;
-    return align256(ws_bytes(tc_splits(nQ, nDB), nQ, k)) + align256(tc_tiled_bytes(nQ, N, kTcQueryRows));
+    return align256(tc_lists_bytes(nQ, nDB, k)) + align256(tc_tiled_bytes(nQ, N, kTcQueryRows));
 }
 
 bs_status bs_topk_pretiled(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const void *DB_tiled,
@@ -805,22 +815,13 @@ bs_status bs_topk_pretiled(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, 
     unsigned int *err = error_word();
     if (!err) return BS_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
-    const uint32_t splits = tc_splits(nQ, nDB);
-    const size_t need = align256(ws_bytes(splits, nQ, k)) + align256(tc_tiled_bytes(nQ, N, kTcQueryRows));
+    const size_t lists = tc_lists_bytes(nQ, nDB, k);
+    const size_t need = align256(lists) + align256(tc_tiled_bytes(nQ, N, kTcQueryRows));
     if (!workspace || workspace_bytes < need) return BS_ERR_NO_MEMORY;
     if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return BS_ERR_INVALID_ARG;
     uint8_t *w = reinterpret_cast<uint8_t *>(workspace);
-    float *ws_key = nullptr;
-    uint32_t *ws_idx = nullptr;
-    if (splits > 1) {
-        ws_key = reinterpret_cast<float *>(w);
-        ws_idx = reinterpret_cast<uint32_t *>(ws_key + (size_t)splits * nQ * k);
-    }
-    void *tiled = w + align256(ws_bytes(splits, nQ, k));
-    bs_status s1 = topk_tc(Q, pcQ, nQ, nullptr, pcDB, nDB, N, m, k, 0, 0, score, idx, ws_key,
-                           ws_idx, splits, tiled, DB_tiled, -1, 0, err, st);
-    if (s1 != BS_OK || splits <= 1) return s1;
-    return launch_merge(m, ws_key, ws_idx, nQ, k, splits, score, idx, st);
+    return topk_tc(Q, pcQ, nQ, nullptr, pcDB, nDB, N, m, k, 0, 0, score, idx, w, lists, w + align256(lists),
+                   DB_tiled, -1, 0, err, st);
 }
 
 size_t bs_topk_batched_workspace_bytes(const bs_topk_job *jobs, uint32_t n_jobs, uint32_t k) {

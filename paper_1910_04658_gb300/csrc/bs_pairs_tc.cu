@@ -319,20 +319,63 @@ static cudaError_t launch_measure(int measure, int cfg, const tc::Args<NJ> &p, u
     }
 }
 
+// The launches of one tensor-core top-k call.  With the FP4 database copy
+// (configurations 10..14) every query block streams the whole copy, which is
+// larger than L2, so the first launch deals whole row blocks out in rounds --
+// block c takes row blocks [c R, (c + 1) R) -- and all blocks sweep the
+// database tiles in the same order at the same time, reading each tile from
+// L2 while it is hot; the rows left over (fewer than one per block) run as a
+// second launch with the balanced ranges and partial lists of the usual
+// schedule.  Otherwise one launch with the balanced ranges.
+bs_status tc_call_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, int cfg_req, bool same,
+                       bool pretiled, TcCallPlan &pl) {
+    pl = TcCallPlan();
+    pl.cfg = cfg_req >= 0 ? cfg_req : tc_default_cfg(k, !pretiled);
+    if (pl.cfg < 0 || !tc_cfg_fits(pl.cfg, k)) return BS_ERR_UNSUPPORTED;
+    pl.fp4_db = tc_cfg_tma(pl.cfg);
+    pl.fp4_q = tc_cfg_query_tma(pl.cfg);
+    if (pl.fp4_db && pretiled) return BS_ERR_UNSUPPORTED;   // a kept tiled database has no FP4 copy
+    if (nQ == 0 || nDB == 0) return BS_OK;
+    const uint32_t rbs = (nQ + tc::BM - 1) / tc::BM;
+    const uint32_t G = tc::max_blocks();
+    pl.rounds = pl.fp4_db ? rbs / G : 0;
+    pl.q_split = (uint32_t)std::min<uint64_t>(nQ, (uint64_t)pl.rounds * G * tc::BM);
+    const uint32_t nQ2 = nQ - pl.q_split;
+    pl.splits = nQ2 > 0 ? tc_splits(nQ2, nDB) : 1;
+    pl.lists_bytes = pl.splits > 1 ? (size_t)pl.splits * nQ2 * k * 8 : 0;
+    pl.launches = (pl.fp4_db ? 1 : (pretiled ? 0 : 1)) + (pl.fp4_q ? (same ? 0 : 1) : 1) +
+                  (pl.rounds > 0 ? 1 : 0) + (nQ2 > 0 ? 1 : 0) + (pl.splits > 1 ? 1 : 0);
+    return BS_OK;
+}
+
+// partial-list bytes that cover the call plan of every configuration
+size_t tc_lists_bytes(uint32_t nQ, uint32_t nDB, uint32_t k) {
+    if (nQ == 0 || nDB == 0) return 0;
+    const uint32_t s = tc_splits(nQ, nDB);
+    size_t b = s > 1 ? (size_t)s * nQ * k * 8 : 0;
+    TcCallPlan pl;
+    for (int c = tc::kTcFirstTma; c < tc::kTcConfigs; ++c)
+        if (tc_cfg_fits(c, k) && tc_call_plan(nQ, nDB, 256, k, c, false, false, pl) == BS_OK)
+            b = std::max(b, pl.lists_bytes);
+    return b;
+}
+
 bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
                   const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
-                  int exclude_self, uint32_t self_off, float *score, uint32_t *idx, float *ws_key,
-                  uint32_t *ws_idx, uint32_t splits, void *tiled, const void *db_tiled, int cfg_req,
-                  uint32_t inject, unsigned int *err, cudaStream_t stream) {
-    const int cfg = cfg_req >= 0 ? cfg_req : tc_default_cfg(k, db_tiled == nullptr);
-    if (cfg < 0 || !tc_cfg_fits(cfg, k)) return BS_ERR_UNSUPPORTED;
-    const bool fp4_db = tc_cfg_tma(cfg);
-    const bool fp4_q = tc_cfg_query_tma(cfg);
-    if (fp4_db && db_tiled) return BS_ERR_UNSUPPORTED;   // a kept tiled database has no FP4 copy
-    static thread_local tc::Args<1> p;   // ~2 KB of launch arguments, rebuilt per call
-    memset(&p, 0, sizeof(p));
-    // k-chunk-tiled copies: Q in 128-row blocks, DB in 208-row blocks (none for
-    // DB when the caller keeps it tiled, or the FP4 copy for the TMA configurations)
+                  int exclude_self, uint32_t self_off, float *score, uint32_t *idx, void *lists,
+                  size_t lists_bytes, void *tiled, const void *db_tiled, int cfg_req, uint32_t inject,
+                  unsigned int *err, cudaStream_t stream) {
+    const bool same = Q == DB && nQ == nDB;
+    TcCallPlan pl;
+    const bs_status ps = tc_call_plan(nQ, nDB, N, k, cfg_req, same, db_tiled != nullptr, pl);
+    if (ps != BS_OK) return ps;
+    if (nQ == 0 || nDB == 0) return BS_OK;
+    if (pl.lists_bytes > lists_bytes || (pl.lists_bytes > 0 && !lists)) return BS_ERR_NO_MEMORY;
+    const int cfg = pl.cfg;
+    static thread_local tc::Args<1> p;   // ~2 KB of launch arguments, rebuilt per launch
+    // operand copies: the FP4 copies for the TMA configurations (all-pairs: the
+    // database's copy serves as the query operand too), else k-chunk tiles --
+    // Q in 128-row, DB in 208-row blocks (none for DB when the caller keeps it tiled)
     auto widen = [&](const uint32_t *src, uint32_t rows, uint4 *dst) {
         const size_t chunks = (size_t)rows * (N / 128);
         const uint32_t blocks = (uint32_t)std::min<size_t>((chunks + 255) / 256, (size_t)sm_count() * 16);
@@ -343,43 +386,67 @@ bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uin
     uint4 *tQ = reinterpret_cast<uint4 *>(tiled);
     const size_t q_bytes = std::max(tc_tiled_bytes(nQ, N, tc::BM), tc_fp4_bytes(nQ, N));
     uint4 *db_area = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(tiled) + ((q_bytes + 255) & ~(size_t)255));
-    // the query operand: its FP4 copy (all-pairs: the database's copy serves both)
-    // or its k-chunk tiles
-    const bool same = Q == DB && nQ == nDB;
-    if (fp4_q) {
+    if (pl.fp4_q) {
         if (!same && !widen(Q, nQ, tQ)) return BS_ERR_CUDA;
     } else if (tile_sketches(Q, nQ, N, tc::BM, tQ, stream) != BS_OK) {
         return BS_ERR_CUDA;
     }
     const uint4 *tDB = reinterpret_cast<const uint4 *>(db_tiled);
-    if (fp4_db) {
+    if (pl.fp4_db) {
         if (!widen(DB, nDB, db_area)) return BS_ERR_CUDA;
-        if (!tc::make_map_fp4(&p.maps[1], db_area, nDB, N, tc::BN)) return BS_ERR_CUDA;
-        if (fp4_q && !tc::make_map_fp4(&p.maps[0], same ? (const void *)db_area : (const void *)tQ, nQ, N, tc::BM))
-            return BS_ERR_CUDA;
     } else if (!db_tiled) {
         if (tile_sketches(DB, nDB, N, tc::BN, db_area, stream) != BS_OK) return BS_ERR_CUDA;
         tDB = db_area;
     }
-    tc::Job &J = p.job[0];
-    tc::fill_job(J, pcQ, pcDB, nQ, nDB, N);
-    J.tQ = tQ; J.tDB = tDB;
-    J.exclude_self = exclude_self;
-    J.self_off = self_off;
-    J.score = score; J.idx = idx; J.ws_key = ws_key; J.ws_idx = ws_idx;
-    tc::Schedule s;
-    tc::single_schedule(nQ, nDB, s, &J.unit_base);
-    if (s.units == 0) return BS_OK;
-    if (s.splits != splits) return BS_ERR_INVALID_ARG;   // workspace planned for another shape
-    memcpy(p.block_start, s.block_start, sizeof(uint64_t) * (s.grid + 1));
-    p.njobs = 1;
-    p.k = k; p.splits = splits;
-    p.inject = inject ? tc::INJECT_STALL : tc::INJECT_NONE;
-    p.wait_limit = inject ? kTcInjectWaitLimit : kTcWaitLimit;
-    p.err = err;
-    const cudaError_t ce = launch_measure(measure, cfg, p, s.grid, stream);
-    if (ce == cudaErrorInvalidConfiguration) return BS_ERR_UNSUPPORTED;
-    return ce == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+    const uint8_t *q_fp4 = same ? reinterpret_cast<const uint8_t *>(db_area) : reinterpret_cast<const uint8_t *>(tQ);
+    // one launch over query rows [q_lo, q_lo + rows): in rounds of whole row
+    // blocks, or with the balanced ranges (and partial lists when splits > 1)
+    auto run = [&](uint32_t q_lo, uint32_t rows, bool rounds) -> bs_status {
+        memset(&p, 0, sizeof(p));
+        if (pl.fp4_db && !tc::make_map_fp4(&p.maps[1], db_area, nDB, N, tc::BN)) return BS_ERR_CUDA;
+        if (pl.fp4_q && !tc::make_map_fp4(&p.maps[0], q_fp4 + (size_t)q_lo * (N / 2), rows, N, tc::BM))
+            return BS_ERR_CUDA;
+        tc::Job &J = p.job[0];
+        tc::fill_job(J, pcQ + q_lo, pcDB, rows, nDB, N);
+        J.tQ = tQ + (size_t)(q_lo / tc::BM) * (N / 128) * tc::BM;   // q_lo is a multiple of 128
+        J.tDB = tDB;
+        J.exclude_self = exclude_self;
+        J.self_off = self_off;
+        J.q_base = q_lo;
+        J.score = score + (size_t)q_lo * k;
+        J.idx = idx + (size_t)q_lo * k;
+        tc::Schedule s;
+        if (rounds) {
+            s.grid = tc::max_blocks();
+            s.splits = 1;
+            const uint64_t per = (uint64_t)pl.rounds * J.tiles;
+            for (uint32_t c = 0; c <= s.grid; ++c) s.block_start[c] = (uint64_t)c * per;
+            J.unit_base = 0;
+        } else {
+            tc::single_schedule(rows, nDB, s, &J.unit_base);
+        }
+        if (s.splits > 1) {
+            J.ws_key = reinterpret_cast<float *>(lists);
+            J.ws_idx = reinterpret_cast<uint32_t *>(J.ws_key + (size_t)s.splits * rows * k);
+        }
+        memcpy(p.block_start, s.block_start, sizeof(uint64_t) * (s.grid + 1));
+        p.njobs = 1;
+        p.k = k; p.splits = s.splits;
+        p.inject = inject ? tc::INJECT_STALL : tc::INJECT_NONE;
+        p.wait_limit = inject ? kTcInjectWaitLimit : kTcWaitLimit;
+        p.err = err;
+        const cudaError_t ce = launch_measure(measure, cfg, p, s.grid, stream);
+        if (ce == cudaErrorInvalidConfiguration) return BS_ERR_UNSUPPORTED;
+        if (ce != cudaSuccess) return BS_ERR_CUDA;
+        if (s.splits <= 1) return BS_OK;
+        return launch_merge(measure, J.ws_key, J.ws_idx, rows, k, s.splits, J.score, J.idx, stream);
+    };
+    if (pl.q_split > 0) {
+        const bs_status s1 = run(0, pl.q_split, true);
+        if (s1 != BS_OK) return s1;
+    }
+    if (pl.q_split < nQ) return run(pl.q_split, nQ - pl.q_split, false);
+    return BS_OK;
 }
 
 bs_status estimate_tc(const uint32_t *A, const uint32_t *pcA, uint32_t nA, const uint32_t *B,

@@ -164,7 +164,8 @@ struct Job {
     uint64_t unit_base;         // first work unit of this job
     uint32_t nQ, nDB, N, nKc;
     uint32_t rbs, tiles;        // row blocks, database tiles
-    uint32_t self_off;          // exclude_self drops the pair q == self_off + j
+    uint32_t self_off;          // exclude_self drops the pair q_base + q == self_off + j
+    uint32_t q_base;            // global index of the job's first query row
     int exclude_self;
     float invL;                 // 1 / ln(1 - 1/N)
     float log2N;
@@ -1147,7 +1148,7 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
                 if (col_c + 32 > J.nDB)
                     mask &= col_c >= J.nDB ? 0u : (0xFFFFFFFFu >> (32 - (J.nDB - col_c)));
                 if (J.exclude_self) {
-                    const long long qs = (long long)q - (long long)J.self_off - (long long)col_c;
+                    const long long qs = (long long)q + (long long)J.q_base - (long long)J.self_off - (long long)col_c;
                     if (qs >= 0 && qs < 32) mask &= ~(1u << (uint32_t)qs);
                 }
                 if (!live) mask = 0;

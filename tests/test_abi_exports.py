@@ -57,25 +57,39 @@ def test_env_variant_override_in_plan():
 
 def test_tensor_core_plan_parts_match_the_persistent_schedule():
     # bs_topk_plan is host-only; without a GPU the library assumes 148 SMs.
-    # Parts = the most blocks any 128-row query block is spread over when the
-    # U = row blocks x 208-row database tiles are dealt out as equal contiguous
-    # ranges, block c starting at unit ceil(c U / G): unit x then sits in block
-    # floor(x G / U).
+    # The default tensor-core configuration for N = 4096, k = 50 reads FP4
+    # copies of both operands: R = rbs // G rounds of whole 128-row blocks go
+    # to the G blocks first (block c: row blocks [c R, (c + 1) R)), the rows
+    # left over run as a second launch whose U = row blocks x 208-row database
+    # tiles are dealt out as equal contiguous ranges, block c starting at unit
+    # ceil(c U / G): unit x then sits in block floor(x G / U), and the parts of
+    # a row block are the blocks it spans.
     from paper_1910_04658_gb300 import binding as B
 
-    def parts(nq, ndb, G=148):
+    G = 148
+
+    def parts(nq, ndb):
         rbs, T = (nq + 127) // 128, (ndb + 207) // 208
         U = rbs * T
-        G = min(G, U)
-        first = lambda x: (x * G) // U
+        g = min(G, U)
+        first = lambda x: (x * g) // U
         return max(first(rb * T + T - 1) - first(rb * T) + 1 for rb in range(rbs))
 
-    for nq, ndb in ((100_000, 100_000), (4096, 1_000_000), (1000, 1000), (37, 20_000), (129, 257)):
-        uses_tc, splits, launches = B.bs_topk_plan(nq, ndb, 4096, 50, B.BS_VARIANT_TC, nq == ndb)
-        assert uses_tc and splits == parts(nq, ndb), (nq, ndb, splits, parts(nq, ndb))
-        # two re-layouts (Q in 128-row, DB in 208-row blocks), the ranking
-        # kernel, and the merge when some row block is split
-        assert launches == 3 + (splits > 1)
+    for nq, ndb in ((100_000, 100_000), (4096, 1_000_000), (1000, 1000), (37, 20_000), (129, 257),
+                    (148 * 128 * 2, 3000), (148 * 128 * 2 - 5, 3000)):
+        for same in (True, False):
+            if same and nq != ndb:
+                continue
+            uses_tc, splits, launches = B.bs_topk_plan(nq, ndb, 4096, 50, B.BS_VARIANT_TC, same)
+            rbs = (nq + 127) // 128
+            rounds = rbs // G
+            q_split = min(nq, rounds * G * 128)
+            rest = nq - q_split
+            want = parts(rest, ndb) if rest > 0 else 1
+            assert uses_tc and splits == want, (nq, ndb, splits, want)
+            # the FP4 copies (one for all-pairs), the rounds launch, the
+            # launch over the rest, the merge of its partial lists
+            assert launches == 1 + (0 if same else 1) + (rounds > 0) + (rest > 0) + (want > 1), (nq, ndb)
 
 
 def test_batched_plan_claims_whole_row_blocks():
