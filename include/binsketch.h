@@ -181,8 +181,9 @@ bs_status bs_estimate_pairs_ex(const uint32_t *A, const uint32_t *pcA, uint32_t 
  * database; the tensor-core kernel's persistent blocks cut some row blocks
  * in two), and for the tensor-core kernel k-chunk-tiled copies of Q (rows
  * rounded up to 128) and DB (rows rounded up to 208), N/8 bytes per row --
- * or, for the configurations that read it (c = 10, 11 below), the FP4 copy
- * of DB, N/2 bytes per row.
+ * or, for the configurations that read them (c >= 10 below), the FP4
+ * copies of Q and DB, N/2 bytes per row; plus partial lists for the plan of
+ * every configuration.
  */
 size_t bs_topk_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k);
 
@@ -248,13 +249,22 @@ bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
  *          TMA moves each 256-bit slot of a tile from it into shared memory,
  *          3 database slots, 2 query slots, 2 groups
  *   c = 11: as c = 10 with 4 database slots and the shared heap
+ *   c = 12: both operands from FP4 copies by TMA (the query block's too; for
+ *          Q == DB one copy serves both), no widening warps, 3 stages, 3
+ *          epilogue groups sharing one heap per row
+ *   c = 13: as c = 12 with 2 stages (every k up to BS_TOPK_K_MAX fits)
+ *   c = 14: as c = 12 with 2 epilogue groups
  * The default, for bs_topk / bs_topk_ex / bs_topk_shard / bs_topk_noalloc,
- * is the first of 10, 11 that fits k, else the first of 0, 1, ..., 9 that
- * fits; calls with a database kept tiled (bs_topk_pretiled) and the batched
- * form use 0..9 only (c = 10, 11 there return BS_ERR_UNSUPPORTED).
+ * is the first of 12, 13, 14, 10, 11 that fits k, else the first of 0, 1,
+ * ..., 9 that fits; calls with a database kept tiled (bs_topk_pretiled) and
+ * the batched form use 0..9 only (c >= 10 there return BS_ERR_UNSUPPORTED).
+ * With c >= 10 a call whose query rows fill R >= 1 rounds of one 128-row
+ * block per SM runs those rounds as one launch (every SM sweeps the
+ * database tiles in the same order, so the FP4 copy streams from L2) and
+ * the rows left over as a second launch with partial lists.
  * Environment: for calls that pass BS_VARIANT_AUTO (bs_topk among them) the
  * variable BS_VARIANT, read once, overrides the choice: "popc" forces the
- * CUDA-core kernel, "tc<c>" (c = 0..11) selects configuration c wherever the
+ * CUDA-core kernel, "tc<c>" (c = 0..14) selects configuration c wherever the
  * tensor-core kernel applies and c fits k.
  * A configuration whose shared memory does not fit k returns
  * BS_ERR_UNSUPPORTED.  bs_topk_workspace_bytes() covers every variant.
@@ -373,11 +383,13 @@ bs_status bs_topk_merge(const float *score_parts, const uint32_t *idx_parts, uin
                         float *score, uint32_t *idx, bs_stream_t stream);
 
 /*
- * bs_topk_plan -- how bs_topk_ex would run this shape, without running it:
- * *uses_tc = 1 when the tensor-core kernel is chosen, *splits = partial
- * lists per query row (a merge kernel runs when > 1), *launches = kernels launched per
+ * bs_topk_plan -- how bs_topk_ex would run this shape with its default
+ * configuration, without running it: *uses_tc = 1 when the tensor-core
+ * kernel is chosen, *splits = partial lists per query row of the launch that
+ * uses them (a merge kernel runs when > 1; with the FP4 copies, the launch
+ * over the rows left after the rounds), *launches = kernels launched per
  * call.  same_matrix != 0 when Q and DB will be the same array (the
- * tensor-core path then re-lays out one matrix instead of two).  Any output
+ * tensor-core path then makes one FP4 copy instead of two).  Any output
  * pointer may be NULL.  Host only; Q/DB alignment is assumed to be 16 bytes.
  */
 bs_status bs_topk_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, uint32_t variant,
