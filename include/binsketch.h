@@ -424,6 +424,37 @@ bs_status bs_topk_pretiled(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, 
                            bs_stream_t stream);
 
 /*
+ * bs_fp4_bytes / bs_fp4_sketches -- keep a sketch database as the FP4 copy
+ * the default tensor-core configurations read by TMA: every sketch bit one
+ * 4-bit E2M1 element (set: 1.0, clear: 0), 32-bit word w written as the 16
+ * bytes ((w << 1) & M, w & M, (w >> 1) & M, (w >> 2) & M), M = 0x22222222,
+ * rows contiguous (N/2 bytes each, 4x the packed sketch).  Same paper
+ * content as the sketches (Definition "BinSketch", Sec. 3).
+ *  sketch  uint32[n_rows][N/32] in (16-byte aligned), N % 128 == 0
+ *  fp4     bs_fp4_bytes(n_rows, N) bytes out (16-byte aligned)
+ * Errors: BS_ERR_INVALID_ARG for N outside the tensor-core shapes, NULL or
+ * misaligned pointers.  bs_fp4_bytes returns 0 for such N.
+ */
+size_t bs_fp4_bytes(uint32_t n_rows, uint32_t N);
+bs_status bs_fp4_sketches(const uint32_t *sketch, uint32_t n_rows, uint32_t N, void *fp4,
+                          bs_stream_t stream);
+
+/*
+ * bs_topk_prewidened -- bs_topk_pretiled against a database kept as its FP4
+ * copy (bs_fp4_sketches): the default configuration order of bs_topk (both
+ * operands by TMA; the queries' FP4 copy is made in the workspace), so a
+ * resident corpus is searched with the fastest kernel and no per-call
+ * database pass.  Same requirements, results and errors as
+ * bs_topk_pretiled (the lists are identical, bit for bit); workspace:
+ * bs_topk_prewidened_workspace_bytes.
+ */
+size_t bs_topk_prewidened_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k);
+bs_status bs_topk_prewidened(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const void *DB_fp4,
+                             const uint32_t *pcDB, uint32_t nDB, uint32_t N, uint32_t by, uint32_t k,
+                             float *score, uint32_t *idx, void *workspace, size_t workspace_bytes,
+                             bs_stream_t stream);
+
+/*
  * bs_topk_noalloc -- bs_topk for callers that may not allocate GPU memory
  * (a serving process whose arena owns the whole device, a plugin living in
  * another framework's allocator, a request path that must not pay for an

@@ -94,6 +94,11 @@ SIGNATURES = [
     ("bs_topk_pretiled_workspace_bytes", _sz, [_u32, _u32, _u32, _u32]),
     ("bs_topk_pretiled", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, _vp, _vp, _vp,
                                 _sz, _vp]),
+    ("bs_fp4_bytes", _sz, [_u32, _u32]),
+    ("bs_fp4_sketches", _i32, [_vp, _u32, _u32, _vp, _vp]),
+    ("bs_topk_prewidened_workspace_bytes", _sz, [_u32, _u32, _u32, _u32]),
+    ("bs_topk_prewidened", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, _vp, _vp, _vp,
+                                  _sz, _vp]),
     ("bs_topk_noalloc", _i32, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, _i32, _vp, _vp,
                                _vp]),
     ("bs_onehot_csr", _i32, [_vp, _u32, _u32, _vp, _vp, _vp, _vp]),
@@ -341,6 +346,27 @@ def bs_topk_pretiled(Q, pcQ, nQ, DB_tiled, pcDB, nDB, N, by, k, score, idx, work
     _check(lib().bs_topk_pretiled(_p(Q), _p(pcQ), nQ, _p(DB_tiled), _p(pcDB), nDB, N, by, k,
                                   _p(score), _p(idx), _p(workspace), workspace_bytes, _s(stream)),
            "bs_topk_pretiled")
+
+
+def bs_fp4_bytes(n_rows, N) -> int:
+    return int(lib().bs_fp4_bytes(n_rows, N))
+
+
+def bs_fp4_sketches(sketch, n_rows, N, fp4, stream=None):
+    _check(lib().bs_fp4_sketches(_p(sketch, n_rows * (N // 8), "sketch"), n_rows, N,
+                                 _p(fp4, n_rows * (N // 2), "fp4"), _s(stream)), "bs_fp4_sketches")
+
+
+def bs_topk_prewidened_workspace_bytes(nQ, nDB, N, k) -> int:
+    return int(lib().bs_topk_prewidened_workspace_bytes(nQ, nDB, N, k))
+
+
+def bs_topk_prewidened(Q, pcQ, nQ, DB_fp4, pcDB, nDB, N, by, k, score, idx, workspace=None,
+                       workspace_bytes=0, stream=None):
+    _check(lib().bs_topk_prewidened(_p(Q, nQ * (N // 8), "Q"), _p(pcQ, 4 * nQ, "pcQ"), nQ,
+                                    _p(DB_fp4, nDB * (N // 2), "DB_fp4"), _p(pcDB, 4 * nDB, "pcDB"),
+                                    nDB, N, by, k, _p(score, 4 * nQ * k, "score"), _p(idx, 4 * nQ * k, "idx"),
+                                    _p(workspace), workspace_bytes, _s(stream)), "bs_topk_prewidened")
 
 
 def bs_topk_noalloc(Q, pcQ, nQ, DB, pcDB, nDB, N, by, k, exclude_self, score, idx, stream=None):

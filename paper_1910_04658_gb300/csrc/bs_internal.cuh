@@ -326,7 +326,11 @@ struct TcCallPlan {
     uint32_t rounds = 0, q_split = 0, splits = 1, launches = 0;
     size_t lists_bytes = 0;
 };
-bs_status tc_call_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, int cfg, bool same, bool pretiled,
+// kept: how the caller keeps the database -- not at all (the call makes the
+// operand copy it needs), tiled (bs_tile_sketches) or as the FP4 copy
+// (bs_fp4_sketches)
+enum { KEPT_NONE = 0, KEPT_TILED = 1, KEPT_FP4 = 2 };
+bs_status tc_call_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, int cfg, bool same, int kept,
                        TcCallPlan &pl);
 // partial-list bytes that cover the plan of every configuration
 size_t tc_lists_bytes(uint32_t nQ, uint32_t nDB, uint32_t k);
@@ -334,15 +338,18 @@ size_t tc_lists_bytes(uint32_t nQ, uint32_t nDB, uint32_t k);
 // every configuration); tiled: scratch for the operand copies, the larger of
 // tc_tiled_bytes(nQ, N, 128) and tc_fp4_bytes(nQ, N) rounded up to 256 bytes,
 // then the larger of tc_tiled_bytes(nDB, N, 208) and tc_fp4_bytes(nDB, N)
-// (the second part unused when db_tiled, a database kept tiled by
-// bs_tile_sketches, is given); the call merges its partial lists itself.
+// (the second part unused when the caller keeps the database: db_kept, tiled
+// by bs_tile_sketches or the FP4 copy of bs_fp4_sketches as `kept` says);
+// the call merges its partial lists itself.
 // inject: test-only fault injection (0 = none, 1 = the MMA issuer never
 // announces its first accumulator; waits give up after kTcInjectWaitLimit)
 bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
                   const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
                   int exclude_self, uint32_t self_off, float *score, uint32_t *idx, void *lists,
-                  size_t lists_bytes, void *tiled, const void *db_tiled, int cfg, uint32_t inject,
+                  size_t lists_bytes, void *tiled, const void *db_kept, int kept, int cfg, uint32_t inject,
                   unsigned int *err, cudaStream_t stream);
+// row-major sketches [n][N/32] -> the FP4 copy [n][N/2 bytes] (N % 128 == 0)
+bs_status fp4_sketches(const uint32_t *sk, uint32_t n, uint32_t N, void *fp4, cudaStream_t stream);
 // full count / estimate matrices on the tensor cores (N % 128 == 0, 256 <= N
 // <= 8192, 16-byte aligned A and B), reading the row-major sketches directly
 bool tc_store_supported(const uint32_t *A, const uint32_t *B, uint32_t N);

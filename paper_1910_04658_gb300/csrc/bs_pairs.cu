@@ -690,7 +690,7 @@ static bs_status topk_impl(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, 
         if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return BS_ERR_INVALID_ARG;
         uint8_t *w = reinterpret_cast<uint8_t *>(workspace);
         return topk_tc(Q, pcQ, nQ, DB, pcDB, nDB, N, m, k, exclude_self, self_off, score, idx, w, lists,
-                       w + align256(lists), nullptr, tc_cfg, inject, err, st);
+                       w + align256(lists), nullptr, KEPT_NONE, tc_cfg, inject, err, st);
     }
     const uint32_t splits = popc_splits(nQ, nDB);
     const size_t need = ws_bytes(splits, nQ, k);
@@ -763,7 +763,7 @@ bs_status bs_topk_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, uint32
         TcCallPlan pl;
         const int ev = variant == BS_VARIANT_AUTO ? env_variant() : -2;
         const bs_status ps = tc_call_plan(nQ, nDB, N, k, ev >= 0 && tc_cfg_fits(ev, k) ? ev : -1,
-                                          same_matrix != 0, false, pl);
+                                          same_matrix != 0, KEPT_NONE, pl);
         if (ps != BS_OK) return ps;
         s = pl.splits;
         l = pl.launches;
@@ -821,7 +821,53 @@ bs_status bs_topk_pretiled(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, 
     if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return BS_ERR_INVALID_ARG;
     uint8_t *w = reinterpret_cast<uint8_t *>(workspace);
     return topk_tc(Q, pcQ, nQ, nullptr, pcDB, nDB, N, m, k, 0, 0, score, idx, w, lists, w + align256(lists),
-                   DB_tiled, -1, 0, err, st);
+                   DB_tiled, KEPT_TILED, -1, 0, err, st);
+}
+
+size_t bs_fp4_bytes(uint32_t n_rows, uint32_t N) {
+    if (!valid_N(N) || (N % 128) != 0) return 0;
+    return tc_fp4_bytes(n_rows, N);
+}
+
+bs_status bs_fp4_sketches(const uint32_t *sketch, uint32_t n_rows, uint32_t N, void *fp4, bs_stream_t stream) {
+    BS_NVTX_RANGE();
+    if (!valid_N(N) || (N % 128) != 0) return BS_ERR_INVALID_ARG;
+    if (n_rows == 0) return BS_OK;
+    if (!sketch || !fp4) return BS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(sketch) & 15u) || (reinterpret_cast<uintptr_t>(fp4) & 15u))
+        return BS_ERR_INVALID_ARG;
+    return fp4_sketches(sketch, n_rows, N, fp4, (cudaStream_t)stream);
+}
+
+size_t bs_topk_prewidened_workspace_bytes(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k) {
+    if (nQ == 0 || nDB == 0 || !valid_N(N) || !tc_shape_ok(N, k)) return 0;
+    const size_t q = std::max(tc_tiled_bytes(nQ, N, kTcQueryRows), tc_fp4_bytes(nQ, N));
+    return align256(tc_lists_bytes(nQ, nDB, k)) + align256(q);
+}
+
+bs_status bs_topk_prewidened(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const void *DB_fp4,
+                             const uint32_t *pcDB, uint32_t nDB, uint32_t N, uint32_t by, uint32_t k,
+                             float *score, uint32_t *idx, void *workspace, size_t workspace_bytes,
+                             bs_stream_t stream) {
+    BS_NVTX_RANGE();
+    if (!valid_N(N)) return BS_ERR_INVALID_ARG;
+    if (k == 0 || k > BS_TOPK_K_MAX) return BS_ERR_INVALID_ARG;
+    const int m = measure_code(by);
+    if (m < 0) return BS_ERR_INVALID_ARG;
+    if (nQ == 0) return BS_OK;
+    if (!tc_shape_ok(N, k) || nDB == 0) return BS_ERR_UNSUPPORTED;
+    if (!Q || !pcQ || !DB_fp4 || !pcDB || !score || !idx) return BS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(Q) & 15u) || (reinterpret_cast<uintptr_t>(DB_fp4) & 15u))
+        return BS_ERR_INVALID_ARG;
+    unsigned int *err = error_word();
+    if (!err) return BS_ERR_CUDA;
+    const size_t lists = tc_lists_bytes(nQ, nDB, k);
+    const size_t need = bs_topk_prewidened_workspace_bytes(nQ, nDB, N, k);
+    if (!workspace || workspace_bytes < need) return BS_ERR_NO_MEMORY;
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return BS_ERR_INVALID_ARG;
+    uint8_t *w = reinterpret_cast<uint8_t *>(workspace);
+    return topk_tc(Q, pcQ, nQ, nullptr, pcDB, nDB, N, m, k, 0, 0, score, idx, w, lists, w + align256(lists),
+                   DB_fp4, KEPT_FP4, -1, 0, err, (cudaStream_t)stream);
 }
 
 size_t bs_topk_batched_workspace_bytes(const bs_topk_job *jobs, uint32_t n_jobs, uint32_t k) {

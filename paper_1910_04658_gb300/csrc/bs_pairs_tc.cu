@@ -299,6 +299,15 @@ size_t tc_tiled_bytes(uint32_t n, uint32_t N, uint32_t R) { return (size_t)((n +
 // Bytes of the FP4 copy of n rows (the TMA configurations' database operand).
 size_t tc_fp4_bytes(uint32_t n, uint32_t N) { return (size_t)n * (N / 2); }
 
+bs_status fp4_sketches(const uint32_t *sk, uint32_t n, uint32_t N, void *fp4, cudaStream_t stream) {
+    const size_t chunks = (size_t)n * (N / 128);
+    if (chunks == 0) return BS_OK;
+    const uint32_t blocks = (uint32_t)std::min<size_t>((chunks + 255) / 256, (size_t)sm_count() * 16);
+    tc::widen_fp4_kernel<<<blocks, 256, 0, stream>>>(reinterpret_cast<const uint4 *>(sk), chunks,
+                                                     reinterpret_cast<uint4 *>(fp4));
+    return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+}
+
 bs_status tile_sketches(const uint32_t *sk, uint32_t n, uint32_t N, uint32_t R, void *tiled, cudaStream_t stream) {
     if (n == 0) return BS_OK;
     const uint32_t nKc = N / 128;
@@ -328,13 +337,14 @@ static cudaError_t launch_measure(int measure, int cfg, const tc::Args<NJ> &p, u
 // second launch with the balanced ranges and partial lists of the usual
 // schedule.  Otherwise one launch with the balanced ranges.
 bs_status tc_call_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, int cfg_req, bool same,
-                       bool pretiled, TcCallPlan &pl) {
+                       int kept, TcCallPlan &pl) {
     pl = TcCallPlan();
-    pl.cfg = cfg_req >= 0 ? cfg_req : tc_default_cfg(k, !pretiled);
+    pl.cfg = cfg_req >= 0 ? cfg_req : tc_default_cfg(k, kept != KEPT_TILED);
     if (pl.cfg < 0 || !tc_cfg_fits(pl.cfg, k)) return BS_ERR_UNSUPPORTED;
     pl.fp4_db = tc_cfg_tma(pl.cfg);
     pl.fp4_q = tc_cfg_query_tma(pl.cfg);
-    if (pl.fp4_db && pretiled) return BS_ERR_UNSUPPORTED;   // a kept tiled database has no FP4 copy
+    if (pl.fp4_db && kept == KEPT_TILED) return BS_ERR_UNSUPPORTED;   // a kept tiled database has no FP4 copy
+    if (!pl.fp4_db && kept == KEPT_FP4) return BS_ERR_UNSUPPORTED;    // and a kept FP4 copy no tiles
     if (nQ == 0 || nDB == 0) return BS_OK;
     const uint32_t rbs = (nQ + tc::BM - 1) / tc::BM;
     const uint32_t G = tc::max_blocks();
@@ -343,7 +353,7 @@ bs_status tc_call_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, int cf
     const uint32_t nQ2 = nQ - pl.q_split;
     pl.splits = nQ2 > 0 ? tc_splits(nQ2, nDB) : 1;
     pl.lists_bytes = pl.splits > 1 ? (size_t)pl.splits * nQ2 * k * 8 : 0;
-    pl.launches = (pl.fp4_db ? 1 : (pretiled ? 0 : 1)) + (pl.fp4_q ? (same ? 0 : 1) : 1) +
+    pl.launches = (kept != KEPT_NONE ? 0 : 1) + (pl.fp4_q ? (same ? 0 : 1) : 1) +
                   (pl.rounds > 0 ? 1 : 0) + (nQ2 > 0 ? 1 : 0) + (pl.splits > 1 ? 1 : 0);
     return BS_OK;
 }
@@ -355,7 +365,7 @@ size_t tc_lists_bytes(uint32_t nQ, uint32_t nDB, uint32_t k) {
     size_t b = s > 1 ? (size_t)s * nQ * k * 8 : 0;
     TcCallPlan pl;
     for (int c = tc::kTcFirstTma; c < tc::kTcConfigs; ++c)
-        if (tc_cfg_fits(c, k) && tc_call_plan(nQ, nDB, 256, k, c, false, false, pl) == BS_OK)
+        if (tc_cfg_fits(c, k) && tc_call_plan(nQ, nDB, 256, k, c, false, KEPT_NONE, pl) == BS_OK)
             b = std::max(b, pl.lists_bytes);
     return b;
 }
@@ -363,11 +373,12 @@ size_t tc_lists_bytes(uint32_t nQ, uint32_t nDB, uint32_t k) {
 bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uint32_t *DB,
                   const uint32_t *pcDB, uint32_t nDB, uint32_t N, int measure, uint32_t k,
                   int exclude_self, uint32_t self_off, float *score, uint32_t *idx, void *lists,
-                  size_t lists_bytes, void *tiled, const void *db_tiled, int cfg_req, uint32_t inject,
-                  unsigned int *err, cudaStream_t stream) {
-    const bool same = Q == DB && nQ == nDB;
+                  size_t lists_bytes, void *tiled, const void *db_kept, int kept, int cfg_req,
+                  uint32_t inject, unsigned int *err, cudaStream_t stream) {
+    const bool same = kept == KEPT_NONE && Q == DB && nQ == nDB;
+    const void *db_tiled = kept == KEPT_TILED ? db_kept : nullptr;
     TcCallPlan pl;
-    const bs_status ps = tc_call_plan(nQ, nDB, N, k, cfg_req, same, db_tiled != nullptr, pl);
+    const bs_status ps = tc_call_plan(nQ, nDB, N, k, cfg_req, same, kept, pl);
     if (ps != BS_OK) return ps;
     if (nQ == 0 || nDB == 0) return BS_OK;
     if (pl.lists_bytes > lists_bytes || (pl.lists_bytes > 0 && !lists)) return BS_ERR_NO_MEMORY;
@@ -392,7 +403,9 @@ bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uin
         return BS_ERR_CUDA;
     }
     const uint4 *tDB = reinterpret_cast<const uint4 *>(db_tiled);
-    if (pl.fp4_db) {
+    if (kept == KEPT_FP4) {
+        db_area = const_cast<uint4 *>(reinterpret_cast<const uint4 *>(db_kept));
+    } else if (pl.fp4_db) {
         if (!widen(DB, nDB, db_area)) return BS_ERR_CUDA;
     } else if (!db_tiled) {
         if (tile_sketches(DB, nDB, N, tc::BN, db_area, stream) != BS_OK) return BS_ERR_CUDA;

@@ -270,7 +270,9 @@ def poisson_requests(rng: np.random.Generator, n_requests: int, rate_per_s: floa
 # ----------------------------------------------------------------------------
 
 class SketchDB:
-    """Sketches of a corpus kept in HBM, tiled for the tensor-core search."""
+    """Sketches of a corpus kept in HBM with the two copies the tensor-core
+    search reads: tiled (bs_topk_pretiled) and FP4 (bs_topk_prewidened, the
+    one the executor uses: both operands by TMA, 4x the packed size)."""
 
     def __init__(self, row_ptr, col, d: int, N: int, seed: int = 0, stream=None):
         import torch
@@ -281,8 +283,16 @@ class SketchDB:
         self.sketch = torch.empty((n, N // 32), dtype=torch.int32, device=dev)
         self.pc = torch.empty((n,), dtype=torch.int32, device=dev)
         B.bs_sketch(row_ptr, col, n, col.numel(), d, N, seed, self.sketch, self.pc, stream)
-        self.tiled = torch.empty((B.bs_tiled_bytes(n, N),), dtype=torch.uint8, device=dev)
-        B.bs_tile_sketches(self.sketch, n, N, self.tiled, stream)
+        self._copies(stream)
+
+    def _copies(self, stream=None):
+        import torch
+        from . import binding as B
+        dev = self.sketch.device
+        self.tiled = torch.empty((B.bs_tiled_bytes(self.n, self.N),), dtype=torch.uint8, device=dev)
+        B.bs_tile_sketches(self.sketch, self.n, self.N, self.tiled, stream)
+        self.fp4 = torch.empty((B.bs_fp4_bytes(self.n, self.N),), dtype=torch.uint8, device=dev)
+        B.bs_fp4_sketches(self.sketch, self.n, self.N, self.fp4, stream)
 
     def save(self, path: str) -> None:
         """Write the sketches with their (N, seed) (checkpoint.py format)."""
@@ -292,16 +302,14 @@ class SketchDB:
     @classmethod
     def load(cls, path: str, device: str = "cuda", expect_N: int = None, expect_seed: int = None,
              stream=None) -> "SketchDB":
-        """A database from a checkpoint, re-tiled for the tensor-core search;
+        """A database from a checkpoint, its tensor-core copies rebuilt;
         refuses one sketched with another (N, seed) than expected."""
-        import torch
-        from . import binding as B, checkpoint
+        from . import checkpoint
         sk, pc, meta = checkpoint.load_sketches(path, device, expect_N, expect_seed)
         db = cls.__new__(cls)
         db.n, db.d, db.N, db.seed = meta.n, meta.d, meta.N, meta.seed
         db.sketch, db.pc = sk, pc
-        db.tiled = torch.empty((B.bs_tiled_bytes(db.n, db.N),), dtype=torch.uint8, device=device)
-        B.bs_tile_sketches(db.sketch, db.n, db.N, db.tiled, stream)
+        db._copies(stream)
         return db
 
 
@@ -336,7 +344,7 @@ class GpuExecutor(Executor):
 
     def _parts(self, nq, nnz):
         N, k = self.db.N, self.k
-        ws = self.B.bs_topk_pretiled_workspace_bytes(nq, self.db.n, N, k)
+        ws = self.B.bs_topk_prewidened_workspace_bytes(nq, self.db.n, N, k)
         a = lambda x: (int(x) + 255) // 256 * 256
         return [("rp", a(8 * (nq + 1))), ("col", a(4 * max(nnz, 1))), ("sk", a(nq * N // 8)),
                 ("pc", a(4 * nq)), ("score", a(4 * nq * k)), ("idx", a(4 * nq * k)), ("ws", a(ws))]
@@ -373,10 +381,10 @@ class GpuExecutor(Executor):
             g = {name: self.base + o for name, o in ptr.items()}
             B.bs_sketch(g["rp"], g["col"], nq, nnz, self.db.d, self.db.N, self.db.seed,
                         g["sk"], g["pc"], s)
-            ws_bytes = B.bs_topk_pretiled_workspace_bytes(nq, self.db.n, self.db.N, self.k)
-            B.bs_topk_pretiled(g["sk"], g["pc"], nq, self.db.tiled, self.db.pc, self.db.n,
-                               self.db.N, self.by, self.k, g["score"], g["idx"], g["ws"],
-                               ws_bytes, s)
+            ws_bytes = B.bs_topk_prewidened_workspace_bytes(nq, self.db.n, self.db.N, self.k)
+            B.bs_topk_prewidened(g["sk"], g["pc"], nq, self.db.fp4, self.db.pc, self.db.n,
+                                 self.db.N, self.by, self.k, g["score"], g["idx"], g["ws"],
+                                 ws_bytes, s)
             kk = self.k
             st["score"][:nq].view(torch.uint8).view(-1).copy_(
                 A[ptr["score"]:ptr["score"] + 4 * nq * kk], non_blocking=True)

@@ -96,6 +96,36 @@ def test_pretiled_matches_topk(served):
     assert np.array_equal(u32(i1), u32(i2)) and np.array_equal(s1.cpu().numpy(), s2.cpu().numpy())
 
 
+def test_prewidened_matches_pretiled_and_fp4_layout(served):
+    # the FP4 copy is the documented widening of every word, and the search
+    # against it returns, bit for bit, the lists of the tiled database
+    db_csr, db, reqs = served
+    w = u32(db.sketch[:64])
+    M = np.uint32(0x22222222)
+    want = np.stack([(w << np.uint32(1)) & M, w & M, (w >> np.uint32(1)) & M, (w >> np.uint32(2)) & M],
+                    axis=-1).reshape(64, -1)
+    got = db.fp4[:64 * (N // 2)].cpu().numpy().view(np.uint32).reshape(64, -1)
+    assert np.array_equal(got, want)
+    r = reqs[3]
+    rp = torch.from_numpy(r.row_ptr.view(np.int64)).cuda()
+    col = torch.from_numpy(r.col.view(np.int32)).cuda()
+    q = r.n_queries
+    sk = torch.empty((q, N // 32), dtype=torch.int32, device="cuda")
+    pc = torch.empty((q,), dtype=torch.int32, device="cuda")
+    B.bs_sketch(rp, col, q, r.nnz, db.d, N, 5, sk, pc)
+    out = []
+    for fn, wsfn, base in ((B.bs_topk_pretiled, B.bs_topk_pretiled_workspace_bytes, db.tiled),
+                           (B.bs_topk_prewidened, B.bs_topk_prewidened_workspace_bytes, db.fp4)):
+        s = torch.empty((q, K), dtype=torch.float32, device="cuda")
+        i = torch.empty((q, K), dtype=torch.int32, device="cuda")
+        wsb = wsfn(q, db.n, N, K)
+        ws = torch.empty((wsb,), dtype=torch.uint8, device="cuda")
+        fn(sk, pc, q, base, db.pc, db.n, N, B.BS_JS, K, s, i, ws, wsb)
+        assert B.bs_get_async_error() == 0
+        out.append((s, i))
+    assert torch.equal(out[0][1], out[1][1]) and torch.equal(out[0][0], out[1][0])
+
+
 def test_device_corpus_generator_shape():
     rp, col = inputs.bow_corpus_device(0, 5000, 100_000)
     lens = (rp[1:] - rp[:-1]).cpu().numpy()
