@@ -142,8 +142,8 @@ struct Smem {
     static constexpr int bars = col + 2 * 3 * BNP * 4;
     static constexpr int thr = bars + 512;                      // [NG][BM] key, idx, size
     static constexpr int lock = thr + NG * BM * 12;             // [BM] shared-heap row locks
-    static constexpr int cbuf = lock + BM * 4;                  // [NG][CB][BM] admitted pairs (per-group heaps)
-    static constexpr int heap = cbuf + (SH ? 0 : NG * CB * BM * 4);
+    static constexpr int cbuf = lock + BM * 4;                  // [NG][CB][BM] admitted pairs
+    static constexpr int heap = cbuf + NG * CB * BM * 4;
     static_assert((2 * NOP + 2 * RD + 2 * NB + 5 + 2 * IR) * 8 + 8 + 4 * IR <= 512, "barrier area");
 };
 
@@ -990,10 +990,17 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
                     --nbuf;
                     const uint32_t ent = cb[nbuf * BM + r];
                     const uint32_t j = ent & 255u;
-                    st = consider<M>(st, hent, r, d_col0 + j, ent >> 8, (uint32_t)d_cv[j].x, a, lnA,
-                                     eff_k, eff_i, N, invL, (int)p.k);
-                    if (st.thr_i != NO_IDX && better(st.thr_k, st.thr_i, eff_k, eff_i)) {
-                        eff_k = st.thr_k; eff_i = st.thr_i;
+                    if (SHARED) {
+                        const float root = consider_shared<M>(hent, thr_key, heap_size, row_lock, r, d_col0 + j,
+                                                              ent >> 8, (uint32_t)d_cv[j].x, a, lnA, eff_k, N,
+                                                              invL, (int)p.k, p.err);
+                        if (root > eff_k) { eff_k = root; eff_i = 0xFFFFFFFEu; }
+                    } else {
+                        st = consider<M>(st, hent, r, d_col0 + j, ent >> 8, (uint32_t)d_cv[j].x, a, lnA,
+                                         eff_k, eff_i, N, invL, (int)p.k);
+                        if (st.thr_i != NO_IDX && better(st.thr_k, st.thr_i, eff_k, eff_i)) {
+                            eff_k = st.thr_k; eff_i = st.thr_i;
+                        }
                     }
                 }
             }
@@ -1182,9 +1189,7 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
                         }
                     }
                 };
-                if (SHARED) {
-                    insert_direct(mask);
-                } else if (__any_sync(0xffffffffu, __popc(mask) > CB - nbuf)) {
+                if (__any_sync(0xffffffffu, __popc(mask) > CB - nbuf)) {
                     drain();
                     insert_direct(mask);
                 } else {
@@ -1210,7 +1215,10 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[ab]);
             if (MODE == MODE_STORE) continue;
-            if (!SHARED) {   // this tile's buffered pairs (TMEM no longer needed)
+            if (SHARED) {    // this tile's buffered pairs (TMEM no longer needed)
+                drain();
+                if (eff_i != NO_IDX) filt = make_filter<M>(eff_k, rc, invL, J.log2N);
+            } else {
                 const int sz0 = st.size;
                 const uint32_t ri0 = st.thr_i;
                 const float rk0 = st.thr_k;
