@@ -256,8 +256,10 @@ bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
  *   c = 14: as c = 12 with 2 epilogue groups
  * The default, for bs_topk / bs_topk_ex / bs_topk_shard / bs_topk_noalloc,
  * is the first of 12, 13, 14, 10, 11 that fits k, else the first of 0, 1,
- * ..., 9 that fits; calls with a database kept tiled (bs_topk_pretiled) and
- * the batched form use 0..9 only (c >= 10 there return BS_ERR_UNSUPPORTED).
+ * ..., 9 that fits; calls with a database kept tiled (bs_topk_pretiled) use
+ * 0..9 only, a database kept as its FP4 copy (bs_topk_prewidened) 10..14
+ * only, and the batched form the first of 12, 13, 14, 0, ..., 9 that fits
+ * (c = 10, 11 there return BS_ERR_UNSUPPORTED).
  * With c >= 10 a call whose query rows fill R >= 1 rounds of one 128-row
  * block per SM runs those rounds as one launch (every SM sweeps the
  * database tiles in the same order, so the FP4 copy streams from L2) and
@@ -308,10 +310,10 @@ bs_status bs_topk_ex(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
  *  variant     BS_VARIANT_AUTO or BS_VARIANT_TC, optionally with
  *              BS_VARIANT_TC_CFG(c): one block configuration for the launch
  *  workspace   device memory of at least bs_topk_batched_workspace_bytes()
- *              bytes, 256-byte aligned: the claim counter and tiled copies
- *              of every job's sketches
- * Launches: one re-layout kernel for all jobs (it also zeroes the counter)
- * and the persistent ranking kernel.  Calls that share a workspace must run
+ *              bytes, 256-byte aligned: the claim counter and, per job, its
+ *              operand copies (tiled, or FP4 for c = 12..14)
+ * Launches: one re-layout (or FP4 widening) kernel for all jobs (it also
+ * zeroes the counter) and the persistent ranking kernel.  Calls that share a workspace must run
  * in order (one stream).
  * Errors: BS_ERR_INVALID_ARG for n_jobs outside 1..BS_TOPK_BATCH_MAX, a bad
  * measure or k, NULL arrays; BS_ERR_UNSUPPORTED for a job outside the

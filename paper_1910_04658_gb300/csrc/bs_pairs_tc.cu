@@ -203,6 +203,38 @@ __global__ void __launch_bounds__(256) widen_fp4_kernel(const uint4 *__restrict_
     }
 }
 
+// The FP4 copies of many matrices in one launch: matrix m's 16-byte input
+// chunks are [chunk_base[m], chunk_base[m+1]) of the grid-stride range; block
+// 0 also zeroes the batch's claim counter (when given).
+struct WidenJobs {
+    const uint4 *src[2 * MAXJ];   // a job adds DB, and Q unless Q is DB
+    uint4 *dst[2 * MAXJ];
+    uint64_t chunk_base[2 * MAXJ + 1];
+    uint32_t count;
+    unsigned int *counter;
+};
+
+__global__ void __launch_bounds__(256) widen_fp4_batched_kernel(const __grid_constant__ WidenJobs wj) {
+    if (wj.counter && blockIdx.x == 0 && threadIdx.x == 0) *wj.counter = 0u;
+    const uint64_t total = wj.chunk_base[wj.count];
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        uint32_t lo = 0, hi = wj.count - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (wj.chunk_base[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        const uint64_t x = i - wj.chunk_base[lo];
+        const uint4 v = wj.src[lo][x];
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            wj.dst[lo][4 * x + t] = make_uint4((w[t] << 1) & 0x22222222u, w[t] & 0x22222222u,
+                                               (w[t] >> 1) & 0x22222222u, (w[t] >> 2) & 0x22222222u);
+    }
+}
+
 // 2-D tensor map over the FP4 copy [rows][N / 2 bytes]: boxes of one 256-bit
 // operand slot (128 bytes) x box_rows rows (BN for a database tile, BM for a
 // query block) with the 128-byte swizzle, so a box lands
@@ -265,6 +297,16 @@ int tc_default_cfg(uint32_t k, bool allow_tma) {
     if (allow_tma)
         for (int c : tma_order)
             if (tc_cfg_fits(c, k)) return c;
+    for (int c = 0; c < tc::kTcFirstTma; ++c)
+        if (tc_cfg_fits(c, k)) return c;
+    return -1;
+}
+
+// the batched form: the configurations with both operands by TMA (12, 13, 14)
+// first, then the widening ones (the database-only TMA ones need one problem)
+static int tc_default_cfg_batched(uint32_t k) {
+    for (int c : {12, 13, 14})
+        if (tc_cfg_fits(c, k)) return c;
     for (int c = 0; c < tc::kTcFirstTma; ++c)
         if (tc_cfg_fits(c, k)) return c;
     return -1;
@@ -529,11 +571,16 @@ bs_status plan_batch(const bs_topk_job *jobs, uint32_t n, uint32_t k, BatchPlan 
     return BS_OK;
 }
 
-// workspace: [claim counter, 256 bytes] then per job [Q tiled in 128-row
-// blocks][DB tiled in 208-row blocks]
+// workspace: [claim counter, 256 bytes] then per job its operand copies --
+// Q tiled in 128-row blocks and DB in 208-row blocks, or (configurations with
+// both operands by TMA) the FP4 copies of DB and, unless Q is DB, of Q; each
+// job's region holds either
 constexpr size_t COUNTER_BYTES = 256;
 size_t job_ws(const bs_topk_job &jb) {
-    return align256(tc_tiled_bytes(jb.nQ, jb.N, tc::BM)) + align256(tc_tiled_bytes(jb.nDB, jb.N, tc::BN));
+    const bool same = jb.Q == jb.DB && jb.nQ == jb.nDB;
+    const size_t tiled = align256(tc_tiled_bytes(jb.nQ, jb.N, tc::BM)) + align256(tc_tiled_bytes(jb.nDB, jb.N, tc::BN));
+    const size_t fp4 = align256(tc_fp4_bytes(jb.nDB, jb.N)) + (same ? 0 : align256(tc_fp4_bytes(jb.nQ, jb.N)));
+    return std::max(tiled, fp4);
 }
 }  // namespace
 
@@ -564,8 +611,10 @@ bs_status topk_tc_batched(const bs_topk_job *jobs, uint32_t n, int measure, uint
         if ((reinterpret_cast<uintptr_t>(jb.Q) & 15u) || (reinterpret_cast<uintptr_t>(jb.DB) & 15u))
             return BS_ERR_UNSUPPORTED;
     }
-    const int cfg = cfg_req >= 0 ? cfg_req : tc_default_cfg(k, false);
-    if (cfg < 0 || !tc_cfg_fits(cfg, k) || tc_cfg_tma(cfg)) return BS_ERR_UNSUPPORTED;
+    const int cfg = cfg_req >= 0 ? cfg_req : tc_default_cfg_batched(k);
+    if (cfg < 0 || !tc_cfg_fits(cfg, k)) return BS_ERR_UNSUPPORTED;
+    const bool fp4 = tc_cfg_query_tma(cfg);   // both operands by TMA from FP4 copies
+    if (tc_cfg_tma(cfg) && !fp4) return BS_ERR_UNSUPPORTED;   // database-only TMA: one problem
     static thread_local BatchPlan bp;
     const bs_status ps = plan_batch(jobs, n, k, bp);
     if (ps != BS_OK) return ps;
@@ -577,15 +626,59 @@ bs_status topk_tc_batched(const bs_topk_job *jobs, uint32_t n, int measure, uint
 
     static thread_local tc::Args<tc::MAXJ> p;
     static thread_local tc::TileJobs tj;
+    static thread_local tc::WidenJobs wj;
     memset(&p, 0, sizeof(p));
     memset(&tj, 0, sizeof(tj));
+    memset(&wj, 0, sizeof(wj));
     uint8_t *w = reinterpret_cast<uint8_t *>(workspace);
     unsigned int *counter = reinterpret_cast<unsigned int *>(w);
     w += COUNTER_BYTES;
+    if (fp4) {   // the FP4 copies of every job (one launch, which also zeroes the counter) and their maps
+        for (uint32_t j = 0; j < bp.nj; ++j) {
+            const bs_topk_job &jb = jobs[bp.src[j]];
+            uint8_t *region = w;
+            w += job_ws(jb);
+            const bool same = jb.Q == jb.DB && jb.nQ == jb.nDB;
+            uint8_t *db4 = region;
+            uint8_t *q4 = same ? db4 : region + align256(tc_fp4_bytes(jb.nDB, jb.N));
+            auto add = [&](const uint32_t *src, uint32_t rows, uint8_t *dst) {
+                const uint32_t m = wj.count++;
+                wj.src[m] = reinterpret_cast<const uint4 *>(src);
+                wj.dst[m] = reinterpret_cast<uint4 *>(dst);
+                wj.chunk_base[m + 1] = wj.chunk_base[m] + (uint64_t)rows * (jb.N / 128);
+            };
+            add(jb.DB, jb.nDB, db4);
+            if (!same) add(jb.Q, jb.nQ, q4);
+            tc::Job &J = p.job[j];
+            tc::fill_job(J, jb.pcQ, jb.pcDB, jb.nQ, jb.nDB, jb.N);
+            J.exclude_self = jb.exclude_self;
+            J.self_off = 0;
+            J.score = jb.score; J.idx = jb.idx; J.ws_key = nullptr; J.ws_idx = nullptr;
+            J.unit_base = bp.item_base[j];
+            if (!tc::make_map_fp4(&p.jmap[j][0], q4, jb.nQ, jb.N, tc::BM) ||
+                !tc::make_map_fp4(&p.jmap[j][1], db4, jb.nDB, jb.N, tc::BN))
+                return BS_ERR_CUDA;
+        }
+        wj.counter = counter;   // zeroed here, ahead of the pair kernel on this stream
+        const uint64_t total = wj.chunk_base[wj.count];
+        const uint32_t blocks = (uint32_t)std::min<uint64_t>((total + 255) / 256, (uint64_t)sm_count() * 16);
+        tc::widen_fp4_batched_kernel<<<blocks > 0 ? blocks : 1, 256, 0, stream>>>(wj);
+        if (cudaGetLastError() != cudaSuccess) return BS_ERR_CUDA;
+        p.njobs = bp.nj;
+        p.k = k;
+        p.splits = 1;
+        p.counter = counter;
+        p.items = (uint32_t)bp.items;
+        p.wait_limit = kTcWaitLimit;
+        p.err = err;
+        const cudaError_t ce = launch_measure(measure, cfg, p, bp.grid, stream);
+        if (ce == cudaErrorInvalidConfiguration) return BS_ERR_UNSUPPORTED;
+        return ce == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+    }
     uint32_t blk = 0;
-    auto add_tile = [&](const uint32_t *src, uint32_t rows, uint32_t N, uint32_t R) {
-        uint4 *dst = reinterpret_cast<uint4 *>(w);
-        w += align256(tc_tiled_bytes(rows, N, R));
+    auto add_tile = [&](const uint32_t *src, uint32_t rows, uint32_t N, uint32_t R, uint8_t *&at) {
+        uint4 *dst = reinterpret_cast<uint4 *>(at);
+        at += align256(tc_tiled_bytes(rows, N, R));
         const uint32_t m = tj.count++;
         tj.src[m] = reinterpret_cast<const uint4 *>(src);
         tj.dst[m] = dst;
@@ -600,8 +693,10 @@ bs_status topk_tc_batched(const bs_topk_job *jobs, uint32_t n, int measure, uint
         const bs_topk_job &jb = jobs[bp.src[j]];
         tc::Job &J = p.job[j];
         tc::fill_job(J, jb.pcQ, jb.pcDB, jb.nQ, jb.nDB, jb.N);
-        J.tQ = add_tile(jb.Q, jb.nQ, jb.N, tc::BM);
-        J.tDB = add_tile(jb.DB, jb.nDB, jb.N, tc::BN);
+        uint8_t *at = w;
+        w += job_ws(jb);
+        J.tQ = add_tile(jb.Q, jb.nQ, jb.N, tc::BM, at);
+        J.tDB = add_tile(jb.DB, jb.nDB, jb.N, tc::BN, at);
         J.exclude_self = jb.exclude_self;
         J.self_off = 0;
         J.score = jb.score; J.idx = jb.idx; J.ws_key = nullptr; J.ws_idx = nullptr;

@@ -173,7 +173,9 @@ struct Job {
 
 template <int NJ>
 struct Args {
-    CUtensorMap maps[2];              // store: A (box SK/16 words x 128 rows), B (x 208 rows)
+    CUtensorMap maps[2];              // store: A (box SK/16 words x 128 rows), B (x 208 rows);
+                                      // one TMA top-k problem: the FP4 copies of Q and DB
+    CUtensorMap jmap[NJ > 1 ? NJ : 1][2];   // a batch's TMA configurations: each job's FP4 maps
     Job job[NJ];
     uint64_t block_start[MAXG + 1];   // block c: units [block_start[c], block_start[c+1])
     uint32_t njobs;
@@ -675,7 +677,8 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
     constexpr bool BT = NB > 0;
     constexpr bool AT = NOP == 0;
     constexpr int EPI0 = epi_warp0(!AT);   // first epilogue warp
-    static_assert(!BT || (MODE == MODE_TOPK && NJ == 1 && SK == 128), "TMA database operand: one top-k problem");
+    static_assert(!BT || (MODE == MODE_TOPK && SK == 128 && (NJ == 1 || NOP == 0)),
+                  "TMA database operand: one top-k problem, or a batch with both operands by TMA");
     static_assert(!AT || (BT && RD == 0), "TMA query operand: stages of both operands");
     static_assert(NG <= 2 || SHARED, "three epilogue groups share one heap per row");
     constexpr uint32_t NOPS = NOP > 0 ? NOP : 1, RDS = RD > 0 ? RD : 1, NBS = NB > 0 ? NB : 1;
@@ -826,7 +829,10 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
             uint32_t rs = 0;   // raw slots issued
             uint32_t bs = 0;   // TMA database slots (AT: stages) issued
             // the raw slots of one tile
-            auto issue_tile = [&](const Job &J, uint32_t rb, uint32_t tile) {
+            auto issue_tile = [&](uint32_t jx, uint32_t rb, uint32_t tile) {
+                const Job &J = jobs[jx];
+                const CUtensorMap *mapA = NJ > 1 ? &p.jmap[NJ > 1 ? jx : 0][0] : &p.maps[0];
+                const CUtensorMap *mapB = NJ > 1 ? &p.jmap[NJ > 1 ? jx : 0][1] : &p.maps[1];
                 const uint32_t nKc = J.nKc;
                 const uint32_t nsl = slots_per_tile<SK>(nKc);
                 for (uint32_t c = 0; c < nsl; ++c) {
@@ -836,8 +842,8 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
                         if (*abort_flag) return;
                         uint8_t *dst = op + ob * Smem::STAGE;
                         mbar_arrive_expect_tx(&b_full[ob], Smem::STAGE);
-                        tma_load_2d(dst, &p.maps[0], &b_full[ob], (int)(c * SK), (int)(rb * BM));
-                        tma_load_2d(dst + Smem::ABYTES, &p.maps[1], &b_full[ob], (int)(c * SK), (int)(tile * BN));
+                        tma_load_2d(dst, mapA, &b_full[ob], (int)(c * SK), (int)(rb * BM));
+                        tma_load_2d(dst + Smem::ABYTES, mapB, &b_full[ob], (int)(c * SK), (int)(tile * BN));
                         ++bs;
                         continue;
                     }
@@ -892,12 +898,12 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
                     if (item == ITEM_END) break;
                     cur.set_item(item);
                     const Job &J = jobs[cur.j];
-                    for (uint32_t tile = 0; tile < J.tiles && !*abort_flag; ++tile) issue_tile(J, cur.rb, tile);
+                    for (uint32_t tile = 0; tile < J.tiles && !*abort_flag; ++tile) issue_tile(cur.j, cur.rb, tile);
                 }
             } else {
                 TileSeq<false> seq;
                 seq.init_static(jobs, njobs, u_lo, n_my_tiles);
-                while (seq.next(wait, abort_flag) && !*abort_flag) issue_tile(jobs[seq.j], seq.rb, seq.tile);
+                while (seq.next(wait, abort_flag) && !*abort_flag) issue_tile(seq.j, seq.rb, seq.tile);
             }
             // every copy issued here has landed before the block may exit
             for (uint32_t i = rs > RDS ? rs - RDS : 0; i < rs; ++i)

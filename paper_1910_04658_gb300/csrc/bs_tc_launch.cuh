@@ -24,7 +24,7 @@ cudaError_t launch_topk(int cfg, const Args<NJ> &p, uint32_t grid, cudaStream_t 
     switch (cfg) {
 #define X(c, nop, ng, sk, rd, sh, nb)                                                                  \
     case c:                                                                                            \
-        if constexpr (nb == 0 || NJ == 1)                                                              \
+        if constexpr (nb == 0 || NJ == 1 || nop == 0)                                                  \
             go(pair_tc_kernel<MODE_TOPK, M, nop, ng, sk, rd, sh, NJ, nb>,                              \
                smem_bytes<nop, ng, sk, rd, sh, nb>(p.k) + jobs_smem, threads_for(ng, nop > 0));        \
         break;

@@ -105,11 +105,17 @@ def test_batched_plan_claims_whole_row_blocks():
     tab = [job(100_000, 100_000, 4096, 1 << 32), job(300, 300, 256, 2 << 32), job(5000, 20, 8192, 3 << 32)]
     assert B.bs_topk_batched_plan(tab, 50) == (1, 2)
     assert B.bs_topk_batched_plan([job(0, 10, 1024, 1 << 32)], 50) == (1, 0)
-    # workspace: a 256-byte counter, then each job's tiled Q (rows to 128) and DB (rows to 208)
+    # workspace: a 256-byte counter, then per job the larger of its tiled Q
+    # (rows to 128) and DB (rows to 208) and its FP4 copies (DB, and Q unless
+    # Q is DB: N / 2 bytes a row)
     ws = B.bs_topk_batched_workspace_bytes(tab, 50)
     a256 = lambda x: (x + 255) // 256 * 256
-    want = 256 + sum(a256(-(-nq // 128) * 128 * N // 8) + a256(-(-ndb // 208) * 208 * N // 8)
-                     for nq, ndb, N in ((100_000, 100_000, 4096), (300, 300, 256), (5000, 20, 8192)))
+
+    def per_job(nq, ndb, N):
+        tiled = a256(-(-nq // 128) * 128 * N // 8) + a256(-(-ndb // 208) * 208 * N // 8)
+        fp4 = a256(ndb * N // 2) + (0 if nq == ndb else a256(nq * N // 2))
+        return max(tiled, fp4)
+    want = 256 + sum(per_job(nq, ndb, N) for nq, ndb, N in ((100_000, 100_000, 4096), (300, 300, 256), (5000, 20, 8192)))
     assert ws == want, (ws, want)
     with pytest.raises(B.BinSketchError):   # N = 96: not a tensor-core shape
         B.bs_topk_batched_plan([job(10, 10, 96, 1 << 32)], 50)
