@@ -300,7 +300,10 @@ bs_status launch_merge(int measure, const float *ws_key, const uint32_t *ws_idx,
 // M, one TMEM lane per row), database tiles of 208 rows (the MMA's N)
 constexpr uint32_t kTcQueryRows = 128, kTcTileRows = 208;
 bool tc_supported(const uint32_t *Q, const uint32_t *DB, uint32_t N, uint32_t k);
-uint32_t tc_splits(uint32_t nQ, uint32_t nDB);
+// partial lists per row of the balanced schedule with tb-row database tiles
+uint32_t tc_splits(uint32_t nQ, uint32_t nDB, uint32_t tb = 208);
+// database rows per tile (the MMA's N) of a block configuration
+uint32_t tc_cfg_tile_rows(int cfg);
 // bytes of a k-chunk-tiled copy of an n-row sketch matrix in R-row blocks
 // (R = 128 for queries, 208 for a database)
 size_t tc_tiled_bytes(uint32_t n, uint32_t N, uint32_t R);
@@ -323,7 +326,7 @@ constexpr long long kTcInjectWaitLimit = 2000000ll;
 struct TcCallPlan {
     int cfg = -1;
     bool fp4_q = false, fp4_db = false;
-    uint32_t rounds = 0, q_split = 0, splits = 1, launches = 0;
+    uint32_t rounds = 0, q_split = 0, splits = 1, launches = 0, tile_rows = 208;
     size_t lists_bytes = 0;
 };
 // kept: how the caller keeps the database -- not at all (the call makes the

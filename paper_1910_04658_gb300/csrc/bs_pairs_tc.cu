@@ -169,18 +169,18 @@ static void make_schedule(uint32_t nj, const uint32_t *rbs, const uint32_t *tile
     s.splits = parts;
 }
 
-static void single_schedule(uint32_t nQ, uint32_t nDB, Schedule &s, uint64_t *unit_base) {
-    const uint32_t rbs = (nQ + BM - 1) / BM, tiles = (nDB + BN - 1) / BN;
+static void single_schedule(uint32_t nQ, uint32_t nDB, Schedule &s, uint64_t *unit_base, uint32_t tb = BN) {
+    const uint32_t rbs = (nQ + BM - 1) / BM, tiles = (nDB + tb - 1) / tb;
     const uint64_t cost = 1;
     make_schedule(1, &rbs, &tiles, &cost, unit_base, s);
 }
 
 static void fill_job(Job &J, const uint32_t *pcQ, const uint32_t *pcDB, uint32_t nQ, uint32_t nDB,
-                     uint32_t N) {
+                     uint32_t N, uint32_t tb = BN) {
     J.pcQ = pcQ; J.pcDB = pcDB;
     J.nQ = nQ; J.nDB = nDB; J.N = N; J.nKc = N / 128;
     J.rbs = (nQ + BM - 1) / BM;
-    J.tiles = (nDB + BN - 1) / BN;
+    J.tiles = (nDB + tb - 1) / tb;
     J.invL = (float)(1.0 / log1p(-1.0 / (double)N));
     J.log2N = (float)log2((double)N);
 }
@@ -261,8 +261,8 @@ static bool make_map_fp4(CUtensorMap *m, const void *ptr, uint32_t rows, uint32_
 
 static size_t tc_cfg_smem(int cfg, uint32_t k) {
     switch (cfg) {
-#define X(c, nop, ng, sk, rd, sh, nb) \
-    case c: return tc::smem_bytes<nop, ng, sk, rd, sh, nb>(k);
+#define X(c, nop, ng, sk, rd, sh, nb, tb) \
+    case c: return tc::smem_bytes<nop, ng, sk, rd, sh, nb, tb>(k);
         BS_TC_CONFIGS(X)
 #undef X
     }
@@ -275,9 +275,20 @@ static_assert(tc::kTcConfigs == kTcConfigCount && tc::kTcFirstTma == kTcFirstTma
 bool tc_cfg_tma(int cfg) { return cfg >= tc::kTcFirstTma; }
 
 // configurations with no widening warps: the query operand by TMA as well
+// database rows per tile (the MMA's N) of a configuration
+uint32_t tc_cfg_tile_rows(int cfg) {
+    switch (cfg) {
+#define X(c, nop, ng, sk, rd, sh, nb, tb) \
+    case c: return tb;
+        BS_TC_CONFIGS(X)
+#undef X
+    }
+    return tc::BN;
+}
+
 static bool tc_cfg_query_tma(int cfg) {
     switch (cfg) {
-#define X(c, nop, ng, sk, rd, sh, nb) \
+#define X(c, nop, ng, sk, rd, sh, nb, tb) \
     case c: return nop == 0;
         BS_TC_CONFIGS(X)
 #undef X
@@ -326,11 +337,11 @@ bool tc_store_supported(const uint32_t *A, const uint32_t *B, uint32_t N) {
            (reinterpret_cast<uintptr_t>(B) & 15u) == 0;
 }
 
-uint32_t tc_splits(uint32_t nQ, uint32_t nDB) {
+uint32_t tc_splits(uint32_t nQ, uint32_t nDB, uint32_t tb) {
     if (nQ == 0 || nDB == 0) return 1;
     tc::Schedule s;
     uint64_t ub;
-    tc::single_schedule(nQ, nDB, s, &ub);
+    tc::single_schedule(nQ, nDB, s, &ub, tb);
     return s.splits;
 }
 
@@ -393,7 +404,8 @@ bs_status tc_call_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, int cf
     pl.rounds = pl.fp4_db ? rbs / G : 0;
     pl.q_split = (uint32_t)std::min<uint64_t>(nQ, (uint64_t)pl.rounds * G * tc::BM);
     const uint32_t nQ2 = nQ - pl.q_split;
-    pl.splits = nQ2 > 0 ? tc_splits(nQ2, nDB) : 1;
+    pl.tile_rows = tc_cfg_tile_rows(pl.cfg);
+    pl.splits = nQ2 > 0 ? tc_splits(nQ2, nDB, pl.tile_rows) : 1;
     pl.lists_bytes = pl.splits > 1 ? (size_t)pl.splits * nQ2 * k * 8 : 0;
     pl.launches = (kept != KEPT_NONE ? 0 : 1) + (pl.fp4_q ? (same ? 0 : 1) : 1) +
                   (pl.rounds > 0 ? 1 : 0) + (nQ2 > 0 ? 1 : 0) + (pl.splits > 1 ? 1 : 0);
@@ -458,11 +470,11 @@ bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uin
     // blocks, or with the balanced ranges (and partial lists when splits > 1)
     auto run = [&](uint32_t q_lo, uint32_t rows, bool rounds) -> bs_status {
         memset(&p, 0, sizeof(p));
-        if (pl.fp4_db && !tc::make_map_fp4(&p.maps[1], db_area, nDB, N, tc::BN)) return BS_ERR_CUDA;
+        if (pl.fp4_db && !tc::make_map_fp4(&p.maps[1], db_area, nDB, N, pl.tile_rows)) return BS_ERR_CUDA;
         if (pl.fp4_q && !tc::make_map_fp4(&p.maps[0], q_fp4 + (size_t)q_lo * (N / 2), rows, N, tc::BM))
             return BS_ERR_CUDA;
         tc::Job &J = p.job[0];
-        tc::fill_job(J, pcQ + q_lo, pcDB, rows, nDB, N);
+        tc::fill_job(J, pcQ + q_lo, pcDB, rows, nDB, N, pl.tile_rows);
         J.tQ = tQ + (size_t)(q_lo / tc::BM) * (N / 128) * tc::BM;   // q_lo is a multiple of 128
         J.tDB = tDB;
         J.exclude_self = exclude_self;
@@ -478,7 +490,7 @@ bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uin
             for (uint32_t c = 0; c <= s.grid; ++c) s.block_start[c] = (uint64_t)c * per;
             J.unit_base = 0;
         } else {
-            tc::single_schedule(rows, nDB, s, &J.unit_base);
+            tc::single_schedule(rows, nDB, s, &J.unit_base, pl.tile_rows);
         }
         if (s.splits > 1) {
             J.ws_key = reinterpret_cast<float *>(lists);
@@ -650,13 +662,13 @@ bs_status topk_tc_batched(const bs_topk_job *jobs, uint32_t n, int measure, uint
             add(jb.DB, jb.nDB, db4);
             if (!same) add(jb.Q, jb.nQ, q4);
             tc::Job &J = p.job[j];
-            tc::fill_job(J, jb.pcQ, jb.pcDB, jb.nQ, jb.nDB, jb.N);
+            tc::fill_job(J, jb.pcQ, jb.pcDB, jb.nQ, jb.nDB, jb.N, tc_cfg_tile_rows(cfg));
             J.exclude_self = jb.exclude_self;
             J.self_off = 0;
             J.score = jb.score; J.idx = jb.idx; J.ws_key = nullptr; J.ws_idx = nullptr;
             J.unit_base = bp.item_base[j];
             if (!tc::make_map_fp4(&p.jmap[j][0], q4, jb.nQ, jb.N, tc::BM) ||
-                !tc::make_map_fp4(&p.jmap[j][1], db4, jb.nDB, jb.N, tc::BN))
+                !tc::make_map_fp4(&p.jmap[j][1], db4, jb.nDB, jb.N, tc_cfg_tile_rows(cfg)))
                 return BS_ERR_CUDA;
         }
         wj.counter = counter;   // zeroed here, ahead of the pair kernel on this stream

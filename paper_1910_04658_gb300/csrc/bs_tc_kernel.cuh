@@ -66,7 +66,6 @@ constexpr int BN = kTcTileRows;            // database rows per tile (UMMA N)
 constexpr int BNP = 256;                   // per-column arrays padded to whole 32-column chunks
 constexpr int KCW = 4;                     // packed words per k-chunk (128 bits)
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t A_COL = 2 * BN;         // 416: query operand slots (SK / 4 columns each)
 constexpr uint32_t SF_COL = 480;           // unit scale factors (A at +0, B at +16)
 constexpr int MAXG = 192;                  // most persistent blocks per launch
 constexpr int MAXJ = BS_TOPK_BATCH_MAX;    // most jobs per batched launch
@@ -87,10 +86,10 @@ __host__ __device__ constexpr int threads_for(int NG, bool widen = true) { retur
 // sits in TMEM, SK / 4 columns per slot.  A raw slot holds the same bits
 // packed as they arrive: tiled, [k-chunk][rows] x 16 bytes; through the tensor
 // maps, [rows][SK / 4 bytes].
-template <int SK>
+template <int SK, int TB = BN>
 struct Geo {
     static_assert(SK == 128 || SK == 64, "slot width");
-    static constexpr int BYTES = BN * SK;                   // database operand bytes per slot
+    static constexpr int BYTES = TB * SK;                   // database operand bytes per slot
     static constexpr int TCOLS = SK / 4;                    // TMEM columns of a query operand slot
     static constexpr int MMAS = SK / 32;                    // K = 64 (32 bytes) per MMA
     static constexpr int WPS = SK / 16;                     // packed words per slot and row
@@ -99,7 +98,7 @@ struct Geo {
     static constexpr uint64_t LAYOUT = SK == 128 ? 2 : 4;   // descriptor swizzle code
     static constexpr int RAW_ROW = WPS * 4;                 // packed bytes per row
     static constexpr int RAW_A = BM * RAW_ROW;
-    static constexpr int RAW_B = BN * RAW_ROW;
+    static constexpr int RAW_B = TB * RAW_ROW;
     static constexpr int RAW_SLOT = (RAW_A + RAW_B + 1023) / 1024 * 1024;
     static_assert(BYTES % (8 * SK) == 0, "swizzle atom alignment");
     static_assert(RAW_A % 1024 == 0, "raw slot alignment");
@@ -126,19 +125,21 @@ constexpr float LOG2_FILTER_SLACK = -1.76126e-4f;   // log2(FILTER_SLACK), folde
 // Shared-memory layout for NOP operand slots and RD raw slots of SK bytes
 // per row and NG epilogue groups (offsets from the 1024-aligned base); the
 // heaps follow.
-template <int NOP, int NG, int SK, int RD, int NB = 0, bool SH = false>
+template <int NOP, int NG, int SK, int RD, int NB = 0, bool SH = false, int TB = BN>
 struct Smem {
-    static_assert(NOP * Geo<SK>::TCOLS <= (int)(SF_COL - A_COL), "query operand slots exceed their TMEM columns");
+    using G = Geo<SK, TB>;
+    static_assert(NOP * G::TCOLS <= (int)SF_COL - 2 * TB, "query operand slots exceed their TMEM columns");
+    static_assert(2 * TB <= (int)SF_COL, "two accumulators and the scale factors exceed TMEM");
     // NOP = 0: NB stages of both operands, filled by TMA from the FP4 copies
     // (query block BM x SK bytes, then database tile BN x SK bytes);
     // NB > 0: NB database slots filled by TMA from the FP4 copy, raw slots hold
     // the query operand only; NB = 0: NOP database slots the widening warps fill
     static constexpr int ABYTES = BM * SK;
-    static constexpr int STAGE = ABYTES + Geo<SK>::BYTES;
+    static constexpr int STAGE = ABYTES + G::BYTES;
     static_assert(ABYTES % 1024 == 0 && STAGE % 1024 == 0, "stage alignment");
     static constexpr int op = 0;
-    static constexpr int raw = op + (NOP == 0 ? NB * STAGE : (NB > 0 ? NB : NOP) * Geo<SK>::BYTES);
-    static constexpr int col = raw + RD * (NB > 0 ? Geo<SK>::RAW_A : Geo<SK>::RAW_SLOT);   // [2 tiles][3][BNP] floats
+    static constexpr int raw = op + (NOP == 0 ? NB * STAGE : (NB > 0 ? NB : NOP) * G::BYTES);
+    static constexpr int col = raw + RD * (NB > 0 ? G::RAW_A : G::RAW_SLOT);   // [2 tiles][3][BNP] floats
     static constexpr int bars = col + 2 * 3 * BNP * 4;
     static constexpr int thr = bars + 512;                      // [NG][BM] key, idx, size
     static constexpr int lock = thr + NG * BM * 12;             // [BM] shared-heap row locks
@@ -283,8 +284,9 @@ __device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
 // Instruction descriptor of the block-scaled MMA: A = B = E2M1 (code 1 of the
 // mxf4 kind), both K-major, scale factors UE8M0 (bit 23), N = 208, M = 128,
 // scale-factor selectors 0, dense K = 64.
-constexpr uint32_t IDESC = (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | (1u << 23) |
-                           ((uint32_t)(BM >> 4) << 24);
+__host__ __device__ constexpr uint32_t idesc_for(int tb) {
+    return (1u << 7) | (1u << 10) | ((uint32_t)(tb >> 3) << 17) | (1u << 23) | ((uint32_t)(BM >> 4) << 24);
+}
 constexpr uint32_t UNIT_SCALES = 0x7F7F7F7Fu;   // four UE8M0 2^0
 
 // Widen the WPS packed words x[] of one row into FP4 and store them into the
@@ -663,11 +665,16 @@ __device__ __forceinline__ uint32_t block_of(const Args<NJ> &p, uint64_t x, uint
     return lo;
 }
 
-template <int MODE, int M, int NOP, int NG, int SK, int RD, bool SHARED, int NJ, int NB = 0>
+template <int MODE, int M, int NOP, int NG, int SK, int RD, bool SHARED, int NJ, int NB = 0, int TB = BN>
 __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
     pair_tc_kernel(const __grid_constant__ Args<NJ> p) {
-    using Smem = tc::Smem<NOP, NG, SK, RD, NB, SHARED>;
-    using G = Geo<SK>;
+    // TB: database rows per tile (the MMA's N)
+    using Smem = tc::Smem<NOP, NG, SK, RD, NB, SHARED, TB>;
+    using G = Geo<SK, TB>;
+    constexpr uint32_t IDESC_T = idesc_for(TB);
+    constexpr uint32_t A_COL_T = 2 * TB;   // query operand slots in TMEM (when widened)
+    static_assert(TB == BN || NOP == 0, "other tile heights: both operands by TMA");
+    static_assert(TB % 16 == 0 && TB <= 256, "MMA N");
     // BT: the database operand arrives already widened, by TMA from an FP4
     // copy in global memory (tensor map p.maps[1], 128-byte swizzle), into NB
     // shared-memory slots; the widening warps write only the query operand.
@@ -788,7 +795,7 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
                 const uint32_t ab = t & 1;
                 if (t >= 2) wait(&acc_empty[ab], ((t >> 1) - 1) & 1);
                 tc_fence_after();
-                const uint32_t d_tmem = tmem + ab * BN;
+                const uint32_t d_tmem = tmem + ab * TB;
                 for (uint32_t c = 0; c < nsl; ++c, ++sl) {
                     const uint32_t o = sl % NOPS;
                     const uint32_t ob = BT ? sl % NBS : o;   // database slot (AT: stage)
@@ -802,13 +809,13 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
 #pragma unroll
                             for (int kk = 0; kk < G::MMAS; ++kk)
                                 mma_fp4_ss(d_tmem, sw_desc<SK>(a_addr + kk * 32), sw_desc<SK>(b_addr + kk * 32),
-                                           IDESC, sfa, sfb, (c | (uint32_t)kk) != 0);
+                                           IDESC_T, sfa, sfb, (c | (uint32_t)kk) != 0);
                         } else {
-                            const uint32_t a_tmem = tmem + A_COL + o * G::TCOLS;
+                            const uint32_t a_tmem = tmem + A_COL_T + o * G::TCOLS;
                             const uint32_t b_addr = smem_u32(op + ob * G::BYTES);
 #pragma unroll
                             for (int kk = 0; kk < G::MMAS; ++kk)
-                                mma_fp4(d_tmem, a_tmem + 8 * kk, sw_desc<SK>(b_addr + kk * 32), IDESC, sfa, sfb,
+                                mma_fp4(d_tmem, a_tmem + 8 * kk, sw_desc<SK>(b_addr + kk * 32), IDESC_T, sfa, sfb,
                                         (c | (uint32_t)kk) != 0);
                         }
                     }
@@ -843,7 +850,7 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
                         uint8_t *dst = op + ob * Smem::STAGE;
                         mbar_arrive_expect_tx(&b_full[ob], Smem::STAGE);
                         tma_load_2d(dst, mapA, &b_full[ob], (int)(c * SK), (int)(rb * BM));
-                        tma_load_2d(dst + Smem::ABYTES, mapB, &b_full[ob], (int)(c * SK), (int)(tile * BN));
+                        tma_load_2d(dst + Smem::ABYTES, mapB, &b_full[ob], (int)(c * SK), (int)(tile * TB));
                         ++bs;
                         continue;
                     }
@@ -861,20 +868,20 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
                         if (bs >= (uint32_t)NBS) wait(&b_empty[ob], ((bs / NBS) - 1) & 1);
                         if (*abort_flag) return;
                         mbar_arrive_expect_tx(&b_full[ob], G::BYTES);
-                        tma_load_2d(op + ob * G::BYTES, &p.maps[1], &b_full[ob], (int)(c * SK), (int)(tile * BN));
+                        tma_load_2d(op + ob * G::BYTES, &p.maps[1], &b_full[ob], (int)(c * SK), (int)(tile * TB));
                         ++bs;
                         continue;
                     }
                     if (MODE == MODE_STORE) {   // strided rows through the tensor maps
                         mbar_arrive_expect_tx(&raw_full[o], G::RAW_A + G::RAW_B);
                         tma_load_2d(dst, &p.maps[0], &raw_full[o], (int)(G::WPS * c), (int)(rb * BM));
-                        tma_load_2d(dst + G::RAW_A, &p.maps[1], &raw_full[o], (int)(G::WPS * c), (int)(tile * BN));
+                        tma_load_2d(dst + G::RAW_A, &p.maps[1], &raw_full[o], (int)(G::WPS * c), (int)(tile * TB));
                     } else {                    // one contiguous run per operand
                         const uint32_t kc0 = c * G::KPS;
                         const uint32_t np = nKc - kc0 < (uint32_t)G::KPS ? nKc - kc0 : (uint32_t)G::KPS;
-                        mbar_arrive_expect_tx(&raw_full[o], np * (BM + BN) * 16);
+                        mbar_arrive_expect_tx(&raw_full[o], np * (BM + TB) * 16);
                         bulk_load(dst, J.tQ + ((size_t)rb * nKc + kc0) * BM, np * BM * 16, &raw_full[o]);
-                        bulk_load(dst + G::RAW_A, J.tDB + ((size_t)tile * nKc + kc0) * BN, np * BN * 16,
+                        bulk_load(dst + G::RAW_A, J.tDB + ((size_t)tile * nKc + kc0) * TB, np * TB * 16,
                                   &raw_full[o]);
                     }
                     ++rs;
@@ -916,8 +923,8 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
         // thread e owns query row e -- the row of its warp's TMEM lane quarter --
         // and database rows e and e + 128 of a slot
         const int e = (warp & 3) * 32 + lane;   // 0..127
-        const bool two_b = e + 128 < BN;
-        const uint32_t a_lane = tmem + ((uint32_t)((warp & 3) * 32) << 16) + A_COL;
+        const bool two_b = e + 128 < TB;
+        const uint32_t a_lane = tmem + ((uint32_t)((warp & 3) * 32) << 16) + A_COL_T;
         uint32_t sl = 0;
         TileSeq<DYN> seq;
         if (DYN) seq.init_dynamic(jobs, njobs, item_full, item_ring);
@@ -937,8 +944,8 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
                 } else {
                     const int valid = (int)(nKc - c * G::KPS);
                     raw_row<SK>(src, BM * 16, 16, e, valid, xa);
-                    if (!BT) raw_row<SK>(src + G::RAW_A, BN * 16, 16, e, valid, xb0);
-                    if (!BT && two_b) raw_row<SK>(src + G::RAW_A, BN * 16, 16, e + 128, valid, xb1);
+                    if (!BT) raw_row<SK>(src + G::RAW_A, TB * 16, 16, e, valid, xb0);
+                    if (!BT && two_b) raw_row<SK>(src + G::RAW_A, TB * 16, 16, e + 128, valid, xb1);
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&raw_empty[ro]);   // the raw slot may be refilled
@@ -961,11 +968,12 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
         const int quarter = warp & 3;              // TMEM lanes this warp may access
         const int r = quarter * 32 + lane;         // row within the block
         // tile columns of this group
-        // (two groups: 96 and 112 of the 208 columns, three: 64, 64 and 80 --
-        // the most even splits whose 32-column TMEM loads all start at a
-        // multiple of 32)
-        const int c_lo = NG == 1 ? 0 : (NG == 2 ? grp * GSPLIT : grp * 64);
-        const int c_hi = NG == 1 ? BN : (NG == 2 ? (grp == 1 ? BN : GSPLIT) : (grp == NG - 1 ? BN : (grp + 1) * 64));
+        // (two groups: 96 and 112 of 208 columns; three: 64, 64 and 80 of 208,
+        // 80 each of 240 -- even splits whose TMEM loads of 32 or 16 columns
+        // all start at a multiple of their width)
+        constexpr int G3 = TB == 240 ? 80 : 64;
+        const int c_lo = NG == 1 ? 0 : (NG == 2 ? grp * GSPLIT : grp * G3);
+        const int c_hi = NG == 1 ? TB : (NG == 2 ? (grp == 1 ? TB : GSPLIT) : (grp == NG - 1 ? TB : (grp + 1) * G3));
         // row constants of the current row block (set at each segment start)
         uint32_t q = 0, a = 0;
         bool row_ok = false;
@@ -1046,7 +1054,7 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
                     const uint32_t j = (uint32_t)(c_lo + e + 128 * i);
-                    const uint32_t col = tile * BN + j;
+                    const uint32_t col = tile * TB + j;
                     b_pre[i] = (j < (uint32_t)c_hi && col < J.nDB) ? __ldg(J.pcDB + col) : 0u;
                 }
             }
@@ -1082,7 +1090,7 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
                         const uint32_t j = (uint32_t)(c_lo + e + 128 * i);
-                        const uint32_t col = ntile * BN + j;
+                        const uint32_t col = ntile * TB + j;
                         b_pre[i] = (j < (uint32_t)c_hi && col < J2.nDB) ? __ldg(J2.pcDB + col) : 0u;
                     }
                 }
@@ -1091,19 +1099,20 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
             const uint32_t ab = t & 1;
             wait(&acc_full[ab], (t >> 1) & 1);
             tc_fence_after();
-            const uint32_t col0 = tile * BN;
+            const uint32_t col0 = tile * TB;
             d_col0 = col0;
             d_cv = cv;
             // every lane stays in the loops below (they vote); dead rows admit nothing
             const bool live = row_ok && !*abort_flag;
-            const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + ab * BN;
+            const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + ab * TB;
 #pragma unroll 1
-            for (int ch = c_lo / 32; ch * 32 < c_hi; ++ch) {
-                const int width = c_hi - ch * 32 < 32 ? c_hi - ch * 32 : 32;   // 32, or 16 at the end
+            for (int c0 = c_lo, width = 0; c0 < c_hi; c0 += width) {
+                // 32 columns where aligned and in range, else 16
+                width = ((c0 & 31) == 0 && c0 + 32 <= c_hi) ? 32 : 16;
                 uint32_t v[32];
-                if (width == 32) tmem_ld32_async(trow + ch * 32, v);
-                else tmem_ld16_async(trow + ch * 32, v);
-                const uint32_t col_c = col0 + ch * 32;
+                if (width == 32) tmem_ld32_async(trow + c0, v);
+                else tmem_ld16_async(trow + c0, v);
+                const uint32_t col_c = col0 + c0;
                 if (MODE == MODE_STORE) {
                     tmem_wait();
                     if (live) {
@@ -1112,7 +1121,7 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
 #pragma unroll 4
                         for (int jj = 0; jj < 32; ++jj) {
                             if (jj >= width || col_c + jj >= J.nDB) break;
-                            const int j = ch * 32 + jj;
+                            const int j = c0 + jj;
                             const uint32_t c = (uint32_t)__uint_as_float(v[jj]);
                             const uint32_t b = (uint32_t)cv[j].x;
                             const float lnB = cv[j].y;
@@ -1149,7 +1158,7 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
                 uint32_t mask = 0;
 #pragma unroll
                 for (int jj = 0; jj < 32; ++jj) {
-                    const int j = ch * 32 + jj;
+                    const int j = c0 + jj;
                     const float cf = __uint_as_float(v[jj]);   // exact count
                     // U' = N - min(a + b - c, N - 1) = max(N - a - b + c, 1), exact in FP32
                     const float2 bf = cv[j];
@@ -1179,7 +1188,7 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
                             const uint32_t jj = __ffs(m) - 1;
                             m &= m - 1;
                             const uint32_t c = (uint32_t)__uint_as_float(select32(v, jj));
-                            const int j = ch * 32 + (int)jj;
+                            const int j = c0 + (int)jj;
                             if (SHARED) {
                                 const float root = consider_shared<M>(hent, thr_key, heap_size, row_lock,
                                                                       r, col_c + jj, c, (uint32_t)cv[j].x, a, lnA,
@@ -1204,7 +1213,7 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
                             const uint32_t jj = __ffs(mask) - 1;
                             mask &= mask - 1;
                             const uint32_t c = (uint32_t)__uint_as_float(select32(v, jj));
-                            cb[nbuf * BM + r] = (c << 8) | (uint32_t)(ch * 32 + (int)jj);
+                            cb[nbuf * BM + r] = (c << 8) | (uint32_t)(c0 + (int)jj);
                             ++nbuf;
                         }
                     }
@@ -1317,28 +1326,28 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
 // cores at the cost of overlap between widening and MMA.
 // ---------------------------------------------------------------------------
 #define BS_TC_CONFIGS(X)             \
-    X(0, 2, 2, 128, 4, false, 0)     \
-    X(1, 2, 2, 128, 4, true, 0)      \
-    X(2, 4, 2, 64, 8, false, 0)      \
-    X(3, 4, 2, 64, 8, true, 0)       \
-    X(4, 2, 1, 128, 4, false, 0)     \
-    X(5, 2, 2, 128, 6, false, 0)     \
-    X(6, 2, 2, 128, 2, false, 0)     \
-    X(7, 2, 2, 128, 6, true, 0)      \
-    X(8, 2, 1, 128, 2, false, 0)     \
-    X(9, 1, 1, 128, 2, false, 0)     \
-    X(10, 2, 2, 128, 4, false, 3)    \
-    X(11, 2, 2, 128, 4, true, 4)     \
-    X(12, 0, 3, 128, 0, true, 3)     \
-    X(13, 0, 3, 128, 0, true, 2)     \
-    X(14, 0, 2, 128, 0, true, 3)
+    X(0, 2, 2, 128, 4, false, 0, 208)     \
+    X(1, 2, 2, 128, 4, true, 0, 208)      \
+    X(2, 4, 2, 64, 8, false, 0, 208)      \
+    X(3, 4, 2, 64, 8, true, 0, 208)       \
+    X(4, 2, 1, 128, 4, false, 0, 208)     \
+    X(5, 2, 2, 128, 6, false, 0, 208)     \
+    X(6, 2, 2, 128, 2, false, 0, 208)     \
+    X(7, 2, 2, 128, 6, true, 0, 208)      \
+    X(8, 2, 1, 128, 2, false, 0, 208)     \
+    X(9, 1, 1, 128, 2, false, 0, 208)     \
+    X(10, 2, 2, 128, 4, false, 3, 208)    \
+    X(11, 2, 2, 128, 4, true, 4, 208)     \
+    X(12, 0, 3, 128, 0, true, 3, 240)     \
+    X(13, 0, 3, 128, 0, true, 2, 240)     \
+    X(14, 0, 2, 128, 0, true, 3, 208)
 constexpr int kTcConfigs = 15;
 constexpr int kTcFirstTma = 10;         // configurations from here on read the FP4 database copy
 constexpr size_t kSmemLimit = 232448;   // 227 KB per block
 
-template <int NOP, int NG, int SK, int RD, bool SH, int NB = 0>
+template <int NOP, int NG, int SK, int RD, bool SH, int NB = 0, int TB = BN>
 __host__ __device__ constexpr size_t smem_bytes(uint32_t k) {
-    return 1024 + Smem<NOP, NG, SK, RD, NB, SH>::heap + (size_t)(SH ? 1 : NG) * k * BM * 8;
+    return 1024 + Smem<NOP, NG, SK, RD, NB, SH, TB>::heap + (size_t)(SH ? 1 : NG) * k * BM * 8;
 }
 
 // Launch of one configuration for one measure (defined in the per-measure

@@ -22,11 +22,11 @@ cudaError_t launch_topk(int cfg, const Args<NJ> &p, uint32_t grid, cudaStream_t 
     // a batch's job table is copied to shared memory behind the heaps
     const size_t jobs_smem = NJ > 1 ? (size_t)p.njobs * sizeof(Job) : 0;
     switch (cfg) {
-#define X(c, nop, ng, sk, rd, sh, nb)                                                                  \
+#define X(c, nop, ng, sk, rd, sh, nb, tb)                                                              \
     case c:                                                                                            \
         if constexpr (nb == 0 || NJ == 1 || nop == 0)                                                  \
-            go(pair_tc_kernel<MODE_TOPK, M, nop, ng, sk, rd, sh, NJ, nb>,                              \
-               smem_bytes<nop, ng, sk, rd, sh, nb>(p.k) + jobs_smem, threads_for(ng, nop > 0));        \
+            go(pair_tc_kernel<MODE_TOPK, M, nop, ng, sk, rd, sh, NJ, nb, tb>,                          \
+               smem_bytes<nop, ng, sk, rd, sh, nb, tb>(p.k) + jobs_smem, threads_for(ng, nop > 0));    \
         break;
         BS_TC_CONFIGS(X)
 #undef X

@@ -60,7 +60,7 @@ def test_tensor_core_plan_parts_match_the_persistent_schedule():
     # The default tensor-core configuration for N = 4096, k = 50 reads FP4
     # copies of both operands: R = rbs // G rounds of whole 128-row blocks go
     # to the G blocks first (block c: row blocks [c R, (c + 1) R)), the rows
-    # left over run as a second launch whose U = row blocks x 208-row database
+    # left over run as a second launch whose U = row blocks x 240-row database
     # tiles are dealt out as equal contiguous ranges, block c starting at unit
     # ceil(c U / G): unit x then sits in block floor(x G / U), and the parts of
     # a row block are the blocks it spans.
@@ -68,8 +68,8 @@ def test_tensor_core_plan_parts_match_the_persistent_schedule():
 
     G = 148
 
-    def parts(nq, ndb):
-        rbs, T = (nq + 127) // 128, (ndb + 207) // 208
+    def parts(nq, ndb):   # the default configuration's database tiles have 240 rows
+        rbs, T = (nq + 127) // 128, (ndb + 239) // 240
         U = rbs * T
         g = min(G, U)
         first = lambda x: (x * g) // U
