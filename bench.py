@@ -350,7 +350,8 @@ def run_ours(args, rank, world, dist):
             "topk_variant": "tensor cores (tcgen05)" if use_tc else "CUDA cores (POPC)",
             "topk_db_splits": splits,
             "popc_variant_topk_ms": t_popc * 1e3 if t_popc else None,
-            "wall_s_timed_region": wall},
+            "wall_s_timed_region": wall,
+            "e2e_ms_steps": [round(x * 1e3, 3) for x in e2e_s]},
         "e2e": {"value": e2e_value, "unit": "pair-estimates/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,

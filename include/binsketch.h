@@ -250,10 +250,11 @@ bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
  *          3 database slots, 2 query slots, 2 groups
  *   c = 11: as c = 10 with 4 database slots and the shared heap
  *   c = 12: both operands from FP4 copies by TMA (the query block's too; for
- *          Q == DB one copy serves both), no widening warps, 3 stages, 3
- *          epilogue groups sharing one heap per row
+ *          Q == DB one copy serves both), no widening warps, database tiles
+ *          of 240 rows (208 for every other c), 3 stages, 3 epilogue groups
+ *          sharing one heap per row
  *   c = 13: as c = 12 with 2 stages (every k up to BS_TOPK_K_MAX fits)
- *   c = 14: as c = 12 with 2 epilogue groups
+ *   c = 14: as c = 12 with 208-row tiles and 2 epilogue groups
  * The default, for bs_topk / bs_topk_ex / bs_topk_shard / bs_topk_noalloc,
  * is the first of 12, 13, 14, 10, 11 that fits k, else the first of 0, 1,
  * ..., 9 that fits; calls with a database kept tiled (bs_topk_pretiled) use

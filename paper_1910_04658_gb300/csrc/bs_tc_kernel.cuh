@@ -5,9 +5,9 @@
 // The common-bit count <a_s, b_s> is a dot product of two 0/1 vectors, i.e.
 // one entry of the product Q * DB^T of the 0/1 sketch matrices.  Packed bits
 // cannot feed tcgen05.mma directly (there is no 1-bit kind, and kind::i8 is
-// not available on sm_103a), so every bit is widened in shared memory to one
-// 4-bit E2M1 element of a block-scaled FP4 MMA (kind::mxf4): a set bit becomes
-// 0x2 = 1.0, a clear bit 0, and every 32-element block carries the unit scale
+// not available on sm_103a), so every bit is widened to one 4-bit E2M1
+// element of a block-scaled FP4 MMA (kind::mxf4): a set bit becomes 0x2 =
+// 1.0, a clear bit 0, and every 32-element block carries the unit scale
 // UE8M0 127 = 2^0, held once in TMEM.  Products are 0 or 1 and every partial
 // sum is an integer <= N <= 8192 < 2^24, so the FP32 accumulator IS the exact
 // count.  A 32-bit word w of a row becomes the 16 bytes
@@ -17,36 +17,37 @@
 //
 // Block (one per SM, persistent): a job table (one job for a single call,
 // up to BS_TOPK_BATCH_MAX for the batched form) is cut into work units
-// (job, 128-row query block, 208-row database tile), numbered job by job and
-// row block by row block; block c takes the contiguous range
-// [block_start[c], block_start[c+1]) that the host balanced by cost.  A row
-// block cut between blocks yields one partial list per block ("part"), merged
-// afterwards.  An operand slot covers SK * 2 sketch bits (128 or 256) of a
-// tile's 128 query and 208 database rows.  The query operand (MMA A) is fed
-// from TMEM and the database operand (MMA B) from shared memory, so shared
-// memory carries the widened bits of the 208 database rows only: per 256-bit
-// slot 26 KB written by the widening warps and 26 KB read by the MMA, about
-// the 416 cycles the MMAs themselves take.
-//   warp 0     TMEM owner (512 columns: two 208-column accumulators, the
-//              query operand slots and the unit scale factors) and
-//              single-thread MMA issuer: tcgen05.mma.kind::mxf4.block_scale
-//              with A in TMEM (M=128, N=208, K=64), 2 or 4 per slot
-//   warp 1     TMA producer (one thread): for every slot, two asynchronous
-//              copies of the packed bits into a RD-deep ring of raw slots,
-//              completion on mbarriers.  Top-k reads k-chunk-tiled copies (Q
-//              in 128-row, DB in 208-row blocks), so each operand of a slot
-//              is one contiguous run (cp.async.bulk); the full-matrix store
-//              reads the row-major sketches through 2-D tensor maps (a 128-row
-//              and a 208-row box; rows and words past the end arrive as
-//              zeros), which costs one request per row
-//   warps 2-5  widening, one query row per thread (the row of its TMEM lane,
-//              written with tcgen05.st) and database rows e and e + 128 (into
-//              the SK-byte-swizzled K-major layout the B descriptors point at)
-//   warps 6+   epilogue, one or two groups of 4 warps, one query row per
-//              thread, 32 TMEM columns per tcgen05.ld.  Top-k: a closed-form
-//              bound on the union count admits only pairs that can beat the
-//              row's current k-th best, whose exact FP32 estimate then enters
-//              a per-row heap in shared memory.  Store: the count and the
+// (job, 128-row query block, TB-row database tile).  One problem: block c
+// takes the contiguous unit range [block_start[c], block_start[c+1]) (a row
+// block cut between blocks yields one partial list per block, a "part",
+// merged afterwards); a batch: blocks claim whole row blocks from a device
+// counter at run time.  An operand slot covers SK * 2 sketch bits (128 or
+// 256) of a tile.  Three ways to feed the operands:
+//  - both by TMA (NOP = 0, the default): the host writes FP4 copies of Q and
+//    DB once per call; per slot one stage holds the query block's and the
+//    database tile's slices (128-byte swizzle, straight from the copies), the
+//    MMA reads both from shared memory.  TB = 240 (TMEM: two 240-column
+//    accumulators and the scale factors).  Warps: 0 MMA, 1 TMA, 2+ epilogue.
+//  - database by TMA, query widened (NB > 0, NOP > 0): the database tile
+//    from its FP4 copy, the query's packed bits through a raw ring and
+//    widened into TMEM by warps 2-5 (tcgen05.st; A fed from TMEM).
+//  - both widened (NB = 0): the packed bits of both (bulk copies of k-chunk
+//    tiles, or 2-D tensor maps over row-major sketches for the full-matrix
+//    store) through a raw ring; warps 2-5 widen the query row into TMEM and
+//    database rows into swizzled shared memory (+ fence.proxy.async).
+//    TB = 208: TMEM holds two 208-column accumulators, the query slots and
+//    the scale factors.
+//   warp 0     TMEM owner (all 512 columns) and single-thread MMA issuer:
+//              tcgen05.mma.kind::mxf4.block_scale (M=128, N=TB, K=64), 2 or
+//              4 per slot, completion by tcgen05.commit to mbarriers
+//   warp 1     producer (one thread): TMA / bulk copies into the stage or
+//              raw rings, completion on mbarriers
+//   epilogue   one to three groups of 4 warps, one query row per thread, 32
+//              or 16 TMEM columns per tcgen05.ld.  Top-k: a closed-form bound
+//              on the union count admits only pairs that can beat the row's
+//              current k-th best, whose exact FP32 estimate then enters a
+//              per-row heap in shared memory (one per group, or one shared by
+//              the groups under a per-row lock).  Store: the count and the
 //              requested estimates of every pair are written out.
 // All waits are bounded (mbarrier try_wait against a cycle budget carried in
 // the arguments); a timeout raises BS_ERR_TIMEOUT, the block drains its
