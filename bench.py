@@ -112,10 +112,13 @@ def measured_peaks():
         return {}
 
 
-def profile_traffic(kernel_file, name):
-    """dram bytes per launch recorded under profiles/ for the current kernel source, else None."""
-    src = os.path.join(ROOT, "paper_1910_04658_gb300", "csrc", kernel_file)
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+def profile_traffic(files, name):
+    """dram bytes per call recorded under profiles/ for the current sources (the
+    kernel, and the host file that schedules its launches), else None."""
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_1910_04658_gb300", "csrc", f), "rb").read())
+    sha = h.hexdigest()[:16]
     path = os.path.join(ROOT, "profiles", f"{name}.txt")
     try:
         rec = {}
@@ -319,7 +322,7 @@ def run_ours(args, rank, world, dist):
         roof = {"bound": "tensor", "kernel": "pair_tc_kernel<TOPK,JS> (tcgen05.mma kind::mxf4)",
                 "achieved": flops / tk_mean / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "frac": flops / tk_mean / 1e12 / peak,
-                "traffic": profile_traffic("bs_tc_kernel.cuh", "pair_tc_topk_traffic"),
+                "traffic": profile_traffic(("bs_tc_kernel.cuh", "bs_pairs_tc.cu"), "pair_tc_topk_traffic"),
                 "peak_source": ("measured cuBLAS bf16 burst x 6 (nominal dense fp4/bf16 ratio 13.5/2.25), of measured"
                                 if bf16 else "fallback 1.9 PF bf16 x 6, of fallback")}
     else:
@@ -328,7 +331,7 @@ def run_ours(args, rank, world, dist):
         roof = {"bound": "alu", "kernel": "pair_kernel<TOPK,JS> (AND+POPC)",
                 "achieved": achieved, "peak": popc_peak, "unit": "Tword-popc/s",
                 "frac": achieved / popc_peak,
-                "traffic": profile_traffic("bs_pairs.cu", "pair_topk_traffic"),
+                "traffic": profile_traffic(("bs_pairs.cu",), "pair_topk_traffic"),
                 "peak_source": "16 POPC/clk/SM x SMs x max SM clock (recipe units/clocks)"}
     sk_med = sorted(t_sk)[len(t_sk) // 2]
     sk_gbs = sketch_bytes(n, nnz, N) / sk_med / 1e9

@@ -264,7 +264,10 @@ bs_status bs_topk(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ,
  * With c >= 10 a call whose query rows fill R >= 1 rounds of one 128-row
  * block per SM runs those rounds as one launch (every SM sweeps the
  * database tiles in the same order, so the FP4 copy streams from L2) and
- * the rows left over as a second launch with partial lists.
+ * the rows left over as a second launch with partial lists; when the
+ * database's FP4 copy is over 64 MiB that launch cuts each of its T row
+ * blocks into the same min(SMs / T, tiles) parts of the database, one SM per
+ * part, so the SMs holding the same part sweep it together.
  * Environment: for calls that pass BS_VARIANT_AUTO (bs_topk among them) the
  * variable BS_VARIANT, read once, overrides the choice: "popc" forces the
  * CUDA-core kernel, "tc<c>" (c = 0..14) selects configuration c wherever the

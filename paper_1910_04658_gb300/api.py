@@ -44,7 +44,7 @@ def estimate_pairs(A, pcA, Bm, pcB, N: int, measures=("ip", "ham", "js", "cos"),
 def topk(Q, pcQ, DB, pcDB, N: int, k: int, by: str = "js", exclude_self: bool = False,
          stream=None, workspace=None, variant: str = "auto"):
     """Top-k of every query row by `by` (bs_topk_ex); variant: "auto",
-    "popc", "tc" or "tc0" .. "tc11" (a tensor-core block configuration)."""
+    "popc", "tc" or "tc0" .. "tc14" (a tensor-core block configuration)."""
     nQ, nDB = Q.shape[0], DB.shape[0]
     score = torch.empty((nQ, k), dtype=torch.float32, device=Q.device)
     idx = torch.empty((nQ, k), dtype=torch.int32, device=Q.device)

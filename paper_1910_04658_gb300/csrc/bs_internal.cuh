@@ -300,8 +300,9 @@ bs_status launch_merge(int measure, const float *ws_key, const uint32_t *ws_idx,
 // M, one TMEM lane per row), database tiles of 208 rows (the MMA's N)
 constexpr uint32_t kTcQueryRows = 128, kTcTileRows = 208;
 bool tc_supported(const uint32_t *Q, const uint32_t *DB, uint32_t N, uint32_t k);
-// partial lists per row of the balanced schedule with tb-row database tiles
-uint32_t tc_splits(uint32_t nQ, uint32_t nDB, uint32_t tb = 208);
+// partial lists per row of the balanced schedule with tb-row database tiles,
+// or (aligned) of the equal parts the rows after a call's rounds are cut into
+uint32_t tc_splits(uint32_t nQ, uint32_t nDB, uint32_t tb = 208, bool aligned = false);
 // database rows per tile (the MMA's N) of a block configuration
 uint32_t tc_cfg_tile_rows(int cfg);
 // bytes of a k-chunk-tiled copy of an n-row sketch matrix in R-row blocks
@@ -323,9 +324,13 @@ constexpr long long kTcInjectWaitLimit = 2000000ll;
 // rounds of whole row blocks (rows [0, q_split)), the partial lists per row of
 // the launch over the remaining rows, the kernels launched and the partial-
 // list bytes the call needs.
+// an FP4 database copy up to this size stays in L2 (129 MB) while a launch
+// sweeps it, whatever order the blocks read it in
+constexpr size_t kTcL2Resident = (size_t)64 << 20;
 struct TcCallPlan {
     int cfg = -1;
     bool fp4_q = false, fp4_db = false;
+    bool aligned = false;   // the rows after the rounds run in aligned equal parts
     uint32_t rounds = 0, q_split = 0, splits = 1, launches = 0, tile_rows = 208;
     size_t lists_bytes = 0;
 };

@@ -175,6 +175,31 @@ static void single_schedule(uint32_t nQ, uint32_t nDB, Schedule &s, uint64_t *un
     make_schedule(1, &rbs, &tiles, &cost, unit_base, s);
 }
 
+// The rows left after the rounds of a call that reads the FP4 database copy
+// (T < G row blocks): every row block is cut into the same P = min(G / T,
+// tiles) parts of its tile sequence, one block per part (block c: row block
+// c / P, part c % P), so the T blocks holding part p of the T row blocks
+// start at the same tile and sweep the copy together, reading each tile from
+// L2 while it is hot.  Balanced ranges over all G blocks would start nearly
+// every block at a different tile of a copy larger than L2 and fetch most
+// tiles from DRAM; the idle G - T P blocks cost less than that.
+static void aligned_schedule(uint32_t nQ, uint32_t nDB, Schedule &s, uint64_t *unit_base, uint32_t tb) {
+    const uint32_t rbs = (nQ + BM - 1) / BM, tiles = (nDB + tb - 1) / tb;
+    const uint32_t G = max_blocks();
+    if (rbs == 0 || tiles == 0 || rbs > G) {
+        single_schedule(nQ, nDB, s, unit_base, tb);
+        return;
+    }
+    const uint32_t P = std::max<uint32_t>(1, std::min(G / rbs, tiles));
+    s.grid = rbs * P;
+    s.units = (uint64_t)rbs * tiles;
+    s.splits = P;
+    for (uint32_t c = 0; c < s.grid; ++c)
+        s.block_start[c] = (uint64_t)(c / P) * tiles + (uint64_t)(c % P) * tiles / P;
+    s.block_start[s.grid] = s.units;
+    *unit_base = 0;
+}
+
 static void fill_job(Job &J, const uint32_t *pcQ, const uint32_t *pcDB, uint32_t nQ, uint32_t nDB,
                      uint32_t N, uint32_t tb = BN) {
     J.pcQ = pcQ; J.pcDB = pcDB;
@@ -337,11 +362,12 @@ bool tc_store_supported(const uint32_t *A, const uint32_t *B, uint32_t N) {
            (reinterpret_cast<uintptr_t>(B) & 15u) == 0;
 }
 
-uint32_t tc_splits(uint32_t nQ, uint32_t nDB, uint32_t tb) {
+uint32_t tc_splits(uint32_t nQ, uint32_t nDB, uint32_t tb, bool aligned) {
     if (nQ == 0 || nDB == 0) return 1;
     tc::Schedule s;
     uint64_t ub;
-    tc::single_schedule(nQ, nDB, s, &ub, tb);
+    if (aligned) tc::aligned_schedule(nQ, nDB, s, &ub, tb);
+    else tc::single_schedule(nQ, nDB, s, &ub, tb);
     return s.splits;
 }
 
@@ -387,8 +413,9 @@ static cudaError_t launch_measure(int measure, int cfg, const tc::Args<NJ> &p, u
 // block c takes row blocks [c R, (c + 1) R) -- and all blocks sweep the
 // database tiles in the same order at the same time, reading each tile from
 // L2 while it is hot; the rows left over (fewer than one per block) run as a
-// second launch with the balanced ranges and partial lists of the usual
-// schedule.  Otherwise one launch with the balanced ranges.
+// second launch whose row blocks are cut into equal, aligned parts (partial
+// lists, merged by the call) when the copy is too large to stay in L2.
+// Otherwise one launch with the balanced ranges.
 bs_status tc_call_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, int cfg_req, bool same,
                        int kept, TcCallPlan &pl) {
     pl = TcCallPlan();
@@ -405,7 +432,8 @@ bs_status tc_call_plan(uint32_t nQ, uint32_t nDB, uint32_t N, uint32_t k, int cf
     pl.q_split = (uint32_t)std::min<uint64_t>(nQ, (uint64_t)pl.rounds * G * tc::BM);
     const uint32_t nQ2 = nQ - pl.q_split;
     pl.tile_rows = tc_cfg_tile_rows(pl.cfg);
-    pl.splits = nQ2 > 0 ? tc_splits(nQ2, nDB, pl.tile_rows) : 1;
+    pl.aligned = pl.fp4_db && tc_fp4_bytes(nDB, N) > kTcL2Resident;
+    pl.splits = nQ2 > 0 ? tc_splits(nQ2, nDB, pl.tile_rows, pl.aligned) : 1;
     pl.lists_bytes = pl.splits > 1 ? (size_t)pl.splits * nQ2 * k * 8 : 0;
     pl.launches = (kept != KEPT_NONE ? 0 : 1) + (pl.fp4_q ? (same ? 0 : 1) : 1) +
                   (pl.rounds > 0 ? 1 : 0) + (nQ2 > 0 ? 1 : 0) + (pl.splits > 1 ? 1 : 0);
@@ -419,8 +447,13 @@ size_t tc_lists_bytes(uint32_t nQ, uint32_t nDB, uint32_t k) {
     size_t b = s > 1 ? (size_t)s * nQ * k * 8 : 0;
     TcCallPlan pl;
     for (int c = tc::kTcFirstTma; c < tc::kTcConfigs; ++c)
-        if (tc_cfg_fits(c, k) && tc_call_plan(nQ, nDB, 256, k, c, false, KEPT_NONE, pl) == BS_OK)
+        if (tc_cfg_fits(c, k) && tc_call_plan(nQ, nDB, 256, k, c, false, KEPT_NONE, pl) == BS_OK) {
             b = std::max(b, pl.lists_bytes);
+            // the aligned parts a larger N's copy would take instead
+            const uint32_t nQ2 = nQ - pl.q_split;
+            const uint32_t sa = nQ2 > 0 ? tc_splits(nQ2, nDB, pl.tile_rows, true) : 1;
+            if (sa > 1) b = std::max(b, (size_t)sa * nQ2 * k * 8);
+        }
     return b;
 }
 
@@ -489,6 +522,8 @@ bs_status topk_tc(const uint32_t *Q, const uint32_t *pcQ, uint32_t nQ, const uin
             const uint64_t per = (uint64_t)pl.rounds * J.tiles;
             for (uint32_t c = 0; c <= s.grid; ++c) s.block_start[c] = (uint64_t)c * per;
             J.unit_base = 0;
+        } else if (pl.aligned) {
+            tc::aligned_schedule(rows, nDB, s, &J.unit_base, pl.tile_rows);
         } else {
             tc::single_schedule(rows, nDB, s, &J.unit_base, pl.tile_rows);
         }

@@ -60,16 +60,22 @@ def test_tensor_core_plan_parts_match_the_persistent_schedule():
     # The default tensor-core configuration for N = 4096, k = 50 reads FP4
     # copies of both operands: R = rbs // G rounds of whole 128-row blocks go
     # to the G blocks first (block c: row blocks [c R, (c + 1) R)), the rows
-    # left over run as a second launch whose U = row blocks x 240-row database
-    # tiles are dealt out as equal contiguous ranges, block c starting at unit
-    # ceil(c U / G): unit x then sits in block floor(x G / U), and the parts of
-    # a row block are the blocks it spans.
+    # left over (fewer row blocks than G) run as a second launch.  When the
+    # database's FP4 copy (N / 2 bytes a row) is over 64 MiB, that launch cuts
+    # each row block's T 240-row database tiles into P = min(G // rbs, T)
+    # equal parts, one block per part, so every row block has P partial lists;
+    # otherwise its U = row blocks x T units are dealt out as equal contiguous
+    # ranges, block c starting at unit ceil(c U / G): unit x then sits in
+    # block floor(x G / U), and the parts of a row block are the blocks it
+    # spans.
     from paper_1910_04658_gb300 import binding as B
 
     G = 148
 
     def parts(nq, ndb):   # the default configuration's database tiles have 240 rows
         rbs, T = (nq + 127) // 128, (ndb + 239) // 240
+        if ndb * 4096 // 2 > 64 << 20:
+            return max(1, min(G // rbs, T))
         U = rbs * T
         g = min(G, U)
         first = lambda x: (x * g) // U

@@ -241,6 +241,30 @@ def test_topk_split_database_merge(N, by, m, variant):
         check_topk_row(s[r], ix[r], oest[m, r], 100, m)
 
 
+@pytest.mark.parametrize("same", [False, True])
+def test_topk_aligned_parts_after_rounds(same):
+    # a database whose FP4 copy (N / 2 bytes a row, 82 MB here) is too large to
+    # stay in L2: the query rows left after the rounds of whole row blocks run
+    # with every row block cut into the same aligned parts of the database
+    # (rows ending inside a 240-row tile, a ragged last query block), merged
+    # by the call -- bit for bit the CUDA-core kernel's lists
+    N, k = 4096, 50
+    dc = inputs.random_csr(42, 40_001, 1_000_000, 1, 400)
+    ds, dp = _gpu_sketch(dc, N, 6)
+    if same:
+        qs, qp, nq = ds, dp, dc.n
+    else:
+        qc = inputs.random_csr(41, 20_000, 1_000_000, 1, 400)
+        qs, qp = _gpu_sketch(qc, N, 6)
+        nq = qc.n
+    uses_tc, splits, launches = B.bs_topk_plan(nq, dc.n, N, k, B.BS_VARIANT_TC, int(same))
+    assert uses_tc and splits > 1
+    ref_s, ref_i = api.topk(qs, qp, ds, dp, N, k, by="js", exclude_self=same, variant="popc")
+    s, i = api.topk(qs, qp, ds, dp, N, k, by="js", exclude_self=same, variant="tc")
+    assert B.bs_get_async_error() == 0
+    assert torch.equal(i, ref_i) and torch.equal(s, ref_s)
+
+
 @pytest.mark.parametrize("N,by,m", [(256, "ip", 0), (1024, "js", 2), (8192, "cos", 3)])
 def test_topk_tc_dense_and_saturated(N, by, m):
     # counts up to N: the FP4 products must still sum exactly in FP32
