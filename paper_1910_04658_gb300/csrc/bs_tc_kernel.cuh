@@ -536,11 +536,17 @@ __device__ __noinline__ float consider_shared(uint2 *hent, float *root_key, int 
     const float key = rank_key<M>(a, b, c, N, lnA, lnB, invL);
     if (!(key >= eff_k)) return eff_k;            // below the row's known root: cannot enter
     uint32_t spins = 0;
+    // test and test-and-set: a waiter polls with plain reads and sleeps
+    // between them, leaving the sub-partition's issue slots and the
+    // shared-memory atomics to the thread that holds the lock
     while (atomicCAS(&lock[t], 0u, 1u) != 0u) {
-        if (++spins > (1u << 22)) {               // never expected: report, drop the pair
-            raise_error(err, BS_ERR_TIMEOUT);
-            return eff_k;
-        }
+        do {
+            if (++spins > (1u << 22)) {           // never expected: report, drop the pair
+                raise_error(err, BS_ERR_TIMEOUT);
+                return eff_k;
+            }
+            __nanosleep(32);
+        } while (*reinterpret_cast<volatile unsigned int *>(&lock[t]) != 0u);
     }
     __threadfence_block();
     Heap h;
@@ -1183,6 +1189,8 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
                 const int size_before = st.size;
                 const uint32_t root_before = st.thr_i;
                 const float rootk_before = st.thr_k;
+                const float effk_before = eff_k;
+                const uint32_t effi_before = eff_i;
                 auto insert_direct = [&](uint32_t m) {
                     while (__any_sync(0xffffffffu, m != 0)) {
                         if (m) {
@@ -1225,7 +1233,9 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
                     thr_key[grp * BM + r] = st.thr_k;
                     thr_idx[grp * BM + r] = st.thr_i;
                 }
-                if (eff_i != NO_IDX) filt = make_filter<M>(eff_k, rc, invL, J.log2N);
+                // the bound again only if this chunk's insertions raised the threshold
+                if (eff_i != NO_IDX && (eff_k != effk_before || eff_i != effi_before))
+                    filt = make_filter<M>(eff_k, rc, invL, J.log2N);
             }
             tc_fence_before();
             __syncwarp();
