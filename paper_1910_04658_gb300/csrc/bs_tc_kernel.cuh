@@ -64,7 +64,6 @@ namespace tc {
 
 constexpr int BM = kTcQueryRows;           // query rows per block (UMMA M, TMEM lanes)
 constexpr int BN = kTcTileRows;            // database rows per tile (UMMA N)
-constexpr int BNP = 256;                   // per-column arrays padded to whole 32-column chunks
 constexpr int KCW = 4;                     // packed words per k-chunk (128 bits)
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t SF_COL = 480;           // unit scale factors (A at +0, B at +16)
@@ -140,8 +139,10 @@ struct Smem {
     static_assert(ABYTES % 1024 == 0 && STAGE % 1024 == 0, "stage alignment");
     static constexpr int op = 0;
     static constexpr int raw = op + (NOP == 0 ? NB * STAGE : (NB > 0 ? NB : NOP) * G::BYTES);
-    static constexpr int col = raw + RD * (NB > 0 ? G::RAW_A : G::RAW_SLOT);   // [2 tiles][3][BNP] floats
-    static constexpr int bars = col + 2 * 3 * BNP * 4;
+    // per-column (b, f0) of a tile, one copy per epilogue warp for its
+    // group's columns: 4 x TB float2
+    static constexpr int col = raw + RD * (NB > 0 ? G::RAW_A : G::RAW_SLOT);
+    static constexpr int bars = col + 4 * TB * 8;
     static constexpr int thr = bars + 512;                      // [NG][BM] key, idx, size
     static constexpr int lock = thr + NG * BM * 12;             // [BM] shared-heap row locks
     static constexpr int cbuf = lock + BM * 4;                  // [NG][CB][BM] admitted pairs
@@ -701,7 +702,7 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *op = base + Smem::op;
     uint8_t *raw = base + Smem::raw;
-    float *colv = reinterpret_cast<float *>(base + Smem::col);      // [2][3][BNP]
+    float2 *colv = reinterpret_cast<float2 *>(base + Smem::col);    // [4][TB] per-warp column values
     uint64_t *bars = reinterpret_cast<uint64_t *>(base + Smem::bars);
     uint64_t *op_full = bars, *op_empty = bars + NOP;
     uint64_t *raw_full = bars + 2 * NOP, *raw_empty = raw_full + RD;
@@ -981,6 +982,16 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
         constexpr int G3 = TB == 240 ? 80 : 64;
         const int c_lo = NG == 1 ? 0 : (NG == 2 ? grp * GSPLIT : grp * G3);
         const int c_hi = NG == 1 ? TB : (NG == 2 ? (grp == 1 ? TB : GSPLIT) : (grp == NG - 1 ? TB : (grp + 1) * G3));
+        // the widest group's columns, and the columns each lane prepares
+        constexpr int GW = NG == 1 ? TB
+                         : (NG == 2 ? (TB - GSPLIT > GSPLIT ? TB - GSPLIT : GSPLIT)
+                                    : (TB - 2 * G3 > G3 ? TB - 2 * G3 : G3));
+        constexpr int CPL = (GW + 31) / 32;
+        // this warp's own copy of its group's per-column values (raw b, bound
+        // term f0), indexed by column - c_lo: every read of them (bound test,
+        // buffered and direct insertions) stays within the warp, so the
+        // group's warps need no barrier between tiles
+        float2 *cv = colv + 4 * c_lo + ((warp - EPI0) & 3) * (c_hi - c_lo);
         // row constants of the current row block (set at each segment start)
         uint32_t q = 0, a = 0;
         bool row_ok = false;
@@ -992,7 +1003,7 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
         uint32_t *cb = reinterpret_cast<uint32_t *>(base + Smem::cbuf) + (size_t)grp * CB * BM;
         int nbuf = 0;
         uint32_t d_col0 = 0;          // first column of the tile the buffer belongs to
-        const float2 *d_cv = reinterpret_cast<const float2 *>(colv);   // that tile's (b, f0) per column
+        const float2 *d_cv = cv;      // that tile's (b, f0) per column (column - c_lo)
         float eff_k = -INFINITY;                   // threshold the filter was built from
         uint32_t eff_i = NO_IDX;
         RowFilter filt;
@@ -1000,7 +1011,7 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
         TileSeq<DYN> seq;
         if (DYN) seq.init_dynamic(jobs, njobs, item_full, item_ring);
         else seq.init_static(jobs, njobs, u_lo, n_my_tiles);
-        uint32_t b_pre[2] = {0u, 0u};   // counts of this thread's columns of the next tile
+        uint32_t b_pre[CPL];            // counts of this lane's columns of the next tile
         bool b_pre_ok = false;          // b_pre holds them
         uint32_t N = jobs[0].N;
         float invL = jobs[0].invL;
@@ -1013,11 +1024,11 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
                     const uint32_t j = ent & 255u;
                     if (SHARED) {
                         const float root = consider_shared<M>(hent, thr_key, heap_size, row_lock, r, d_col0 + j,
-                                                              ent >> 8, (uint32_t)d_cv[j].x, a, lnA, eff_k, N,
+                                                              ent >> 8, (uint32_t)d_cv[j - c_lo].x, a, lnA, eff_k, N,
                                                               invL, (int)p.k, p.err);
                         if (root > eff_k) { eff_k = root; eff_i = 0xFFFFFFFEu; }
                     } else {
-                        st = consider<M>(st, hent, r, d_col0 + j, ent >> 8, (uint32_t)d_cv[j].x, a, lnA,
+                        st = consider<M>(st, hent, r, d_col0 + j, ent >> 8, (uint32_t)d_cv[j - c_lo].x, a, lnA,
                                          eff_k, eff_i, N, invL, (int)p.k);
                         if (st.thr_i != NO_IDX && better(st.thr_k, st.thr_i, eff_k, eff_i)) {
                             eff_k = st.thr_k; eff_i = st.thr_i;
@@ -1053,21 +1064,22 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
                 }
                 if (MODE == MODE_TOPK && NG >= 2) named_sync(9, 128 * NG);
             }
-            float2 *cv = reinterpret_cast<float2 *>(colv + (t & 1) * 3 * BNP);
             // per-column values (raw b, bound term f0) of this group's columns,
-            // one or two per thread; their counts were fetched during the
+            // CPL per lane, into the warp's own copy (its previous tile's
+            // insertions are done); their counts were fetched during the
             // previous tile (the first tile fetches its own)
+            __syncwarp();
             if (!b_pre_ok) {
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const uint32_t j = (uint32_t)(c_lo + e + 128 * i);
+                for (int i = 0; i < CPL; ++i) {
+                    const uint32_t j = (uint32_t)(c_lo + lane + 32 * i);
                     const uint32_t col = tile * TB + j;
                     b_pre[i] = (j < (uint32_t)c_hi && col < J.nDB) ? __ldg(J.pcDB + col) : 0u;
                 }
             }
 #pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int j = c_lo + e + 128 * i;
+            for (int i = 0; i < CPL; ++i) {
+                const int j = c_lo + lane + 32 * i;
                 if (j >= c_hi) continue;
                 const uint32_t b = b_pre[i];
                 const uint32_t b_cl = b < N - 1 ? b : N - 1;
@@ -1078,7 +1090,7 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
                 else if (M == M_COS) f0 = sqrtf(fmaxf(-logf(Bf / (float)N), 0.0f));
                 else if (M == M_IP) f0 = Bf;
                 else f0 = sqrtf(Bf);
-                cv[j] = make_float2((float)b, f0);   // raw count: U' is formed from the raw a, b, c
+                cv[j - c_lo] = make_float2((float)b, f0);   // raw count: U' is formed from the raw a, b, c
             }
             // the next tile's counts, in flight during this one (when the next
             // tile is known: the rest of a static range, or of the same row block)
@@ -1095,20 +1107,19 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
                 if (b_pre_ok) {
                     const Job &J2 = jobs[nj];
 #pragma unroll
-                    for (int i = 0; i < 2; ++i) {
-                        const uint32_t j = (uint32_t)(c_lo + e + 128 * i);
+                    for (int i = 0; i < CPL; ++i) {
+                        const uint32_t j = (uint32_t)(c_lo + lane + 32 * i);
                         const uint32_t col = ntile * TB + j;
                         b_pre[i] = (j < (uint32_t)c_hi && col < J2.nDB) ? __ldg(J2.pcDB + col) : 0u;
                     }
                 }
             }
-            named_sync(2 + grp, 128);
+            __syncwarp();   // the warp's column values are written
             const uint32_t ab = t & 1;
             wait(&acc_full[ab], (t >> 1) & 1);
             tc_fence_after();
             const uint32_t col0 = tile * TB;
             d_col0 = col0;
-            d_cv = cv;
             // every lane stays in the loops below (they vote); dead rows admit nothing
             const bool live = row_ok && !*abort_flag;
             const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + ab * TB;
@@ -1130,8 +1141,8 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
                             if (jj >= width || col_c + jj >= J.nDB) break;
                             const int j = c0 + jj;
                             const uint32_t c = (uint32_t)__uint_as_float(v[jj]);
-                            const uint32_t b = (uint32_t)cv[j].x;
-                            const float lnB = cv[j].y;
+                            const uint32_t b = (uint32_t)cv[j - c_lo].x;
+                            const float lnB = cv[j - c_lo].y;
                             const size_t o = o0 + jj;
                             if (J.counts) J.counts[o] = c;
                             float *out = J.out + o;
@@ -1168,7 +1179,7 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
                     const int j = c0 + jj;
                     const float cf = __uint_as_float(v[jj]);   // exact count
                     // U' = N - min(a + b - c, N - 1) = max(N - a - b + c, 1), exact in FP32
-                    const float2 bf = cv[j];
+                    const float2 bf = cv[j - c_lo];
                     const float U = fmaxf(Na - bf.x + cf, 1.0f);
                     if (admit<M>(filt, U, bf.y)) mask |= 1u << jj;
                 }
@@ -1200,11 +1211,11 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
                             const int j = c0 + (int)jj;
                             if (SHARED) {
                                 const float root = consider_shared<M>(hent, thr_key, heap_size, row_lock,
-                                                                      r, col_c + jj, c, (uint32_t)cv[j].x, a, lnA,
+                                                                      r, col_c + jj, c, (uint32_t)cv[j - c_lo].x, a, lnA,
                                                                       eff_k, N, invL, (int)p.k, p.err);
                                 if (root > eff_k) { eff_k = root; eff_i = 0xFFFFFFFEu; }
                             } else {
-                                st = consider<M>(st, hent, r, col_c + jj, c, (uint32_t)cv[j].x, a, lnA,
+                                st = consider<M>(st, hent, r, col_c + jj, c, (uint32_t)cv[j - c_lo].x, a, lnA,
                                                  eff_k, eff_i, N, invL, (int)p.k);
                                 if (st.thr_i != NO_IDX && better(st.thr_k, st.thr_i, eff_k, eff_i)) {
                                     eff_k = st.thr_k; eff_i = st.thr_i;
