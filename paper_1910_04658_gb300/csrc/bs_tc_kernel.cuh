@@ -972,7 +972,6 @@ __global__ void __launch_bounds__(threads_for(NG, NOP > 0), 1)
     } else {
         // ------------------------------ epilogue ------------------------------
         const int grp = (warp - EPI0) >> 2;        // epilogue group
-        const int e = tid - 32 * EPI0 - 128 * grp; // 0..127 within the group
         const int quarter = warp & 3;              // TMEM lanes this warp may access
         const int r = quarter * 32 + lane;         // row within the block
         // tile columns of this group
