@@ -529,7 +529,7 @@ __device__ __forceinline__ RowState consider(RowState st, uint2 *hent, int t, ui
 // root is repeated under the lock.  Returns the root key once the heap is
 // full, else -inf.
 template <int M>
-__device__ __noinline__ float consider_shared(uint2 *hent, float *root_key, int *hsize,
+__device__ __forceinline__ float consider_shared(uint2 *hent, float *root_key, int *hsize,
                                               unsigned int *lock, int t, uint32_t col, uint32_t c,
                                               uint32_t b, uint32_t a, float lnA, float eff_k,
                                               uint32_t N, float invL, int cap, unsigned int *err) {
